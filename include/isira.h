@@ -1,0 +1,171 @@
+/*
+ * isira.h -- C ABI of the GB300 (sm_103a) iSIRA eigensolver for graph Laplacians.
+ *
+ * Problem (paper Sec. 1.1 and Sec. 2, Eq. 2.1; Algorithm 2 REQUIRE/ENSURE): given a
+ * simple, connected, undirected, unweighted graph with Laplacian L = D - A (Eq. 1.1),
+ * find the d smallest positive eigenvalues of L and orthonormal eigenvectors, with
+ * the integrated shift-invert residual Arnoldi method (Algorithm 2): an FP64 outer
+ * Rayleigh-Ritz loop whose expansion vectors come from inexact solves of the
+ * trimmed, shifted, deflated system of Theorem 2.6 (Eq. 2.14) followed by the
+ * back-map of Theorem 2.4 (Eq. 2.5).
+ *
+ * Conventions shared by every entry point
+ *  - Graphs are CSR adjacency patterns in DEVICE memory: row_ptr int64[n+1]
+ *    (row_ptr[0] == 0, non-decreasing, row_ptr[n] == nnz), col_idx int32[nnz], each
+ *    row's columns sorted ascending, the pattern symmetric, with no self loops and
+ *    no duplicates.  There is no values array: every edge has weight 1 and the
+ *    degree of vertex r is row_ptr[r+1] - row_ptr[r].  The caller owns the CSR; it
+ *    must stay alive and unmodified until isira_destroy.
+ *  - Vertex indices are 0-based.  Dense device matrices are column-major with
+ *    leading dimension n.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All
+ *    work of a handle is ordered on the stream given to isira_create.  Calls that
+ *    return host results (isira_solve, isira_eigpairs) synchronise that stream.
+ *  - The library owns all workspace (allocated in isira_create / isira_solve, freed
+ *    in isira_destroy).  No entry point throws; errors are returned as isira_status.
+ *  - A handle is not thread safe: use one handle per host thread.
+ */
+#ifndef ISIRA_H
+#define ISIRA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ISIRA_API __attribute__((visibility("default")))
+#else
+#define ISIRA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct isira_handle_s* isira_handle;
+
+typedef enum {
+    ISIRA_OK = 0,
+    ISIRA_ERR_INVALID_ARG = 1,     /* a pointer, size or option is out of range */
+    ISIRA_ERR_BAD_GRAPH = 2,       /* validate=1 found a malformed CSR pattern */
+    ISIRA_ERR_NOT_CONNECTED = 3,   /* a second (near) zero eigenvalue was locked */
+    ISIRA_ERR_NO_CONVERGENCE = 4,  /* max_outer reached; already locked pairs are kept */
+    ISIRA_ERR_CUDA = 5,            /* a CUDA runtime call failed */
+    ISIRA_ERR_OOM = 6,             /* device or pinned allocation failed */
+    ISIRA_ERR_NOT_SOLVED = 7       /* eigpairs requested before a successful solve */
+} isira_status;
+
+enum { ISIRA_FP64 = 0,   /* inner solve in FP64 ("plain") */
+       ISIRA_MIXED = 1   /* inner solve in FP32 with FP32 accumulation, outer loop FP64 */ };
+
+typedef struct {
+    int precision;        /* ISIRA_FP64 or ISIRA_MIXED */
+    int m, q;             /* search-space limit and restart size (Algorithm 2, d <= q < m <= 64);
+                             0 = m = max(20, 2d+10), q = max(d+2, m/2) */
+    double tau_inner;     /* inner relative (preconditioned) residual target; <= 0: 1e-3 */
+    int max_inner;        /* inner iteration cap per solve; <= 0: 5000 */
+    int max_outer;        /* outer iteration cap over all eigenpairs; <= 0: 20000 */
+    int64_t trim_index;   /* trimmed vertex i (Theorem 2.3); < 0: vertex of maximum degree,
+                             smallest id on ties (Remark 4.1(i)) */
+    double delta;         /* deflation constant (Eq. 2.6); <= 0: 2 * max degree (Remark 4.1(ii)) */
+    double sigma_omega;   /* after locking lambda_j: sigma = theta2 - max(omega*(theta2 - lambda_j),
+                             0.01*theta2) (Algorithm 2 "move sigma ~ theta2"); <= 0: 0.1 */
+    int drop_rank1;       /* 1: omit (sigma/n) 1h 1h^T from the inner operator (Remark 3.1) */
+    int validate;         /* 1: check the CSR pattern on the device in isira_create */
+    uint64_t seed;        /* SplitMix64 seed of replacement vectors after an orthogonalisation
+                             breakdown and of the default start vector */
+    int spmv_lanes;       /* lanes per row of the light-row SpMV (1,2,4,8,16,32); <= 0: autotune */
+    int inner_chunk;      /* inner iterations launched between convergence checks; <= 0: 16 */
+} isira_opts;
+
+typedef struct {
+    int64_t n, nnz;
+    int64_t trim_index;       /* the vertex actually trimmed */
+    int64_t max_degree;
+    double delta;             /* the deflation constant actually used */
+    double norm_L;            /* Gershgorin bound 2 * max degree, used to scale residuals */
+    int spmv_lanes;           /* chosen light-row lanes per row */
+    int n_heavy_rows, n_medium_rows;
+    int n_locked;             /* eigenpairs locked by the last solve */
+    int outer_steps;          /* Algorithm 2 while-loop iterations */
+    int restarts, breakdowns;
+    long long inner_iters;    /* total MINRES iterations */
+    long long inner_solves;
+    long long spmv_launches;  /* launches of the inner operator kernel (phase 1) */
+    double solve_ms;          /* host wall time of the last isira_solve */
+    double inner_phase1_ms;   /* summed device time of phase-1 launches (only with profiling on) */
+    long long inner_phase1_timed; /* number of phase-1 launches timed */
+} isira_stats;
+
+/* Fills *opts with the defaults listed above (precision = ISIRA_MIXED). */
+ISIRA_API void isira_default_opts(isira_opts* opts);
+
+/* Human-readable name of a status code (static string). */
+ISIRA_API const char* isira_error_string(isira_status s);
+
+/* Creates a solver for the graph (d_row_ptr, d_col_idx) with n vertices and nnz
+ * stored adjacency entries (twice the number of edges).  Runs the setup of
+ * Remark 4.1 on the device (degrees, maximum degree, trimmed index, delta) and picks
+ * the SpMV layout.  opts may be NULL (defaults).  Requires n >= 3.  On success *out
+ * receives a handle to release with isira_destroy; on failure *out is NULL. */
+ISIRA_API isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64_t* d_row_ptr,
+                          const int32_t* d_col_idx, const isira_opts* opts, void* stream);
+
+/* Algorithm 2: computes the k (the paper's d, 1 <= k <= min(32, n-2)) smallest positive
+ * eigenpairs.  sigma: initial shift (the paper uses 0).  tol: the paper's epsilon, an
+ * absolute bound on ||W s1 - theta1 U s1||_2 for unit Ritz vectors (Algorithm 2 line 8).
+ * d_u0: optional device n-vector, the k0 = 1 start basis (must be orthogonal to the
+ * all-ones vector and of unit norm; NULL = a SplitMix64 vector from opts.seed).
+ * Blocks until done.  Returns ISIRA_ERR_NO_CONVERGENCE if max_outer is reached (pairs
+ * locked so far stay available), ISIRA_ERR_NOT_CONNECTED if a locked eigenvalue is
+ * below 1e-10 * norm_L. */
+ISIRA_API isira_status isira_solve(isira_handle h, int k, double sigma, double tol, const double* d_u0);
+
+/* Results of the last solve, sorted ascending.  h_eigvals: host double[n_locked];
+ * d_eigvecs: device n-by-n_locked column-major (may be NULL); h_true_resid: host
+ * double[n_locked] receiving ||L v_j - lambda_j v_j||_2 / norm_L computed in FP64
+ * (may be NULL).  *n_out (may be NULL) receives n_locked. */
+ISIRA_API isira_status isira_eigpairs(isira_handle h, double* h_eigvals, double* d_eigvecs, double* h_true_resid,
+                            int* n_out);
+
+/* Counters of the handle (see isira_stats). */
+ISIRA_API isira_status isira_get_stats(isira_handle h, isira_stats* out);
+
+/* 1 = time every phase-1 launch with CUDA events during later solves (adds events
+ * between launches; results unchanged), 0 = off. */
+ISIRA_API isira_status isira_set_profiling(isira_handle h, int on);
+
+/* Releases the handle and all its device memory.  NULL is ignored. */
+ISIRA_API void isira_destroy(isira_handle h);
+
+/* ---------------------------------------------------------------------------------
+ * Component entry points: single steps of the method on the handle's graph, used by
+ * tests and benchmarks.  Device pointers; results ordered on the handle's stream;
+ * each call synchronises before returning.
+ */
+
+/* The implicit operator of Theorem 2.6 (Eq. 2.14) applied in n-space:
+ *   y_r = (deg_r - sigma) x_r - sum_{c in N(r)} x_c + (sigma/n) sum(x) + delta sum_t V_rt (V^T x)_t
+ * for r != trim, y_trim = 0, with x_trim treated as 0 (drop_rank1 from the handle's
+ * options).  precision selects float (ISIRA_MIXED) or double (ISIRA_FP64) x and y.
+ * d_V: n-by-c double matrix (may be NULL when c == 0), 0 <= c <= 31. */
+ISIRA_API isira_status isira_apply_operator(isira_handle h, int precision, double sigma, int c, const double* d_V,
+                                  const void* d_x, void* d_y);
+
+/* One inner solve (Algorithm 2 line 17): preconditioned MINRES on the operator
+ * above for the right-hand side d_r (double n-vector, its trim entry ignored) to
+ * relative preconditioned residual tau, then the back-map of Eq. 2.5:
+ * d_z (double n-vector) is orthogonal to the all-ones vector.  *iters and *relres
+ * (may be NULL) receive the iteration count and the final relative residual estimate. */
+ISIRA_API isira_status isira_inner_solve(isira_handle h, int precision, double sigma, int c, const double* d_V,
+                               const double* d_r, double tau, int max_it, double* d_z, int* iters,
+                               double* relres);
+
+/* All eigenpairs of a symmetric k-by-k matrix (k <= 64), Algorithm 2 line 6: one CTA of
+ * parallel cyclic Jacobi in FP64.  d_H: k-by-k column-major input (not modified);
+ * d_theta: k ascending eigenvalues; d_S: k-by-k unit eigenvectors, each signed so that
+ * its largest-magnitude entry (first on ties) is positive.  stream as above. */
+ISIRA_API isira_status isira_sym_eig(int k, const double* d_H, double* d_theta, double* d_S, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISIRA_H */

@@ -1,0 +1,238 @@
+"""Thin Python binding of libisira (GB300 / sm_103a iSIRA eigensolver, arXiv:1710.07080).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``libisira.so``.  PyTorch provides device memory and the current CUDA stream.
+The C entry points keep their names (``isira_create``, ``isira_solve``, ...);
+:func:`solve` is the one-call convenience wrapper.  There is no CPU fallback:
+if the library is missing, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libisira.so")
+
+ISIRA_OK = 0
+ISIRA_ERR_INVALID_ARG = 1
+ISIRA_ERR_BAD_GRAPH = 2
+ISIRA_ERR_NOT_CONNECTED = 3
+ISIRA_ERR_NO_CONVERGENCE = 4
+ISIRA_ERR_CUDA = 5
+ISIRA_ERR_OOM = 6
+ISIRA_ERR_NOT_SOLVED = 7
+
+ISIRA_FP64 = 0
+ISIRA_MIXED = 1
+
+EXPORTED = ["isira_default_opts", "isira_error_string", "isira_create", "isira_solve", "isira_eigpairs",
+            "isira_get_stats", "isira_set_profiling", "isira_destroy", "isira_apply_operator",
+            "isira_inner_solve", "isira_sym_eig"]
+
+
+class isira_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("m", C.c_int), ("q", C.c_int), ("tau_inner", C.c_double),
+                ("max_inner", C.c_int), ("max_outer", C.c_int), ("trim_index", C.c_int64), ("delta", C.c_double),
+                ("sigma_omega", C.c_double), ("drop_rank1", C.c_int), ("validate", C.c_int), ("seed", C.c_uint64),
+                ("spmv_lanes", C.c_int), ("inner_chunk", C.c_int)]
+
+
+class isira_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("trim_index", C.c_int64), ("max_degree", C.c_int64),
+                ("delta", C.c_double), ("norm_L", C.c_double), ("spmv_lanes", C.c_int),
+                ("n_heavy_rows", C.c_int), ("n_medium_rows", C.c_int), ("n_locked", C.c_int),
+                ("outer_steps", C.c_int), ("restarts", C.c_int), ("breakdowns", C.c_int),
+                ("inner_iters", C.c_longlong), ("inner_solves", C.c_longlong), ("spmv_launches", C.c_longlong),
+                ("solve_ms", C.c_double), ("inner_phase1_ms", C.c_double), ("inner_phase1_timed", C.c_longlong)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libisira.so is not built ({LIB_PATH}); run __graft_entry__.build() or "
+                          "python paper_1710_07080_gb300/_build.py")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    lib.isira_default_opts.argtypes = [C.POINTER(isira_opts)]
+    lib.isira_default_opts.restype = None
+    lib.isira_error_string.argtypes = [I]
+    lib.isira_error_string.restype = C.c_char_p
+    lib.isira_create.argtypes = [C.POINTER(P), I64, I64, P, P, C.POINTER(isira_opts), P]
+    lib.isira_create.restype = I
+    lib.isira_solve.argtypes = [P, I, D, D, P]
+    lib.isira_solve.restype = I
+    lib.isira_eigpairs.argtypes = [P, P, P, P, C.POINTER(I)]
+    lib.isira_eigpairs.restype = I
+    lib.isira_get_stats.argtypes = [P, C.POINTER(isira_stats)]
+    lib.isira_get_stats.restype = I
+    lib.isira_set_profiling.argtypes = [P, I]
+    lib.isira_set_profiling.restype = I
+    lib.isira_destroy.argtypes = [P]
+    lib.isira_destroy.restype = None
+    lib.isira_apply_operator.argtypes = [P, I, D, I, P, P, P]
+    lib.isira_apply_operator.restype = I
+    lib.isira_inner_solve.argtypes = [P, I, D, I, P, P, D, I, P, C.POINTER(I), C.POINTER(D)]
+    lib.isira_inner_solve.restype = I
+    lib.isira_sym_eig.argtypes = [I, P, P, P, P]
+    lib.isira_sym_eig.restype = I
+    return lib
+
+
+lib = _load()
+
+
+class IsiraError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {lib.isira_error_string(status).decode()} (status {status})")
+
+
+def check(status: int, where: str) -> int:
+    if status != ISIRA_OK:
+        raise IsiraError(status, where)
+    return status
+
+
+def default_opts(**kw) -> isira_opts:
+    o = isira_opts()
+    lib.isira_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_ptr(stream=None) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclass
+class Result:
+    eigvals: "object"        # torch.float64 [k] on the CPU, ascending
+    eigvecs: "object"        # torch.float64 [n, k] on the GPU
+    true_resid: "object"     # torch.float64 [k]: ||L v - lambda v|| / (2 max degree)
+    stats: dict
+    status: int
+
+
+class Solver:
+    """Owns an isira handle for one graph (CSR on the GPU, kept alive by this object)."""
+
+    def __init__(self, row_ptr, col_idx, stream=None, **opts):
+        import torch
+        if row_ptr.dtype != torch.int64 or col_idx.dtype != torch.int32:
+            raise TypeError("row_ptr must be int64 and col_idx int32")
+        if not (row_ptr.is_cuda and col_idx.is_cuda):
+            raise TypeError("the CSR arrays must be CUDA tensors")
+        self.row_ptr = row_ptr.contiguous()
+        self.col_idx = col_idx.contiguous()
+        self.n = self.row_ptr.numel() - 1
+        self.nnz = self.col_idx.numel()
+        self.opts = default_opts(**opts)
+        self.stream = _stream_ptr(stream)
+        h = C.c_void_p()
+        check(lib.isira_create(C.byref(h), self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col_idx),
+                               C.byref(self.opts), self.stream), "isira_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.isira_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def stats(self) -> dict:
+        st = isira_stats()
+        check(lib.isira_get_stats(self.h, C.byref(st)), "isira_get_stats")
+        return st.as_dict()
+
+    def set_profiling(self, on: bool):
+        check(lib.isira_set_profiling(self.h, int(bool(on))), "isira_set_profiling")
+
+    def solve(self, k: int, sigma: float = 0.0, tol: float | None = None, u0=None, rel_tol: float = 1e-8,
+              raise_on_error: bool = True) -> int:
+        """Algorithm 2.  tol: absolute bound on ||r||_2 (the paper's epsilon); default rel_tol * 2 max degree."""
+        if tol is None:
+            tol = rel_tol * self.stats()["norm_L"]
+        st = lib.isira_solve(self.h, int(k), float(sigma), float(tol), _ptr(u0))
+        if raise_on_error and st not in (ISIRA_OK,):
+            raise IsiraError(st, "isira_solve")
+        return st
+
+    def eigpairs(self, want_vectors: bool = True, want_resid: bool = True):
+        import torch
+        st = self.stats()
+        k = st["n_locked"]
+        lam = torch.empty(k, dtype=torch.float64)
+        vec = torch.empty((k, self.n), dtype=torch.float64, device=self.row_ptr.device) if want_vectors else None
+        res = torch.empty(k, dtype=torch.float64) if want_resid else None
+        nout = C.c_int(0)
+        check(lib.isira_eigpairs(self.h, _ptr(lam), _ptr(vec), _ptr(res), C.byref(nout)), "isira_eigpairs")
+        return lam, (vec.t() if vec is not None else None), res
+
+    def apply_operator(self, x, sigma: float = 0.0, V=None):
+        """y = trimmed, shifted, deflated operator (Eq. 2.14) applied in n-space."""
+        import torch
+        prec = ISIRA_MIXED if x.dtype == torch.float32 else ISIRA_FP64
+        y = torch.empty_like(x)
+        c = 0 if V is None else V.shape[1]
+        Vc = None if V is None else V.t().contiguous()   # column-major n-by-c
+        check(lib.isira_apply_operator(self.h, prec, float(sigma), c, _ptr(Vc), _ptr(x.contiguous()), _ptr(y)),
+              "isira_apply_operator")
+        return y
+
+    def inner_solve(self, r, sigma: float = 0.0, V=None, tau: float = 1e-3, max_it: int = 5000,
+                    precision: int = ISIRA_MIXED):
+        import torch
+        z = torch.empty_like(r, dtype=torch.float64)
+        c = 0 if V is None else V.shape[1]
+        Vc = None if V is None else V.t().contiguous()
+        its = C.c_int(0)
+        rel = C.c_double(0.0)
+        check(lib.isira_inner_solve(self.h, precision, float(sigma), c, _ptr(Vc), _ptr(r.contiguous()), float(tau),
+                                    int(max_it), _ptr(z), C.byref(its), C.byref(rel)), "isira_inner_solve")
+        return z, its.value, rel.value
+
+
+def sym_eig(H):
+    """All eigenpairs of a symmetric k-by-k CUDA float64 matrix on the GPU (k <= 64)."""
+    import torch
+    k = H.shape[0]
+    Hc = H.t().contiguous()          # column-major
+    th = torch.empty(k, dtype=torch.float64, device=H.device)
+    S = torch.empty((k, k), dtype=torch.float64, device=H.device)
+    check(lib.isira_sym_eig(k, _ptr(Hc), _ptr(th), _ptr(S), _stream_ptr()), "isira_sym_eig")
+    return th, S.t()                 # S was written column-major
+
+
+def solve(row_ptr, col_idx, k: int, sigma: float = 0.0, tol: float | None = None, rel_tol: float = 1e-8, u0=None,
+          **opts) -> Result:
+    """Computes the k smallest positive eigenpairs of the Laplacian of the graph (row_ptr, col_idx)."""
+    with Solver(row_ptr, col_idx, **opts) as s:
+        status = s.solve(k, sigma, tol, u0=u0, rel_tol=rel_tol, raise_on_error=False)
+        if status not in (ISIRA_OK, ISIRA_ERR_NO_CONVERGENCE, ISIRA_ERR_NOT_CONNECTED):
+            raise IsiraError(status, "isira_solve")
+        lam, vec, res = s.eigpairs()
+        return Result(lam, vec, res, s.stats(), status)

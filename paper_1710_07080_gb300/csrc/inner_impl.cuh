@@ -1,0 +1,579 @@
+// inner_impl.cuh -- the inexact inner solve of Algorithm 2 (line 17) on the GPU.
+//
+// Operator (Theorem 2.6, Eq. 2.14), applied in n-space with the trimmed entry i
+// pinned to zero (x_i = 0 in every Krylov vector, y_i = 0):
+//   (Mh x)_r = (deg_r - sigma) x_r - sum_{c in N(r)} x_c + (sigma/n) 1^T x + delta (Vh (Vh^T x))_r.
+// Preconditioner (Remark 3.2 with a diagonal Mh_sigma, Eq. 3.6 for the deflation):
+//   P = D + delta Vh Vh^T,  D = diag(max(deg_r - sigma, deg_r / 2)),
+//   P^{-1} y = D^{-1} (y - Vh t),  t = C^{-1} Vh^T D^{-1} y,  C = delta^{-1} I + Vh^T D^{-1} Vh.
+// Solver: preconditioned MINRES (Paige & Saunders 1975).  One iteration k is two
+// launches:
+//   phase 1: the SpMV with the whole row epilogue fused in: y1 = Mh v_k - (beta_k /
+//            beta_{k-1}) r_{k-1}, with r_{k-1} = P z_{k-1} rebuilt from z_{k-1} (so the
+//            Lanczos residual vectors are never stored), the deferred solution update
+//            of iteration k-1 (w, x), and the reductions alpha_k = v_k^T y1 and
+//            Vh^T D^{-1} y1;
+//   phase 2: y = y1 - (alpha_k / beta_k) r_k, z_{k+1} = P^{-1} y (SMW), and the
+//            reductions y^T z (beta_{k+1}^2), 1^T z, Vh^T z; its last block runs the
+//            Givens recurrence and the stopping test.
+// Vectors per row and iteration: z_k (gathered), z_{k-1}, Y, three rotating w
+// buffers, x, and c columns of Vh.
+#pragma once
+#include "internal.h"
+
+namespace isira {
+
+template <typename T>
+__device__ __forceinline__ T precond_diag(T deg, T sigma) {
+    T m = deg - sigma;
+    T h = deg * T(0.5);
+    return m < h ? h : m;
+}
+
+template <typename T>
+__device__ __forceinline__ T* wbuf(const InnerArgs<T>& a, int j) {
+    int r = j % 3;
+    return r == 0 ? a.wb0 : (r == 1 ? a.wb1 : a.wb2);
+}
+
+// ------------------------------------------------------------------ phase 1
+
+template <typename T, int NC>
+struct Phase1Epi {
+    int64_t trim, ldv;
+    T sigma;
+    int c;
+    const T* Vt;
+    T* Y; T* x;
+    const T* zc; const T* zp; const T* wo2; const T* wo1; T* wn;
+    T inv_beta, cprev, inv_oldb, s_term, oldeps, dlt, inv_gamma, phi;
+    int has_prev;
+    const T* u1s;          // shared memory, c entries
+    T acc[1 + NC];
+
+    __device__ __forceinline__ void operator()(int64_t r, int64_t deg, T gsum) {
+        if (r == trim) {
+            Y[r] = T(0);
+            if (has_prev) wn[r] = T(0);
+            return;
+        }
+        const T degT = (T)deg;
+        const T zr = zc[r];
+        const T D = precond_diag(degT, sigma);
+        T vr[NC > 0 ? NC : 1];
+        T vdot = 0;
+#pragma unroll
+        for (int t = 0; t < NC; ++t) {
+            if (t < c) {
+                vr[t] = Vt[(int64_t)t * ldv + r];
+                vdot += vr[t] * u1s[t];
+            }
+        }
+        T y1 = ((degT - sigma) * zr - gsum + s_term) * inv_beta + vdot;
+        if (has_prev) {
+            const T zpr = zp[r];
+            y1 -= cprev * D * zpr;
+            // deferred update of iteration k-1: w_{k-1} and x
+            const T v = zpr * inv_oldb;
+            const T w = (v - oldeps * wo2[r] - dlt * wo1[r]) * inv_gamma;
+            wn[r] = w;
+            x[r] += phi * w;
+        }
+        Y[r] = y1;
+        acc[0] += zr * inv_beta * y1;
+        const T yd = y1 / D;
+#pragma unroll
+        for (int t = 0; t < NC; ++t)
+            if (t < c) acc[1 + t] += vr[t] * yd;
+    }
+};
+
+template <typename T, int G, int NC>
+__global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
+    InnerState<T>* st = a.st;
+    if (st->done) return;
+    const int k = st->itn + 1;
+    __shared__ T u1s[NC > 0 ? NC : 1];
+    __shared__ T red[1 + NC];
+    Phase1Epi<T, NC> epi;
+    epi.trim = a.trim;
+    epi.ldv = a.ldv;
+    epi.sigma = a.sigma;
+    epi.c = a.c;
+    epi.Vt = a.Vt;
+    epi.Y = a.Y;
+    epi.x = a.x;
+    epi.zc = ((k - 1) & 1) ? a.z1 : a.z0;
+    epi.zp = (k & 1) ? a.z1 : a.z0;
+    const T beta = st->beta, oldb = st->oldb;
+    epi.inv_beta = T(1) / beta;
+    epi.has_prev = k >= 2;
+    epi.cprev = epi.has_prev ? beta / oldb : T(0);
+    epi.inv_oldb = epi.has_prev ? T(1) / oldb : T(0);
+    epi.s_term = a.sig_n * st->s_cur;
+    const int j = k - 1;                    // iteration whose w/x update is deferred to here
+    epi.wo2 = wbuf(a, j + 1);               // w_{j-2}
+    epi.wo1 = wbuf(a, j + 2);               // w_{j-1}
+    epi.wn = wbuf(a, j);                    // w_j
+    epi.oldeps = st->w_oldeps;
+    epi.dlt = st->w_dlt;
+    epi.inv_gamma = st->w_inv_gamma;
+    epi.phi = st->w_phi;
+    for (int t = threadIdx.x; t < a.c; t += blockDim.x) u1s[t] = st->u1[t];
+    epi.u1s = u1s;
+#pragma unroll
+    for (int t = 0; t < 1 + NC; ++t) epi.acc[t] = T(0);
+    __syncthreads();
+
+    for_each_row_gather<T, G>(a.rs, epi.zc, epi);
+
+    if (block_partials_arrive<T, 1 + NC>(epi.acc, 1 + a.c, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, 1 + a.c, red, a.counter);
+        // alpha_k and the SMW coefficient of phase 2:
+        //   Vh^T D^{-1} y = h1 - (alpha/beta) (g + delta G g),  tv = C^{-1} (that)
+        __shared__ double rhs[kCMax];
+        const T alpha = red[0];
+        const double coef = (double)alpha / (double)beta;
+        const int c = a.c;
+        for (int t = threadIdx.x; t < c; t += blockDim.x) {
+            double gg = 0.0;
+            for (int s = 0; s < c; ++s) gg += a.Gm[t + s * c] * (double)st->g_cur[s];
+            rhs[t] = (double)red[1 + t] - coef * ((double)st->g_cur[t] + (double)a.delta * gg);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < c; t += blockDim.x) {
+            double tv = 0.0;
+            for (int s = 0; s < c; ++s) tv += a.Cinv[t + s * c] * rhs[s];
+            st->tv[t] = (T)tv;
+            st->qv[t] = (T)(coef * (double)a.delta * (double)st->g_cur[t]);
+        }
+        if (threadIdx.x == 0) st->alpha = alpha;
+    }
+}
+
+// ------------------------------------------------------------------ phase 2
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init) {
+    InnerState<T>* st = a.st;
+    if (!init && st->done) return;
+    const int k = init ? 0 : st->itn + 1;
+    const T* zc = ((k - 1) & 1) ? a.z1 : a.z0;
+    T* zn = (k & 1) ? a.z1 : a.z0;
+    const T coef = init ? T(0) : st->alpha / st->beta;
+    __shared__ T qvs[NC > 0 ? NC : 1], tvs[NC > 0 ? NC : 1];
+    __shared__ T red[2 + NC];
+    for (int t = threadIdx.x; t < a.c; t += blockDim.x) {
+        qvs[t] = init ? T(0) : st->qv[t];
+        tvs[t] = st->tv[t];
+    }
+    __syncthreads();
+    T acc[2 + NC];
+#pragma unroll
+    for (int t = 0; t < 2 + NC; ++t) acc[t] = T(0);
+    const int64_t n = a.rs.n;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        if (r == a.trim) {
+            zn[r] = T(0);
+            continue;
+        }
+        const T degT = (T)(a.rs.rp[r + 1] - a.rs.rp[r]);
+        const T D = precond_diag(degT, a.sigma);
+        T vr[NC > 0 ? NC : 1];
+        T q1 = 0, q2 = 0;
+#pragma unroll
+        for (int t = 0; t < NC; ++t) {
+            if (t < a.c) {
+                vr[t] = a.Vt[(int64_t)t * a.ldv + r];
+                q1 += vr[t] * qvs[t];
+                q2 += vr[t] * tvs[t];
+            }
+        }
+        T y = a.Y[r];
+        if (!init) y -= coef * D * zc[r] + q1;
+        const T z = (y - q2) / D;
+        zn[r] = z;
+        acc[0] += y * z;
+        acc[1] += z;
+#pragma unroll
+        for (int t = 0; t < NC; ++t)
+            if (t < a.c) acc[2 + t] += vr[t] * z;
+    }
+    if (block_partials_arrive<T, 2 + NC>(acc, 2 + a.c, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, 2 + a.c, red, a.counter);
+        __shared__ T bnew_s, bold_s;
+        if (threadIdx.x == 0) {
+            const T bb = red[0];
+            const T bnew = bb > T(0) ? sqrt(bb) : T(0);
+            bold_s = st->beta;
+            bnew_s = bnew;
+            int done;
+            if (init) {
+                st->beta1 = bnew;
+                st->beta = bnew;
+                st->oldb = T(0);
+                st->phibar = bnew;
+                st->cs = T(-1);
+                st->sn = T(0);
+                st->dbar = T(0);
+                st->epsln = T(0);
+                st->itn = 0;
+                st->pending = 0;
+                done = !(bnew > T(0));
+            } else {
+                // Givens step of MINRES for column k of the Lanczos tridiagonal matrix
+                const T alpha = st->alpha;
+                const T cs = st->cs, sn = st->sn, dbar = st->dbar;
+                const T oldeps = st->epsln;
+                const T dlt = cs * dbar + sn * alpha;
+                const T gbar = sn * dbar - cs * alpha;
+                const T epsln = sn * bnew;
+                const T dbar2 = -cs * bnew;
+                T gamma = sqrt(gbar * gbar + bnew * bnew);
+                if (!(gamma > T(0))) gamma = T(1e-30);
+                const T cs2 = gbar / gamma, sn2 = bnew / gamma;
+                const T phi = cs2 * st->phibar;
+                const T phibar = sn2 * st->phibar;
+                st->w_oldeps = oldeps;
+                st->w_dlt = dlt;
+                st->w_inv_gamma = T(1) / gamma;
+                st->w_phi = phi;
+                st->cs = cs2;
+                st->sn = sn2;
+                st->dbar = dbar2;
+                st->epsln = epsln;
+                st->phibar = phibar;
+                st->oldb = st->beta;
+                st->beta = bnew;
+                st->itn = k;
+                st->pending = 1;
+                done = (phibar <= a.tau * st->beta1) || (k >= a.max_it) || !(bnew > T(0));
+            }
+            st->s_cur = red[1];
+            st->done = done;
+            a.hs->inner_done = done;
+            a.hs->inner_iters = st->itn;
+            a.hs->inner_relres = st->beta1 > T(0) ? (double)(st->phibar / st->beta1) : 0.0;
+        }
+        __syncthreads();
+        // c-vectors for the next phase 1: g_prev <- g_cur, g_cur <- Vh^T z_{k+1},
+        // u1 = delta (g_cur / beta_{k+1} - (beta_{k+1} / beta_k) g_prev)
+        const T bnew = bnew_s, bold = bold_s;
+        for (int t = threadIdx.x; t < a.c; t += blockDim.x) {
+            const T gp = init ? T(0) : st->g_cur[t];
+            const T gn = red[2 + t];
+            st->g_prev[t] = gp;
+            st->g_cur[t] = gn;
+            if (bnew > T(0))
+                st->u1[t] = a.delta * (gn / bnew - (init ? T(0) : (bnew / bold) * gp));
+            else
+                st->u1[t] = T(0);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ prep: b = rh / ||r||, h1 = Vh^T D^{-1} b
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_prep(InnerArgs<T> a, const double* R, const double* rnorm_dev) {
+    __shared__ T red[NC > 0 ? NC : 1];
+    const double rn = *rnorm_dev;
+    const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+    T acc[NC > 0 ? NC : 1];
+#pragma unroll
+    for (int t = 0; t < (NC > 0 ? NC : 1); ++t) acc[t] = T(0);
+    const int64_t n = a.rs.n;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const T b = (r == a.trim) ? T(0) : (T)(R[r] * inv);
+        a.Y[r] = b;
+        a.x[r] = T(0);
+        a.wb0[r] = T(0);
+        a.wb1[r] = T(0);
+        a.wb2[r] = T(0);
+        if (NC > 0 && r != a.trim) {
+            const T degT = (T)(a.rs.rp[r + 1] - a.rs.rp[r]);
+            const T bd = b / precond_diag(degT, a.sigma);
+#pragma unroll
+            for (int t = 0; t < NC; ++t)
+                if (t < a.c) acc[t] += a.Vt[(int64_t)t * a.ldv + r] * bd;
+        }
+    }
+    const int nv = NC > 0 ? a.c : 0;
+    if (block_partials_arrive<T, (NC > 0 ? NC : 1)>(acc, nv, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, nv, red, a.counter);
+        InnerState<T>* st = a.st;
+        for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+            double tv = 0.0;
+            for (int s = 0; s < nv; ++s) tv += a.Cinv[t + s * nv] * (double)red[s];
+            st->tv[t] = (T)tv;
+            st->qv[t] = T(0);
+        }
+        if (threadIdx.x == 0) {
+            st->done = 0;
+            st->itn = 0;
+            st->pending = 0;
+            st->alpha = T(0);
+            st->beta = T(1);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ finalize: last deferred update, cast to FP64
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_finalize(InnerArgs<T> a, double* Z) {
+    const InnerState<T>* st = a.st;
+    const int j = st->itn;
+    const int pend = st->pending;
+    const T* zj = ((j - 1) & 1) ? a.z1 : a.z0;
+    const T* wo2 = wbuf(a, j + 1);
+    const T* wo1 = wbuf(a, j + 2);
+    const T inv_oldb = pend ? T(1) / st->oldb : T(0);
+    const T oldeps = st->w_oldeps, dlt = st->w_dlt, inv_gamma = st->w_inv_gamma, phi = st->w_phi;
+    const int64_t n = a.rs.n;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        T xv = a.x[r];
+        if (pend && r != a.trim) {
+            const T w = (zj[r] * inv_oldb - oldeps * wo2[r] - dlt * wo1[r]) * inv_gamma;
+            xv += phi * w;
+        }
+        Z[r] = (r == a.trim) ? 0.0 : (double)xv;
+    }
+}
+
+// ------------------------------------------------------------------ operator statistics for a stand-alone apply
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_opstats(InnerArgs<T> a, const T* x) {
+    __shared__ T red[1 + NC];
+    T acc[1 + NC];
+#pragma unroll
+    for (int t = 0; t < 1 + NC; ++t) acc[t] = T(0);
+    const int64_t n = a.rs.n;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        if (r == a.trim) continue;
+        const T xr = x[r];
+        acc[0] += xr;
+#pragma unroll
+        for (int t = 0; t < NC; ++t)
+            if (t < a.c) acc[1 + t] += a.Vt[(int64_t)t * a.ldv + r] * xr;
+    }
+    if (block_partials_arrive<T, 1 + NC>(acc, 1 + a.c, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, 1 + a.c, red, a.counter);
+        InnerState<T>* st = a.st;
+        for (int t = threadIdx.x; t < a.c; t += blockDim.x) {
+            st->g_cur[t] = red[1 + t];
+            st->u1[t] = a.delta * red[1 + t];
+        }
+        if (threadIdx.x == 0) {
+            st->s_cur = red[0];
+            st->beta = T(1);
+            st->oldb = T(0);
+            st->itn = 0;
+            st->done = 0;
+            st->pending = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ Gram matrix Vh^T D^{-1} Vh and C^{-1}
+
+constexpr int kGramTile = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_gram(InnerArgs<T> a, double* G, double* Cinv, double* partial,
+                                                   int pstride) {
+    extern __shared__ double gsm[];     // [c][kGramTile + 1]
+    const int c = a.c;
+    const int ne = c * (c + 1) / 2;
+    const int64_t n = a.rs.n;
+    constexpr int kPer = 2;             // entries per thread (c <= 31 -> ne <= 496 <= 2 * 256)
+    int ea[kPer], eb[kPer];
+    double acc[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        int e = threadIdx.x + q * blockDim.x;
+        acc[q] = 0.0;
+        ea[q] = -1;
+        eb[q] = -1;
+        if (e < ne) {  // unrank e -> (p, s), p <= s, row-major over the upper triangle
+            int p = 0, rem = e;
+            while (rem >= c - p) { rem -= c - p; ++p; }
+            ea[q] = p;
+            eb[q] = p + rem;
+        }
+    }
+    const int ldt = kGramTile + 1;
+    for (int64_t r0 = (int64_t)blockIdx.x * kGramTile; r0 < n; r0 += (int64_t)gridDim.x * kGramTile) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < c * kGramTile; idx += blockDim.x) {
+            const int col = idx / kGramTile, rr = idx % kGramTile;
+            const int64_t r = r0 + rr;
+            double v = 0.0;
+            if (r < n && r != a.trim) {
+                const T degT = (T)(a.rs.rp[r + 1] - a.rs.rp[r]);
+                v = (double)a.Vt[(int64_t)col * a.ldv + r] * rsqrt((double)precond_diag(degT, a.sigma));
+            }
+            gsm[col * ldt + rr] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            if (ea[q] >= 0) {
+                const double* pa = gsm + ea[q] * ldt;
+                const double* pb = gsm + eb[q] * ldt;
+                double s = 0.0;
+                for (int rr = 0; rr < kGramTile; ++rr) s += pa[rr] * pb[rr];
+                acc[q] += s;
+            }
+        }
+    }
+    // per-block partials (one slot per entry), then the last block sums and factors
+    for (int q = 0; q < kPer; ++q) {
+        int e = threadIdx.x + q * blockDim.x;
+        if (e < ne) partial[(size_t)e * pstride + blockIdx.x] = acc[q];
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int last;
+    if (threadIdx.x == 0) last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __shared__ double Gs[kCMax * kCMax];
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (size_t)e * pstride + b);
+        int p = 0, rem = e;
+        while (rem >= c - p) { rem -= c - p; ++p; }
+        Gs[p + (p + rem) * c] = s;
+        Gs[(p + rem) + p * c] = s;
+    }
+    if (threadIdx.x == 0) *a.counter = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // C = delta^{-1} I + G (SPD), Cholesky C = L L^T, then C^{-1} column by column
+        double Lc[kCMax * kCMax];
+        const double dinv = 1.0 / (double)a.delta;
+        for (int p = 0; p < c; ++p)
+            for (int s = 0; s < c; ++s) {
+                G[p + s * c] = Gs[p + s * c];
+                Lc[p + s * c] = 0.0;
+            }
+        for (int s = 0; s < c; ++s) {
+            double d = Gs[s + s * c] + dinv;
+            for (int t = 0; t < s; ++t) d -= Lc[s + t * c] * Lc[s + t * c];
+            d = sqrt(d > 0.0 ? d : 1e-300);
+            Lc[s + s * c] = d;
+            for (int p = s + 1; p < c; ++p) {
+                double v = Gs[p + s * c];
+                for (int t = 0; t < s; ++t) v -= Lc[p + t * c] * Lc[s + t * c];
+                Lc[p + s * c] = v / d;
+            }
+        }
+        for (int col = 0; col < c; ++col) {
+            double y[kCMax];
+            for (int p = 0; p < c; ++p) {
+                double v = (p == col) ? 1.0 : 0.0;
+                for (int t = 0; t < p; ++t) v -= Lc[p + t * c] * y[t];
+                y[p] = v / Lc[p + p * c];
+            }
+            for (int p = c - 1; p >= 0; --p) {
+                double v = y[p];
+                for (int t = p + 1; t < c; ++t) v -= Lc[t + p * c] * y[t];
+                y[p] = v / Lc[p + p * c];
+            }
+            for (int p = 0; p < c; ++p) Cinv[p + col * c] = y[p];
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_copy_vcol(const double* src, T* dst, int64_t n) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        dst[r] = (T)src[r];
+}
+
+// ------------------------------------------------------------------ launchers
+
+#define ISIRA_NC_DISPATCH(c, F) \
+    do {                        \
+        if ((c) == 0) { F(0); } \
+        else if ((c) <= 8) { F(8); } \
+        else if ((c) <= 16) { F(16); } \
+        else { F(32); }         \
+    } while (0)
+
+template <typename T, int G>
+static void phase1_launch_g(const InnerArgs<T>& a, cudaStream_t s) {
+    const int grid = a.rs.grid();
+#define L1(NC) k_phase1<T, G, NC><<<grid, kThreads, 0, s>>>(a)
+    ISIRA_NC_DISPATCH(a.c, L1);
+#undef L1
+}
+
+template <typename T>
+void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s) {
+    switch (lanes) {
+        case 1: phase1_launch_g<T, 1>(a, s); break;
+        case 2: phase1_launch_g<T, 2>(a, s); break;
+        case 4: phase1_launch_g<T, 4>(a, s); break;
+        case 8: phase1_launch_g<T, 8>(a, s); break;
+        case 16: phase1_launch_g<T, 16>(a, s); break;
+        default: phase1_launch_g<T, 32>(a, s); break;
+    }
+}
+
+template <typename T>
+void inner_phase2(const InnerArgs<T>& a, int init, cudaStream_t s) {
+#define L2(NC) k_phase2<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a, init)
+    ISIRA_NC_DISPATCH(a.c, L2);
+#undef L2
+}
+
+template <typename T>
+void inner_prep_launch(const InnerArgs<T>& a, const double* R, const double* rnorm_dev, cudaStream_t s) {
+#define LP(NC) k_prep<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a, R, rnorm_dev)
+    ISIRA_NC_DISPATCH(a.c, LP);
+#undef LP
+}
+
+template <typename T>
+void inner_finalize_to(const InnerArgs<T>& a, double* Z, cudaStream_t s) {
+    k_finalize<T><<<a.ew_blocks, kThreads, 0, s>>>(a, Z);
+}
+
+template <typename T>
+void inner_opstats(const InnerArgs<T>& a, const T* x, cudaStream_t s) {
+#define LS(NC) k_opstats<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a, x)
+    ISIRA_NC_DISPATCH(a.c, LS);
+#undef LS
+}
+
+template <typename T>
+void gram_setup(const InnerArgs<T>& a, double* G_out, double* Cinv_out, double* partial, cudaStream_t s) {
+    if (a.c <= 0) return;
+    const size_t smem = sizeof(double) * (size_t)a.c * (kGramTile + 1);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * kCMax * (kGramTile + 1)));
+        attr_set = true;
+    }
+    k_gram<T><<<a.ew_blocks, kThreads, smem, s>>>(a, G_out, Cinv_out, partial, a.pstride);
+}
+
+template <typename T>
+void copy_vcol(const double* src, T* dst, int64_t n, cudaStream_t s) {
+    k_copy_vcol<T><<<608, kThreads, 0, s>>>(src, dst, n);
+}
+
+#define ISIRA_INSTANTIATE_INNER(T)                                                                        \
+    template void inner_phase1<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
+    template void inner_phase2<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
+    template void inner_prep_launch<T>(const InnerArgs<T>&, const double*, const double*, cudaStream_t); \
+    template void inner_finalize_to<T>(const InnerArgs<T>&, double*, cudaStream_t);                      \
+    template void inner_opstats<T>(const InnerArgs<T>&, const T*, cudaStream_t);                         \
+    template void gram_setup<T>(const InnerArgs<T>&, double*, double*, double*, cudaStream_t);           \
+    template void copy_vcol<T>(const double*, T*, int64_t, cudaStream_t);
+
+}  // namespace isira

@@ -1,0 +1,104 @@
+// internal.h -- host-side interfaces between the translation units of libisira.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace isira {
+
+// ------------------------------------------------------------------ inner solve
+// State of one preconditioned MINRES solve (Paige & Saunders 1975) kept in device
+// memory: the Lanczos/Givens scalars, the c-vectors of the deflation terms, and the
+// iteration counters.  Written only by the last block of a launch.
+template <typename T>
+struct InnerState {
+    T beta;       // beta_k: v_k = z_k / beta_k
+    T oldb;       // beta_{k-1}
+    T alpha;      // alpha_k from phase 1
+    T beta1;      // initial preconditioned residual norm
+    T cs, sn, dbar, epsln, phibar;
+    T w_oldeps, w_dlt, w_inv_gamma, w_phi;   // coefficients of the deferred w/x update
+    T s_cur;                                 // sum(z_k)
+    T g_cur[kCMax], g_prev[kCMax];           // Vh^T z_k, Vh^T z_{k-1}
+    T u1[kCMax];                             // phase-1 coefficient of Vh_r (see inner_impl.cuh)
+    T qv[kCMax];                             // phase-2: (alpha/beta) delta g_cur
+    T tv[kCMax];                             // phase-2: SMW coefficient C^{-1} Vh^T D^{-1} y
+    int itn, done, pending, pad;
+};
+
+// Per-handle, per-precision buffers and parameters of the inner solve.
+template <typename T>
+struct InnerArgs {
+    RowSched rs;
+    int64_t trim;
+    T sigma, sig_n, delta;      // sig_n = sigma / n, or 0 with drop_rank1
+    const T* Vt;                // Vh in precision T, column-major, leading dim ldv
+    int64_t ldv;
+    int c;
+    T* z0; T* z1; T* Y; T* wb0; T* wb1; T* wb2; T* x;
+    T* partial; int pstride;
+    unsigned* counter;
+    InnerState<T>* st;
+    HostStatus* hs;             // device alias of the mapped host status
+    const double* Cinv;         // c-by-c inverse of C = delta^{-1} I + Vh^T D^{-1} Vh
+    const double* Gm;           // c-by-c Vh^T D^{-1} Vh
+    T tau; int max_it;
+    int ew_blocks;              // grid of the row-elementwise kernels
+};
+
+// Launchers (instantiated for float and double in inner_f32.cu / inner_f64.cu).
+template <typename T> void inner_prep_launch(const InnerArgs<T>& a, const double* R, const double* rnorm_dev,
+                                             cudaStream_t s);
+template <typename T> void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s);
+template <typename T> void inner_phase2(const InnerArgs<T>& a, int init, cudaStream_t s);
+template <typename T> void inner_finalize_to(const InnerArgs<T>& a, double* Z, cudaStream_t s);
+template <typename T> void inner_opstats(const InnerArgs<T>& a, const T* x, cudaStream_t s);
+template <typename T> void gram_setup(const InnerArgs<T>& a, double* G_out, double* Cinv_out, double* scratch,
+                                      cudaStream_t s);
+template <typename T> void copy_vcol(const double* src, T* dst, int64_t n, cudaStream_t s);
+
+// ------------------------------------------------------------------ outer loop (FP64)
+struct OuterArgs {
+    RowSched rs;
+    int64_t n, ld;              // leading dimension of U, W, V
+    double* U; double* W; double* V;
+    double* H;                  // kMMax x kMMax, column-major, ld kMMax
+    double* theta; double* S;   // Ritz values, Ritz vectors (ld kMMax)
+    double* R;                  // residual n-vector
+    double* Z;                  // expansion n-vector
+    double* partial; int pstride;
+    unsigned* counter;
+    HostStatus* hs;
+    double* dscratch;           // small device scratch (>= 4 * kMMax doubles)
+    int ew_blocks;
+    int ts_blocks;              // grid of the tall-skinny kernels
+};
+
+void outer_residual(const OuterArgs& a, int k, cudaStream_t s);
+void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, int lds, HostStatus* hs,
+                   cudaStream_t s);
+// Z <- Z - Q(Q^T Z) - mean(Z) twice, then ||Z||, for Q = [U(:,0:k) V(:,0:c)]; Z already holds the
+// FP64 input.  Writes cgs_in / cgs_out to the host status.
+void outer_cgs2(const OuterArgs& a, int k, int c, cudaStream_t s);
+// U(:,k) = Z/||Z||, W(:,k) = L U(:,k), H(0:k, k) = U(:,0:k+1)^T W(:,k) (and the symmetric row).
+void outer_expand(const OuterArgs& a, int k, int lanes, cudaStream_t s);
+// X(:, 0:ncol) <- X(:, 0:kk) S(:, c0:c0+ncol); with vout != NULL also vout = X S(:, 0).
+void outer_rotate(const OuterArgs& a, double* X, int kk, int c0, int ncol, double* vout, cudaStream_t s);
+// H <- diag(theta(c0 : c0 + cnt))
+void outer_set_diag(const OuterArgs& a, int c0, int cnt, cudaStream_t s);
+// Z <- centred SplitMix64 vector, block `blk` of stream `seed`.
+void outer_random(const OuterArgs& a, uint64_t seed, uint64_t blk, cudaStream_t s);
+// out[j] = ||L V(:,j) - lam[j] V(:,j)||_2^2 for j < d (out is device, d doubles).
+void outer_true_residual(const OuterArgs& a, int d, const double* lam_dev, double* out, int lanes,
+                         cudaStream_t s);
+// y = L x (FP64 full Laplacian), used to seed W(:,0).
+void outer_laplacian(const OuterArgs& a, const double* x, double* y, int lanes, cudaStream_t s);
+
+// setup
+struct DegreeInfo { int64_t max_degree, argmax; int64_t n_heavy, n_medium; };
+void setup_degrees(const int64_t* rp, int64_t n, int light_deg, int32_t* heavy, int32_t* medium,
+                   int64_t* scratch, DegreeInfo* out, cudaStream_t s);
+int validate_csr(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int* d_flag, cudaStream_t s);
+
+}  // namespace isira

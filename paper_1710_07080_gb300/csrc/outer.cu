@@ -1,0 +1,647 @@
+// outer.cu -- FP64 kernels of the outer loop of Algorithm 2 and of the setup.
+//
+//   residual      r = W s1 - theta1 U s1, ||r||                     (Algorithm 2 line 7)
+//   sym_eig       all eigenpairs of H_k, one CTA, parallel Jacobi    (line 6)
+//   cgs2          classical Gram-Schmidt, two passes, against [U V 1] (line 18)
+//   expand        U(:,k) = u, W(:,k) = L u, H(:,k) = U^T W(:,k)      (lines 4, 19)
+//   rotate        X <- X S(:, a:b) in place, row tiles in shared memory (lines 13, 22)
+//   true_residual ||L v_j - lambda_j v_j||                           (final check)
+//   setup         degrees, maximum degree and its vertex, row classes (Remark 4.1)
+// The tall-skinny kernels stage a tile of basis rows in shared memory once and use
+// it twice (row-wise update, column-wise dot products), so U and V are read once
+// per Gram-Schmidt pass.
+#include "internal.h"
+
+namespace isira {
+
+// ------------------------------------------------------------------ residual (line 7)
+
+__global__ void __launch_bounds__(kThreads) k_residual(OuterArgs a, int k) {
+    __shared__ double s1[kMMax];
+    __shared__ double red[1];
+    const double th = a.theta[0];
+    for (int t = threadIdx.x; t < k; t += blockDim.x) s1[t] = a.S[t];
+    __syncthreads();
+    double acc[1] = {0.0};
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int t = 0; t < k; ++t) v += (a.W[(int64_t)t * a.ld + r] - th * a.U[(int64_t)t * a.ld + r]) * s1[t];
+        a.R[r] = v;
+        acc[0] += v * v;
+    }
+    if (block_partials_arrive<double, 1>(acc, 1, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, 1, red, a.counter);
+        if (threadIdx.x == 0) {
+            const double rn = sqrt(red[0]);
+            a.dscratch[0] = rn;
+            a.hs->rnorm = rn;
+            a.hs->theta[0] = a.theta[0];
+            a.hs->theta[1] = k > 1 ? a.theta[1] : a.theta[0];
+        }
+    }
+}
+
+void outer_residual(const OuterArgs& a, int k, cudaStream_t s) {
+    k_residual<<<a.ew_blocks, kThreads, 0, s>>>(a, k);
+}
+
+// ------------------------------------------------------------------ symmetric eigensolver (line 6)
+// Parallel cyclic Jacobi with the round-robin ordering: in each of K-1 rounds the
+// K indices (K = k rounded up to even) form K/2 disjoint pairs, whose rotations are
+// applied together (rows, then columns).  The 2x2 symmetric Schur rotation is the
+// one of Golub & Van Loan Sec. 8.5.2.  Ascending order, sign rule: largest-magnitude
+// entry of each eigenvector positive (first index on ties).
+
+constexpr int kEigLd = kMMax + 1;
+
+__global__ void __launch_bounds__(kThreads) k_sym_eig(const double* H, int ldh, int k, double* theta, double* S,
+                                                      int lds, HostStatus* hs) {
+    extern __shared__ double eig_sm[];
+    double* A = eig_sm;                    // [kMMax][kEigLd]
+    double* Q = eig_sm + kMMax * kEigLd;   // [kMMax][kEigLd]
+    __shared__ double cs_[kMMax / 2], sn_[kMMax / 2];
+    __shared__ int pp_[kMMax / 2], qq_[kMMax / 2];
+    __shared__ double offsum[kWarps];
+    __shared__ int perm[kMMax];
+    const int K = k + (k & 1);
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < K * K; idx += blockDim.x) {
+        const int i = idx % K, j = idx / K;
+        A[i + j * kEigLd] = (i < k && j < k) ? 0.5 * (H[i + j * ldh] + H[j + i * ldh]) : 0.0;
+        Q[i + j * kEigLd] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    int sweeps = -1;
+    for (int sw = 0; sw < 60 && K >= 2; ++sw) {
+        double off = 0.0;
+        for (int idx = tid; idx < K * K; idx += blockDim.x) {
+            const int i = idx % K, j = idx / K;
+            if (i != j) off += A[i + j * kEigLd] * A[i + j * kEigLd];
+        }
+        off = warp_sum(off);
+        if ((tid & 31) == 0) offsum[tid >> 5] = off;
+        __syncthreads();
+        double tot = 0.0;
+        for (int w = 0; w < kWarps; ++w) tot += offsum[w];
+        __syncthreads();
+        if (tot == 0.0) { sweeps = sw; break; }
+        for (int rnd = 0; rnd < K - 1; ++rnd) {
+            if (tid < K / 2) {
+                int p, q;
+                if (tid == 0) { p = K - 1; q = rnd; }
+                else { p = (rnd + tid) % (K - 1); q = (rnd - tid + (K - 1)) % (K - 1); }
+                if (p > q) { int t = p; p = q; q = t; }
+                double c = 1.0, s = 0.0;
+                const double apq = A[p + q * kEigLd];
+                if (apq != 0.0) {
+                    const double app = A[p + p * kEigLd], aqq = A[q + q * kEigLd];
+                    const bool negligible = sw > 2 && fabs(app) + 100.0 * fabs(apq) == fabs(app) &&
+                                            fabs(aqq) + 100.0 * fabs(apq) == fabs(aqq);
+                    if (!negligible) {
+                        const double tau = (aqq - app) / (2.0 * apq);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                    }
+                }
+                cs_[tid] = c; sn_[tid] = s; pp_[tid] = p; qq_[tid] = q;
+            }
+            __syncthreads();
+            // rows p, q of A: A <- J^T A
+            for (int idx = tid; idx < (K / 2) * K; idx += blockDim.x) {
+                const int pr = idx / K, col = idx % K;
+                const double c = cs_[pr], s = sn_[pr];
+                if (s == 0.0) continue;
+                const int p = pp_[pr], q = qq_[pr];
+                const double ap = A[p + col * kEigLd], aq = A[q + col * kEigLd];
+                A[p + col * kEigLd] = c * ap - s * aq;
+                A[q + col * kEigLd] = s * ap + c * aq;
+            }
+            __syncthreads();
+            // columns p, q of A and of Q: A <- A J, Q <- Q J
+            for (int idx = tid; idx < (K / 2) * K; idx += blockDim.x) {
+                const int pr = idx / K, row = idx % K;
+                const double c = cs_[pr], s = sn_[pr];
+                const int p = pp_[pr], q = qq_[pr];
+                if (s == 0.0) {
+                    if (row == 0 && A[p + q * kEigLd] != 0.0 && c == 1.0) {
+                        // negligible entry: drop it (both triangles)
+                        A[p + q * kEigLd] = 0.0;
+                        A[q + p * kEigLd] = 0.0;
+                    }
+                    continue;
+                }
+                const double ap = A[row + p * kEigLd], aq = A[row + q * kEigLd];
+                A[row + p * kEigLd] = c * ap - s * aq;
+                A[row + q * kEigLd] = s * ap + c * aq;
+                const double qp = Q[row + p * kEigLd], qq = Q[row + q * kEigLd];
+                Q[row + p * kEigLd] = c * qp - s * qq;
+                Q[row + q * kEigLd] = s * qp + c * qq;
+            }
+            __syncthreads();
+            if (tid < K / 2 && sn_[tid] != 0.0) {
+                const int p = pp_[tid], q = qq_[tid];
+                A[p + q * kEigLd] = 0.0;
+                A[q + p * kEigLd] = 0.0;
+            }
+            __syncthreads();
+        }
+    }
+    if (K < 2) sweeps = 0;
+    if (tid == 0) {
+        // ascending selection order over the k real indices (stable on ties)
+        for (int i = 0; i < k; ++i) perm[i] = i;
+        for (int i = 0; i < k; ++i) {
+            int best = i;
+            for (int j = i + 1; j < k; ++j)
+                if (A[perm[j] + perm[j] * kEigLd] < A[perm[best] + perm[best] * kEigLd]) best = j;
+            const int t = perm[best];
+            for (int j = best; j > i; --j) perm[j] = perm[j - 1];
+            perm[i] = t;
+        }
+        if (hs) hs->eig_sweeps = sweeps;
+    }
+    __syncthreads();
+    if (tid < k) {
+        const int src = perm[tid];
+        theta[tid] = A[src + src * kEigLd];
+        int imax = 0;
+        for (int r = 1; r < k; ++r)
+            if (fabs(Q[r + src * kEigLd]) > fabs(Q[imax + src * kEigLd])) imax = r;
+        const double sg = Q[imax + src * kEigLd] < 0.0 ? -1.0 : 1.0;
+        for (int r = 0; r < k; ++r) S[r + tid * lds] = sg * Q[r + src * kEigLd];
+    }
+}
+
+void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, int lds, HostStatus* hs,
+                   cudaStream_t s) {
+    const int bytes = (int)(sizeof(double) * 2 * kMMax * kEigLd);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        attr = true;
+    }
+    k_sym_eig<<<1, kThreads, bytes, s>>>(H, ldh, k, theta, S, lds, hs);
+}
+
+// ------------------------------------------------------------------ tall-skinny passes (line 18, line 4)
+
+constexpr int kTsRows = 64;              // rows per shared-memory tile
+constexpr int kTsMaxCols = kMMax + kCMax;
+constexpr int kTsColsPerWarp = (kTsMaxCols + kWarps - 1) / kWarps;
+
+// MODE 0: dots only:      out = [Q^T z, 1^T z, z^T z]
+// MODE 1: update + dots:  z <- z - Q h - mu 1, written back; out = [Q^T z, 1^T z]
+// MODE 2: update + norm:  as MODE 1, out = [z^T z]
+// Q = [U(:, 0:k) V(:, 0:c)].  coef = [h (k + c), mu].  The last block turns the sums
+// into the coefficients of the next pass (coef_next) or into the final norm.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_tall_skinny(OuterArgs a, int k, int c, const double* z_in,
+                                                          double* z_out, const double* coef, double* coef_next,
+                                                          double* Hcol, int hcol) {
+    extern __shared__ double tsm[];
+    const int nq = k + c;
+    double* Qs = tsm;                           // [nq][kTsRows]
+    double* zs = tsm + (size_t)nq * kTsRows;    // [kTsRows]
+    double* hs = zs + kTsRows;                  // [nq + 1]
+    __shared__ double red[kTsMaxCols + 2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (MODE != 0)
+        for (int j = tid; j <= nq; j += blockDim.x) hs[j] = coef[j];
+    const int nv = (MODE == 0) ? nq + 2 : (MODE == 1 ? nq + 1 : 1);
+    double acc[kTsColsPerWarp + 2];
+#pragma unroll
+    for (int i = 0; i < kTsColsPerWarp + 2; ++i) acc[i] = 0.0;
+    for (int64_t r0 = (int64_t)blockIdx.x * kTsRows; r0 < a.n; r0 += (int64_t)gridDim.x * kTsRows) {
+        __syncthreads();
+        for (int idx = tid; idx < nq * kTsRows; idx += blockDim.x) {
+            const int j = idx / kTsRows, rr = idx % kTsRows;
+            const int64_t r = r0 + rr;
+            const double* col = j < k ? a.U + (int64_t)j * a.ld : a.V + (int64_t)(j - k) * a.ld;
+            Qs[idx] = r < a.n ? col[r] : 0.0;
+        }
+        for (int rr = tid; rr < kTsRows; rr += blockDim.x) {
+            const int64_t r = r0 + rr;
+            zs[rr] = r < a.n ? z_in[r] : 0.0;
+        }
+        __syncthreads();
+        if (MODE != 0) {
+            // four threads per row split the columns, then combine with shuffles
+            const int rr = tid >> 2, part = tid & 3;
+            double s = 0.0;
+            for (int j = part; j < nq; j += 4) s += Qs[j * kTsRows + rr] * hs[j];
+            s += __shfl_xor_sync(kFull, s, 1);
+            s += __shfl_xor_sync(kFull, s, 2);
+            __syncthreads();
+            if (part == 0) {
+                const int64_t r = r0 + rr;
+                const double zn = (r < a.n) ? zs[rr] - s - hs[nq] : 0.0;
+                zs[rr] = zn;
+                if (r < a.n) z_out[r] = zn;
+            }
+            __syncthreads();
+        }
+        if (MODE == 2) {
+            for (int rr = tid; rr < kTsRows; rr += blockDim.x) acc[0] += zs[rr] * zs[rr];
+        } else {
+#pragma unroll
+            for (int i = 0; i < kTsColsPerWarp; ++i) {
+                const int j = warp + i * kWarps;
+                if (j < nq) {
+                    double s = 0.0;
+                    for (int rr = lane; rr < kTsRows; rr += 32) s += Qs[j * kTsRows + rr] * zs[rr];
+                    acc[i] += s;
+                }
+            }
+            if (warp == 0)
+                for (int rr = lane; rr < kTsRows; rr += 32) acc[kTsColsPerWarp] += zs[rr];
+            if (MODE == 0 && warp == 1)
+                for (int rr = lane; rr < kTsRows; rr += 32) acc[kTsColsPerWarp + 1] += zs[rr] * zs[rr];
+        }
+    }
+    // gather the per-warp column sums into a per-thread vector of nv slots, then reduce
+    __shared__ double bsum[kTsMaxCols + 2];
+    __syncthreads();
+    if (MODE == 2) {
+        double v = block_sum0(acc[0]);
+        if (tid == 0) bsum[0] = v;
+    } else {
+#pragma unroll
+        for (int i = 0; i < kTsColsPerWarp; ++i) {
+            const int j = warp + i * kWarps;
+            double v = warp_sum(acc[i]);
+            if (lane == 0 && j < nq) bsum[j] = v;
+        }
+        double v = warp_sum(acc[kTsColsPerWarp]);
+        if (warp == 0 && lane == 0) bsum[nq] = v;
+        if (MODE == 0) {
+            double w = warp_sum(acc[kTsColsPerWarp + 1]);
+            if (warp == 1 && lane == 0) bsum[nq + 1] = w;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < nv; i += blockDim.x) a.partial[(size_t)i * a.pstride + blockIdx.x] = bsum[i];
+    __threadfence();
+    __syncthreads();
+    __shared__ int last;
+    if (tid == 0) last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    last_block_sum(a.partial, a.pstride, gridDim.x, nv, red, a.counter);
+    const double inv_n = 1.0 / (double)a.n;
+    if (MODE == 0 && Hcol != nullptr) {
+        // H(0:nq, hcol) and the symmetric row from the dots U^T w
+        for (int j = tid; j < nq; j += blockDim.x) {
+            Hcol[j + (int64_t)hcol * kMMax] = red[j];
+            Hcol[hcol + (int64_t)j * kMMax] = red[j];
+        }
+        return;
+    }
+    if (MODE == 0 || MODE == 1) {
+        for (int j = tid; j < nq; j += blockDim.x) coef_next[j] = red[j];
+        if (tid == 0) {
+            coef_next[nq] = red[nq] * inv_n;
+            if (MODE == 0) {
+                const double zin = sqrt(red[nq + 1]);
+                a.dscratch[1] = zin;
+                a.hs->cgs_in = zin;
+            }
+        }
+    } else if (tid == 0) {
+        const double nz = sqrt(red[0]);
+        a.dscratch[2] = nz;
+        a.hs->cgs_out = nz;
+    }
+}
+
+static void ts_smem_attr() {
+    static bool done = false;
+    if (done) return;
+    const int bytes = (int)(sizeof(double) * ((size_t)kTsMaxCols * kTsRows + kTsRows + kTsMaxCols + 1));
+    cudaFuncSetAttribute(k_tall_skinny<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_tall_skinny<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_tall_skinny<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done = true;
+}
+
+static size_t ts_smem(int nq) { return sizeof(double) * ((size_t)nq * kTsRows + kTsRows + nq + 1); }
+
+void outer_cgs2(const OuterArgs& a, int k, int c, cudaStream_t s) {
+    ts_smem_attr();
+    const int nq = k + c;
+    double* cA = a.dscratch + 8;                 // coefficients of pass B
+    double* cB = a.dscratch + 8 + kTsMaxCols + 1; // coefficients of pass C
+    k_tall_skinny<0><<<a.ts_blocks, kThreads, ts_smem(nq), s>>>(a, k, c, a.Z, nullptr, nullptr, cA, nullptr, 0);
+    k_tall_skinny<1><<<a.ts_blocks, kThreads, ts_smem(nq), s>>>(a, k, c, a.Z, a.Z, cA, cB, nullptr, 0);
+    k_tall_skinny<2><<<a.ts_blocks, kThreads, ts_smem(nq), s>>>(a, k, c, a.Z, a.Z, cB, nullptr, nullptr, 0);
+}
+
+// ------------------------------------------------------------------ expand (lines 4 and 19)
+
+struct ExpandEpi {
+    const double* Z; double* u; double* w; double inv;
+    __device__ __forceinline__ void operator()(int64_t r, int64_t deg, double gsum) {
+        const double ur = Z[r] * inv;
+        u[r] = ur;
+        w[r] = (double)deg * ur - gsum * inv;
+    }
+};
+
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_expand(OuterArgs a, int k) {
+    ExpandEpi e;
+    e.Z = a.Z;
+    e.u = a.U + (int64_t)k * a.ld;
+    e.w = a.W + (int64_t)k * a.ld;
+    const double nz = a.dscratch[2];
+    e.inv = nz > 0.0 ? 1.0 / nz : 0.0;
+    for_each_row_gather<double, G>(a.rs, a.Z, e);
+}
+
+struct LapEpi {
+    const double* x; double* y;
+    __device__ __forceinline__ void operator()(int64_t r, int64_t deg, double gsum) {
+        y[r] = (double)deg * x[r] - gsum;
+    }
+};
+
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_laplacian(RowSched rs, const double* x, double* y) {
+    LapEpi e{x, y};
+    for_each_row_gather<double, G>(rs, x, e);
+}
+
+#define ISIRA_LANES_DISPATCH(lanes, F) \
+    do {                               \
+        switch (lanes) {               \
+            case 1: F(1); break;       \
+            case 2: F(2); break;       \
+            case 4: F(4); break;       \
+            case 8: F(8); break;       \
+            case 16: F(16); break;     \
+            default: F(32); break;     \
+        }                              \
+    } while (0)
+
+void outer_expand(const OuterArgs& a, int k, int lanes, cudaStream_t s) {
+    ts_smem_attr();
+#define LE(G) k_expand<G><<<a.rs.grid(), kThreads, 0, s>>>(a, k)
+    ISIRA_LANES_DISPATCH(lanes, LE);
+#undef LE
+    // H(0:k+1, k) = U(:, 0:k+1)^T W(:, k)
+    k_tall_skinny<0><<<a.ts_blocks, kThreads, ts_smem(k + 1), s>>>(a, k + 1, 0, a.W + (int64_t)k * a.ld, nullptr,
+                                                                   nullptr, nullptr, a.H, k);
+}
+
+void outer_laplacian(const OuterArgs& a, const double* x, double* y, int lanes, cudaStream_t s) {
+#define LL(G) k_laplacian<G><<<a.rs.grid(), kThreads, 0, s>>>(a.rs, x, y)
+    ISIRA_LANES_DISPATCH(lanes, LL);
+#undef LL
+}
+
+// ------------------------------------------------------------------ rotate (restart, purge)
+
+constexpr int kRotRows = 64;
+
+__global__ void __launch_bounds__(kThreads) k_rotate(OuterArgs a, double* X, int kk, int c0, int ncol, double* vout) {
+    extern __shared__ double rsm[];
+    double* Xs = rsm;                           // [kk][kRotRows]
+    double* Ss = rsm + (size_t)kk * kRotRows;   // [kk][ncol + 1]: S(:, c0..c0+ncol-1) then S(:, 0)
+    const int tid = threadIdx.x;
+    const int nsc = ncol + 1;
+    for (int idx = tid; idx < kk * nsc; idx += blockDim.x) {
+        const int i = idx % kk, b = idx / kk;
+        const int scol = b < ncol ? c0 + b : 0;
+        Ss[i + b * kk] = a.S[i + scol * kMMax];
+    }
+    const int nout = ncol + (vout ? 1 : 0);
+    for (int64_t r0 = (int64_t)blockIdx.x * kRotRows; r0 < a.n; r0 += (int64_t)gridDim.x * kRotRows) {
+        __syncthreads();
+        for (int idx = tid; idx < kk * kRotRows; idx += blockDim.x) {
+            const int j = idx / kRotRows, rr = idx % kRotRows;
+            const int64_t r = r0 + rr;
+            Xs[idx] = r < a.n ? X[(int64_t)j * a.ld + r] : 0.0;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < nout * kRotRows; idx += blockDim.x) {
+            const int b = idx / kRotRows, rr = idx % kRotRows;
+            const int64_t r = r0 + rr;
+            if (r >= a.n) continue;
+            const double* sc = Ss + (size_t)b * kk;
+            double v = 0.0;
+            for (int i = 0; i < kk; ++i) v += Xs[i * kRotRows + rr] * sc[i];
+            if (b < ncol) X[(int64_t)b * a.ld + r] = v;
+            else vout[r] = v;
+        }
+    }
+}
+
+void outer_rotate(const OuterArgs& a, double* X, int kk, int c0, int ncol, double* vout, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * ((size_t)kMMax * kRotRows + (size_t)kMMax * (kMMax + 1))));
+        attr = true;
+    }
+    const size_t smem = sizeof(double) * ((size_t)kk * kRotRows + (size_t)kk * (ncol + 1));
+    k_rotate<<<a.ts_blocks, kThreads, smem, s>>>(a, X, kk, c0, ncol, vout);
+}
+
+__global__ void k_set_diag(double* H, const double* theta, int c0, int cnt) {
+    for (int idx = threadIdx.x; idx < kMMax * kMMax; idx += blockDim.x) {
+        const int i = idx % kMMax, j = idx / kMMax;
+        H[idx] = (i == j && i < cnt) ? theta[c0 + i] : 0.0;
+    }
+}
+
+void outer_set_diag(const OuterArgs& a, int c0, int cnt, cudaStream_t s) {
+    k_set_diag<<<1, kThreads, 0, s>>>(a.H, a.theta, c0, cnt);
+}
+
+__global__ void k_random(double* Z, int64_t n, uint64_t seed, uint64_t blk) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        Z[r] = 2.0 * uniform_at(seed, blk * (uint64_t)n + (uint64_t)r) - 1.0;
+}
+
+void outer_random(const OuterArgs& a, uint64_t seed, uint64_t blk, cudaStream_t s) {
+    k_random<<<a.ew_blocks, kThreads, 0, s>>>(a.Z, a.n, seed, blk);
+}
+
+// ------------------------------------------------------------------ true residual
+
+struct TrueResEpi {
+    const double* v; double lam; double acc[1];
+    __device__ __forceinline__ void operator()(int64_t r, int64_t deg, double gsum) {
+        const double d = (double)deg * v[r] - gsum - lam * v[r];
+        acc[0] += d * d;
+    }
+};
+
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_true_residual(OuterArgs a, const double* v, const double* lam_dev,
+                                                            int j, double* out) {
+    __shared__ double red[1];
+    TrueResEpi e;
+    e.v = v;
+    e.lam = lam_dev[j];
+    e.acc[0] = 0.0;
+    for_each_row_gather<double, G>(a.rs, v, e);
+    if (block_partials_arrive<double, 1>(e.acc, 1, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, 1, red, a.counter);
+        if (threadIdx.x == 0) out[j] = red[0];
+    }
+}
+
+void outer_true_residual(const OuterArgs& a, int d, const double* lam_dev, double* out, int lanes, cudaStream_t s) {
+    for (int j = 0; j < d; ++j) {
+        const double* v = a.V + (int64_t)j * a.ld;
+#define LT(G) k_true_residual<G><<<a.rs.grid(), kThreads, 0, s>>>(a, v, lam_dev, j, out)
+        ISIRA_LANES_DISPATCH(lanes, LT);
+#undef LT
+    }
+}
+
+// ------------------------------------------------------------------ setup (Remark 4.1)
+
+constexpr int kSetupBlocks = 1024;
+
+// per block: max degree + smallest argmax over its row chunk, and row-class counts
+__global__ void __launch_bounds__(kThreads) k_deg_count(const int64_t* rp, int64_t n, int64_t chunk, int light_deg,
+                                                        int64_t* sc) {
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = beg + chunk < n ? beg + chunk : n;
+    int64_t best = -1, barg = 0, nh = 0, nm = 0;
+    for (int64_t r = beg + threadIdx.x; r < end; r += blockDim.x) {
+        const int64_t d = rp[r + 1] - rp[r];
+        if (d > best) { best = d; barg = r; }
+        if (d > kHeavyDeg) ++nh;
+        else if (d > light_deg) ++nm;
+    }
+    __shared__ int64_t sb[kThreads], sa[kThreads], sh[kThreads], sm[kThreads];
+    sb[threadIdx.x] = best; sa[threadIdx.x] = barg; sh[threadIdx.x] = nh; sm[threadIdx.x] = nm;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const int q = threadIdx.x + o;
+            if (sb[q] > sb[threadIdx.x] || (sb[q] == sb[threadIdx.x] && sa[q] < sa[threadIdx.x])) {
+                sb[threadIdx.x] = sb[q];
+                sa[threadIdx.x] = sa[q];
+            }
+            sh[threadIdx.x] += sh[q];
+            sm[threadIdx.x] += sm[q];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sc[blockIdx.x] = sb[0];
+        sc[kSetupBlocks + blockIdx.x] = sa[0];
+        sc[2 * kSetupBlocks + blockIdx.x] = sh[0];
+        sc[3 * kSetupBlocks + blockIdx.x] = sm[0];
+    }
+}
+
+// one block: totals, max/argmax, exclusive prefix offsets of the row classes
+__global__ void k_deg_scan(int64_t* sc, int nb) {
+    if (threadIdx.x != 0) return;
+    int64_t best = -1, barg = 0, oh = 0, om = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t d = sc[b], r = sc[kSetupBlocks + b];
+        if (d > best || (d == best && r < barg)) { best = d; barg = r; }
+        const int64_t h = sc[2 * kSetupBlocks + b], m = sc[3 * kSetupBlocks + b];
+        sc[2 * kSetupBlocks + b] = oh;
+        sc[3 * kSetupBlocks + b] = om;
+        oh += h;
+        om += m;
+    }
+    sc[4 * kSetupBlocks + 0] = best;
+    sc[4 * kSetupBlocks + 1] = barg;
+    sc[4 * kSetupBlocks + 2] = oh;
+    sc[4 * kSetupBlocks + 3] = om;
+}
+
+// ordered compaction: each block walks its chunk in tiles of blockDim rows
+__global__ void __launch_bounds__(kThreads) k_deg_fill(const int64_t* rp, int64_t n, int64_t chunk, int light_deg,
+                                                       const int64_t* sc, int32_t* heavy, int32_t* medium) {
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = beg + chunk < n ? beg + chunk : n;
+    int64_t oh = sc[2 * kSetupBlocks + blockIdx.x], om = sc[3 * kSetupBlocks + blockIdx.x];
+    __shared__ int wh[kWarps], wm[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t t0 = beg; t0 < end; t0 += blockDim.x) {
+        const int64_t r = t0 + threadIdx.x;
+        int64_t d = 0;
+        if (r < end) d = rp[r + 1] - rp[r];
+        const bool ih = r < end && d > kHeavyDeg;
+        const bool im = r < end && d > light_deg && d <= kHeavyDeg;
+        const unsigned bh = __ballot_sync(kFull, ih), bm = __ballot_sync(kFull, im);
+        if (lane == 0) { wh[warp] = __popc(bh); wm[warp] = __popc(bm); }
+        __syncthreads();
+        int ph = 0, pm = 0, th = 0, tm = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            if (w < warp) { ph += wh[w]; pm += wm[w]; }
+            th += wh[w];
+            tm += wm[w];
+        }
+        const unsigned lower = (1u << lane) - 1u;
+        if (ih) heavy[oh + ph + __popc(bh & lower)] = (int32_t)r;
+        if (im) medium[om + pm + __popc(bm & lower)] = (int32_t)r;
+        oh += th;
+        om += tm;
+        __syncthreads();
+    }
+}
+
+void setup_degrees(const int64_t* rp, int64_t n, int light_deg, int32_t* heavy, int32_t* medium, int64_t* scratch,
+                   DegreeInfo* out, cudaStream_t s) {
+    const int64_t chunk = (n + kSetupBlocks - 1) / kSetupBlocks;
+    k_deg_count<<<kSetupBlocks, kThreads, 0, s>>>(rp, n, chunk, light_deg, scratch);
+    k_deg_scan<<<1, 32, 0, s>>>(scratch, kSetupBlocks);
+    k_deg_fill<<<kSetupBlocks, kThreads, 0, s>>>(rp, n, chunk, light_deg, scratch, heavy, medium);
+    int64_t tot[4];
+    cudaMemcpyAsync(tot, scratch + 4 * kSetupBlocks, sizeof(tot), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    out->max_degree = tot[0];
+    out->argmax = tot[1];
+    out->n_heavy = tot[2];
+    out->n_medium = tot[3];
+}
+
+// flag bits: 1 row_ptr not monotone / bad ends, 2 column out of range, 4 self loop,
+// 8 columns not strictly increasing (duplicates), 16 asymmetric pattern
+__global__ void __launch_bounds__(kThreads) k_validate(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz,
+                                                       int* flag) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rp[r], e = rp[r + 1];
+        if (b > e || b < 0 || e > nnz || (r == 0 && b != 0) || (r == n - 1 && e != nnz)) {
+            atomicOr(flag, 1);
+            continue;
+        }
+        for (int64_t q = b; q < e; ++q) {
+            const int64_t col = ci[q];
+            if (col < 0 || col >= n) { atomicOr(flag, 2); continue; }
+            if (col == r) atomicOr(flag, 4);
+            if (q > b && ci[q - 1] >= col) atomicOr(flag, 8);
+            // symmetric: r must appear in row col (binary search, rows are sorted)
+            int64_t lo = rp[col], hi = rp[col + 1] - 1;
+            bool found = false;
+            while (lo <= hi && lo >= 0 && hi < nnz) {
+                const int64_t mid = (lo + hi) >> 1;
+                const int64_t v = ci[mid];
+                if (v == r) { found = true; break; }
+                if (v < r) lo = mid + 1; else hi = mid - 1;
+            }
+            if (!found) atomicOr(flag, 16);
+        }
+    }
+}
+
+int validate_csr(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int* d_flag, cudaStream_t s) {
+    cudaMemsetAsync(d_flag, 0, sizeof(int), s);
+    k_validate<<<1216, kThreads, 0, s>>>(rp, ci, n, nnz, d_flag);
+    int h = 0;
+    cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    return h;
+}
+
+}  // namespace isira

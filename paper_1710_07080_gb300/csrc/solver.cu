@@ -1,0 +1,703 @@
+// solver.cu -- host driver of Algorithm 2 and the C ABI declared in include/isira.h.
+//
+// The outer loop runs on the host, one synchronisation per outer step (to read
+// ||r|| and the Ritz values written by the device into mapped pinned memory) and
+// one after each orthogonalisation (breakdown test).  Everything that touches an
+// n-vector runs in the kernels of inner_*.cu and outer.cu.  The inner MINRES solve
+// is launched in chunks of iterations; its kernels return at once after the
+// device-side stopping test has fired, so a chunk may end with a few empty launches.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/isira.h"
+#include "internal.h"
+
+using namespace isira;
+
+namespace {
+
+struct CudaError {
+    cudaError_t e;
+};
+
+inline void ck(cudaError_t e) {
+    if (e != cudaSuccess) throw CudaError{e};
+}
+
+struct StatusError {
+    isira_status s;
+};
+
+template <typename T>
+struct InnerBuffers {
+    T* base = nullptr;
+    InnerState<T>* st = nullptr;
+};
+
+}  // namespace
+
+struct isira_handle_s {
+    int64_t n = 0, nnz = 0, ld = 0;
+    const int64_t* rp = nullptr;
+    const int32_t* ci = nullptr;
+    cudaStream_t stream = nullptr;
+    isira_opts opts{};
+    int nsm = 0;
+    // setup (Remark 4.1)
+    int64_t max_degree = 0, trim = 0;
+    double delta = 0.0, normL = 0.0;
+    int32_t* heavy = nullptr;
+    int32_t* medium = nullptr;
+    int n_heavy = 0, n_medium = 0;
+    RowSched rs{};
+    int lanes = 8;
+    int ew_blocks = 0, ts_blocks = 0;
+    // FP64 outer buffers
+    int m_alloc = 0, d_alloc = 0;
+    double* U = nullptr;
+    double* W = nullptr;
+    double* V = nullptr;
+    double* H = nullptr;
+    double* theta = nullptr;
+    double* S = nullptr;
+    double* R = nullptr;
+    double* Z = nullptr;
+    double* dscratch = nullptr;
+    double* partial = nullptr;
+    size_t partial_elems = 0;
+    unsigned* counter = nullptr;
+    double* Gm = nullptr;
+    double* Cinv = nullptr;
+    double* lam_dev = nullptr;
+    double* tres_dev = nullptr;
+    HostStatus* hs = nullptr;
+    HostStatus* hs_dev = nullptr;
+    // inner buffers (one precision per handle, plus FP64 for component calls)
+    InnerBuffers<float> fb;
+    InnerBuffers<double> db;
+    float* Vt_f = nullptr;
+    // results
+    std::vector<double> lam;
+    int n_locked = 0;
+    bool solved = false;
+    isira_stats stats{};
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev;
+};
+
+namespace {
+
+template <typename T>
+void alloc_inner(isira_handle h, InnerBuffers<T>& b) {
+    if (b.base) return;
+    ck(cudaMalloc(&b.base, sizeof(T) * (size_t)h->ld * 7));
+    ck(cudaMalloc(&b.st, sizeof(InnerState<T>)));
+    ck(cudaMemsetAsync(b.base, 0, sizeof(T) * (size_t)h->ld * 7, h->stream));
+    ck(cudaMemsetAsync(b.st, 0, sizeof(InnerState<T>), h->stream));
+}
+
+template <typename T>
+InnerArgs<T> make_args(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* Vt, int64_t ldv, double tau,
+                       int max_it) {
+    InnerArgs<T> a{};
+    a.rs = h->rs;
+    a.trim = h->trim;
+    a.sigma = (T)sigma;
+    a.sig_n = h->opts.drop_rank1 ? T(0) : (T)(sigma / (double)h->n);
+    a.delta = (T)h->delta;
+    a.Vt = Vt;
+    a.ldv = ldv;
+    a.c = c;
+    T* v = b.base;
+    const int64_t ld = h->ld;
+    a.z0 = v; a.z1 = v + ld; a.Y = v + 2 * ld; a.wb0 = v + 3 * ld; a.wb1 = v + 4 * ld; a.wb2 = v + 5 * ld;
+    a.x = v + 6 * ld;
+    a.partial = reinterpret_cast<T*>(h->partial);
+    a.pstride = (int)(h->partial_elems / 512);
+    a.counter = h->counter;
+    a.st = b.st;
+    a.hs = h->hs_dev;
+    a.Cinv = h->Cinv;
+    a.Gm = h->Gm;
+    a.tau = (T)tau;
+    a.max_it = max_it;
+    a.ew_blocks = h->ew_blocks;
+    return a;
+}
+
+OuterArgs make_outer(isira_handle h) {
+    OuterArgs a{};
+    a.rs = h->rs;
+    a.n = h->n;
+    a.ld = h->ld;
+    a.U = h->U; a.W = h->W; a.V = h->V;
+    a.H = h->H; a.theta = h->theta; a.S = h->S;
+    a.R = h->R; a.Z = h->Z;
+    a.partial = h->partial;
+    a.pstride = (int)(h->partial_elems / 512);
+    a.counter = h->counter;
+    a.hs = h->hs_dev;
+    a.dscratch = h->dscratch;
+    a.ew_blocks = h->ew_blocks;
+    a.ts_blocks = h->ts_blocks;
+    return a;
+}
+
+void sync(isira_handle h) {
+    ck(cudaStreamSynchronize(h->stream));
+    ck(cudaGetLastError());
+}
+
+volatile HostStatus* hst(isira_handle h) { return h->hs; }
+
+// One inner solve on R (right-hand side) into Z (FP64, back-mapped).  Returns iterations.
+template <typename T>
+int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* Vt, int64_t ldv, double tau,
+              int max_it, bool gram_dirty, const double* R, const double* rnorm_dev) {
+    InnerArgs<T> a = make_args<T>(h, b, sigma, c, Vt, ldv, tau, max_it);
+    cudaStream_t s = h->stream;
+    if (gram_dirty && c > 0) gram_setup<T>(a, h->Gm, h->Cinv, h->partial, s);
+    inner_prep_launch<T>(a, R, rnorm_dev, s);
+    inner_phase2<T>(a, 1, s);
+    const int chunk = h->opts.inner_chunk > 0 ? h->opts.inner_chunk : 16;
+    int launched = 0;
+    while (true) {
+        const bool prof = h->profiling != 0;
+        for (int i = 0; i < chunk; ++i) {
+            if (prof) ck(cudaEventRecord(h->ev[2 * i], s));
+            inner_phase1<T>(a, h->lanes, s);
+            if (prof) ck(cudaEventRecord(h->ev[2 * i + 1], s));
+            inner_phase2<T>(a, 0, s);
+        }
+        h->stats.spmv_launches += chunk;
+        sync(h);
+        const int itn = hst(h)->inner_iters;
+        if (prof) {
+            for (int i = 0; i < chunk; ++i) {
+                if (launched + i + 1 > itn) break;   // launches after the stop returned at once
+                float ms = 0.f;
+                ck(cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]));
+                h->stats.inner_phase1_ms += ms;
+                h->stats.inner_phase1_timed += 1;
+            }
+        }
+        launched += chunk;
+        if (hst(h)->inner_done) break;
+        if (launched > max_it + 2 * chunk) break;   // defensive: the device test caps at max_it
+    }
+    inner_finalize_to<T>(a, h->Z, s);
+    h->stats.inner_solves += 1;
+    const int its = hst(h)->inner_iters;
+    h->stats.inner_iters += its;
+    return its;
+}
+
+void ensure_outer(isira_handle h, int m, int d) {
+    const size_t ld = (size_t)h->ld;
+    if (m > h->m_alloc) {
+        if (h->U) cudaFree(h->U);
+        if (h->W) cudaFree(h->W);
+        h->U = h->W = nullptr;
+        ck(cudaMalloc(&h->U, sizeof(double) * ld * m));
+        ck(cudaMalloc(&h->W, sizeof(double) * ld * m));
+        h->m_alloc = m;
+    }
+    if (d > h->d_alloc) {
+        if (h->V) cudaFree(h->V);
+        if (h->Vt_f) cudaFree(h->Vt_f);
+        h->V = nullptr;
+        h->Vt_f = nullptr;
+        ck(cudaMalloc(&h->V, sizeof(double) * ld * d));
+        if (h->opts.precision == ISIRA_MIXED) ck(cudaMalloc(&h->Vt_f, sizeof(float) * ld * d));
+        h->d_alloc = d;
+    }
+}
+
+// Orthonormalise Z against [U(:,0:k) V(:,0:c) 1] and append it as column k (with W, H).
+// Replaces Z by random vectors while the orthogonalisation breaks down.
+bool expand_basis(isira_handle h, int k, int c) {
+    OuterArgs oa = make_outer(h);
+    cudaStream_t s = h->stream;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        outer_cgs2(oa, k, c, s);
+        sync(h);
+        const double zin = hst(h)->cgs_in, zout = hst(h)->cgs_out;
+        if (zout > 1e-10 * zin && zout > 0.0 && std::isfinite(zout)) {
+            outer_expand(oa, k, h->lanes, s);
+            return true;
+        }
+        h->stats.breakdowns += 1;
+        outer_random(oa, h->opts.seed, (uint64_t)(1 + h->stats.breakdowns), s);
+    }
+    return false;
+}
+
+void choose_lanes(isira_handle h) {
+    if (h->opts.spmv_lanes > 0) {
+        int l = h->opts.spmv_lanes;
+        h->lanes = (l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32) ? l : 8;
+        return;
+    }
+    const double mean = (double)h->nnz / (double)h->n;
+    int heur = mean <= 3.0 ? 1 : (mean <= 6.0 ? 2 : (mean <= 12.0 ? 4 : 8));
+    h->lanes = heur;
+    if (h->n < 200000) return;
+    // time the phase-1 kernel of the handle's precision for every lane count
+    cudaStream_t s = h->stream;
+    cudaEvent_t e0, e1;
+    ck(cudaEventCreate(&e0));
+    ck(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_l = heur;
+    for (int l : {1, 2, 4, 8, 16, 32}) {
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (h->opts.precision == ISIRA_MIXED) {
+                InnerArgs<float> a = make_args<float>(h, h->fb, 0.0, 0, nullptr, h->ld, 1e-3, 1);
+                inner_opstats<float>(a, a.z0, s);
+                ck(cudaEventRecord(e0, s));
+                inner_phase1<float>(a, l, s);
+                ck(cudaEventRecord(e1, s));
+            } else {
+                InnerArgs<double> a = make_args<double>(h, h->db, 0.0, 0, nullptr, h->ld, 1e-3, 1);
+                inner_opstats<double>(a, a.z0, s);
+                ck(cudaEventRecord(e0, s));
+                inner_phase1<double>(a, l, s);
+                ck(cudaEventRecord(e1, s));
+            }
+            sync(h);
+            float ms = 0.f;
+            ck(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) tot += ms;
+        }
+        if (tot < best) {
+            best = tot;
+            best_l = l;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->lanes = best_l;
+}
+
+void free_handle(isira_handle h) {
+    if (!h) return;
+    void* ptrs[] = {h->heavy, h->medium, h->U, h->W, h->V, h->H, h->theta, h->S, h->R, h->Z, h->dscratch,
+                    h->partial, h->counter, h->Gm, h->Cinv, h->lam_dev, h->tres_dev, h->fb.base, h->fb.st,
+                    h->db.base, h->db.st, h->Vt_f};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->hs) cudaFreeHost(h->hs);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    delete h;
+}
+
+isira_status map_cuda(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return ISIRA_ERR_OOM;
+    return ISIRA_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+void isira_default_opts(isira_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = ISIRA_MIXED;
+    o->m = 0;
+    o->q = 0;
+    o->tau_inner = 1e-3;
+    o->max_inner = 5000;
+    o->max_outer = 20000;
+    o->trim_index = -1;
+    o->delta = 0.0;
+    o->sigma_omega = 0.1;
+    o->drop_rank1 = 0;
+    o->validate = 0;
+    o->seed = 1;
+    o->spmv_lanes = 0;
+    o->inner_chunk = 16;
+}
+
+const char* isira_error_string(isira_status s) {
+    switch (s) {
+        case ISIRA_OK: return "ok";
+        case ISIRA_ERR_INVALID_ARG: return "invalid argument";
+        case ISIRA_ERR_BAD_GRAPH: return "malformed CSR graph";
+        case ISIRA_ERR_NOT_CONNECTED: return "graph is not connected (second zero eigenvalue)";
+        case ISIRA_ERR_NO_CONVERGENCE: return "outer iteration limit reached before all eigenpairs converged";
+        case ISIRA_ERR_CUDA: return "CUDA runtime error";
+        case ISIRA_ERR_OOM: return "out of memory";
+        case ISIRA_ERR_NOT_SOLVED: return "no successful solve on this handle";
+    }
+    return "unknown status";
+}
+
+isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64_t* d_row_ptr,
+                          const int32_t* d_col_idx, const isira_opts* opts, void* stream) {
+    if (!out) return ISIRA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 3 || nnz < 2 || nnz > ((int64_t)1 << 40) || !d_row_ptr || !d_col_idx || n > INT32_MAX)
+        return ISIRA_ERR_INVALID_ARG;
+    isira_handle h = new (std::nothrow) isira_handle_s();
+    if (!h) return ISIRA_ERR_OOM;
+    try {
+        h->n = n;
+        h->nnz = nnz;
+        h->ld = (n + 31) / 32 * 32;
+        h->rp = d_row_ptr;
+        h->ci = d_col_idx;
+        h->stream = (cudaStream_t)stream;
+        if (opts) h->opts = *opts; else isira_default_opts(&h->opts);
+        if (h->opts.precision != ISIRA_FP64 && h->opts.precision != ISIRA_MIXED) throw StatusError{ISIRA_ERR_INVALID_ARG};
+        int dev = 0;
+        ck(cudaGetDevice(&dev));
+        ck(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+        cudaStream_t s = h->stream;
+        if (h->opts.validate) {
+            int* flag = nullptr;
+            ck(cudaMalloc(&flag, sizeof(int)));
+            int f = validate_csr(d_row_ptr, d_col_idx, n, nnz, flag, s);
+            cudaFree(flag);
+            if (f) throw StatusError{ISIRA_ERR_BAD_GRAPH};
+        }
+        // Remark 4.1: degrees, maximum degree, trimmed index, delta; row classes of the scheduler
+        const int light_deg = 64;
+        ck(cudaMalloc(&h->heavy, sizeof(int32_t) * (size_t)n));
+        ck(cudaMalloc(&h->medium, sizeof(int32_t) * (size_t)n));
+        int64_t* scratch = nullptr;
+        ck(cudaMalloc(&scratch, sizeof(int64_t) * 5 * 1024));
+        DegreeInfo di{};
+        setup_degrees(d_row_ptr, n, light_deg, h->heavy, h->medium, scratch, &di, s);
+        cudaFree(scratch);
+        ck(cudaGetLastError());
+        h->max_degree = di.max_degree;
+        if (di.max_degree < 1) throw StatusError{ISIRA_ERR_BAD_GRAPH};
+        h->trim = (h->opts.trim_index >= 0 && h->opts.trim_index < n) ? h->opts.trim_index : di.argmax;
+        h->delta = h->opts.delta > 0.0 ? h->opts.delta : 2.0 * (double)di.max_degree;
+        h->normL = 2.0 * (double)di.max_degree;
+        h->n_heavy = (int)di.n_heavy;
+        h->n_medium = (int)di.n_medium;
+        RowSched& rs = h->rs;
+        rs.rp = d_row_ptr;
+        rs.ci = d_col_idx;
+        rs.n = n;
+        rs.heavy = h->heavy;
+        rs.medium = h->medium;
+        rs.n_heavy = h->n_heavy;
+        rs.n_medium = h->n_medium;
+        rs.light_deg = light_deg;
+        const int64_t ntiles = (n + 31) / 32;
+        rs.medium_blocks = h->n_medium > 0 ? (int)std::min<int64_t>((h->n_medium + 4 * kWarps - 1) / (4 * kWarps),
+                                                                      (int64_t)h->nsm * 4)
+                                           : 0;
+        rs.light_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + kWarps - 1) / kWarps,
+                                                                      (int64_t)h->nsm * 8));
+        h->ew_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)h->nsm * 4));
+        h->ts_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64, (int64_t)h->nsm * 2));
+        // shared scratch for block partial sums: 512 slots x the largest grid
+        const int64_t maxgrid = std::max<int64_t>({(int64_t)rs.grid(), (int64_t)h->ew_blocks, (int64_t)h->ts_blocks});
+        h->partial_elems = (size_t)512 * (size_t)maxgrid;
+        ck(cudaMalloc(&h->partial, sizeof(double) * h->partial_elems));
+        ck(cudaMalloc(&h->counter, sizeof(unsigned) * 4));
+        ck(cudaMemsetAsync(h->counter, 0, sizeof(unsigned) * 4, s));
+        ck(cudaMalloc(&h->H, sizeof(double) * kMMax * kMMax));
+        ck(cudaMalloc(&h->theta, sizeof(double) * kMMax));
+        ck(cudaMalloc(&h->S, sizeof(double) * kMMax * kMMax));
+        ck(cudaMalloc(&h->R, sizeof(double) * (size_t)h->ld));
+        ck(cudaMalloc(&h->Z, sizeof(double) * (size_t)h->ld));
+        ck(cudaMalloc(&h->dscratch, sizeof(double) * 512));
+        ck(cudaMalloc(&h->Gm, sizeof(double) * kCMax * kCMax));
+        ck(cudaMalloc(&h->Cinv, sizeof(double) * kCMax * kCMax));
+        ck(cudaMalloc(&h->lam_dev, sizeof(double) * kCMax));
+        ck(cudaMalloc(&h->tres_dev, sizeof(double) * kCMax));
+        ck(cudaHostAlloc(&h->hs, sizeof(HostStatus), cudaHostAllocMapped));
+        std::memset(h->hs, 0, sizeof(HostStatus));
+        ck(cudaHostGetDevicePointer((void**)&h->hs_dev, h->hs, 0));
+        if (h->opts.precision == ISIRA_MIXED) alloc_inner(h, h->fb); else alloc_inner(h, h->db);
+        int chunk = h->opts.inner_chunk > 0 ? h->opts.inner_chunk : 16;
+        h->ev.resize(2 * chunk);
+        for (auto& e : h->ev) ck(cudaEventCreate(&e));
+        sync(h);
+        choose_lanes(h);
+        h->stats.n = n;
+        h->stats.nnz = nnz;
+        h->stats.trim_index = h->trim;
+        h->stats.max_degree = h->max_degree;
+        h->stats.delta = h->delta;
+        h->stats.norm_L = h->normL;
+        h->stats.spmv_lanes = h->lanes;
+        h->stats.n_heavy_rows = h->n_heavy;
+        h->stats.n_medium_rows = h->n_medium;
+    } catch (CudaError& e) {
+        isira_status st = map_cuda(e.e);
+        free_handle(h);
+        return st;
+    } catch (StatusError& e) {
+        free_handle(h);
+        return e.s;
+    }
+    *out = h;
+    return ISIRA_OK;
+}
+
+void isira_destroy(isira_handle h) { free_handle(h); }
+
+isira_status isira_set_profiling(isira_handle h, int on) {
+    if (!h) return ISIRA_ERR_INVALID_ARG;
+    h->profiling = on ? 1 : 0;
+    return ISIRA_OK;
+}
+
+isira_status isira_get_stats(isira_handle h, isira_stats* out) {
+    if (!h || !out) return ISIRA_ERR_INVALID_ARG;
+    *out = h->stats;
+    return ISIRA_OK;
+}
+
+isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const double* d_u0) {
+    if (!h) return ISIRA_ERR_INVALID_ARG;
+    if (d < 1 || d > kCMax || d > h->n - 2 || !(tol >= 0.0) || !std::isfinite(sigma)) return ISIRA_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    isira_status status = ISIRA_OK;
+    h->solved = false;
+    try {
+        const isira_opts& o = h->opts;
+        int m = o.m > 0 ? o.m : std::max(20, 2 * d + 10);
+        int q = o.q > 0 ? o.q : std::max(d + 2, m / 2);
+        m = std::min<int64_t>({(int64_t)m, (int64_t)kMMax, h->n - 1});
+        q = std::min(q, m - 1);
+        if (q < d || m < 2) return ISIRA_ERR_INVALID_ARG;
+        const double tau = o.tau_inner > 0.0 ? o.tau_inner : 1e-3;
+        const int max_inner = o.max_inner > 0 ? o.max_inner : 5000;
+        const int max_outer = o.max_outer > 0 ? o.max_outer : 20000;
+        const double omega = o.sigma_omega > 0.0 ? o.sigma_omega : 0.1;
+        ensure_outer(h, m, d);
+        cudaStream_t s = h->stream;
+        // reset counters
+        const isira_stats keep = h->stats;
+        h->stats.n_locked = 0;
+        h->stats.outer_steps = 0;
+        h->stats.restarts = 0;
+        h->stats.breakdowns = 0;
+        h->stats.inner_iters = 0;
+        h->stats.inner_solves = 0;
+        h->stats.spmv_launches = 0;
+        h->stats.inner_phase1_ms = 0.0;
+        h->stats.inner_phase1_timed = 0;
+        (void)keep;
+        h->lam.assign(d, 0.0);
+        OuterArgs oa = make_outer(h);
+        ck(cudaMemsetAsync(h->H, 0, sizeof(double) * kMMax * kMMax, s));
+        // start basis U_{k0}, k0 = 1 (Algorithm 2 REQUIRE): the given vector, or a SplitMix64 one
+        if (d_u0) ck(cudaMemcpyAsync(h->Z, d_u0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+        else outer_random(oa, o.seed, 0, s);
+        if (!expand_basis(h, 0, 0)) throw StatusError{ISIRA_ERR_NO_CONVERGENCE};
+        int k = 1, c = 0;
+        double sig = sigma;
+        bool gram_dirty = true;
+        while (true) {
+            if (h->stats.outer_steps >= max_outer) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
+            h->stats.outer_steps += 1;
+            outer_sym_eig(h->H, kMMax, k, h->theta, h->S, kMMax, h->hs_dev, s);   // line 6
+            outer_residual(oa, k, s);                                              // line 7
+            sync(h);
+            const double rn = hst(h)->rnorm, th1 = hst(h)->theta[0], th2 = hst(h)->theta[1];
+            const bool exhausted = (int64_t)(k + c) >= h->n - 1;
+            if (rn < tol || exhausted) {                                           // lines 8-10: lock
+                double* vcol = h->V + (size_t)c * h->ld;
+                const bool more = (c + 1 < d);
+                outer_rotate(oa, h->U, k, 1, more ? k - 1 : 0, vcol, s);           // v_j = U s1; purge (line 22)
+                if (more && k > 1) outer_rotate(oa, h->W, k, 1, k - 1, nullptr, s);
+                if (h->opts.precision == ISIRA_MIXED) copy_vcol<float>(vcol, h->Vt_f + (size_t)c * h->ld, h->n, s);
+                h->lam[c] = th1;
+                ++c;
+                h->stats.n_locked = c;
+                if (c == d) break;
+                gram_dirty = true;
+                if (k >= 2) {                                                      // line 23: move sigma
+                    outer_set_diag(oa, 1, k - 1, s);
+                    const double move = std::max(omega * (th2 - th1), 0.01 * th2);
+                    sig = th2 - move;
+                    k -= 1;
+                } else {
+                    outer_random(oa, o.seed, (uint64_t)(1000003 + c), s);
+                    if (!expand_basis(h, 0, c)) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
+                    k = 1;
+                }
+                continue;
+            }
+            if (k == m) {                                                          // lines 12-15: restart
+                outer_rotate(oa, h->U, k, 0, q, nullptr, s);
+                outer_rotate(oa, h->W, k, 0, q, nullptr, s);
+                outer_set_diag(oa, 0, q, s);
+                k = q;
+                h->stats.restarts += 1;
+            }
+            // line 17: inner solve of Eq. 2.14 and back-map Eq. 2.5 -> Z
+            if (h->opts.precision == ISIRA_MIXED)
+                run_inner<float>(h, h->fb, sig, c, h->Vt_f, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch);
+            else
+                run_inner<double>(h, h->db, sig, c, h->V, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch);
+            gram_dirty = false;
+            // lines 18-19: orthonormalise against [U V 1] and expand U, W, H
+            if (!expand_basis(h, k, c)) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
+            k += 1;
+        }
+        sync(h);
+        h->n_locked = c;
+        for (int j = 0; j < c; ++j)
+            if (h->lam[j] < 1e-10 * h->normL) status = ISIRA_ERR_NOT_CONNECTED;
+        h->solved = c > 0;
+    } catch (CudaError& e) {
+        status = map_cuda(e.e);
+    } catch (StatusError& e) {
+        status = e.s;
+    }
+    h->stats.solve_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return status;
+}
+
+isira_status isira_eigpairs(isira_handle h, double* h_eigvals, double* d_eigvecs, double* h_true_resid, int* n_out) {
+    if (!h) return ISIRA_ERR_INVALID_ARG;
+    if (!h->solved || h->n_locked < 1) return ISIRA_ERR_NOT_SOLVED;
+    try {
+        const int c = h->n_locked;
+        std::vector<int> order(c);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h->lam[a] < h->lam[b]; });
+        cudaStream_t s = h->stream;
+        if (h_eigvals)
+            for (int j = 0; j < c; ++j) h_eigvals[j] = h->lam[order[j]];
+        if (d_eigvecs)
+            for (int j = 0; j < c; ++j)
+                ck(cudaMemcpyAsync(d_eigvecs + (size_t)j * h->n, h->V + (size_t)order[j] * h->ld,
+                                   sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+        if (h_true_resid) {
+            ck(cudaMemcpyAsync(h->lam_dev, h->lam.data(), sizeof(double) * c, cudaMemcpyHostToDevice, s));
+            OuterArgs oa = make_outer(h);
+            outer_true_residual(oa, c, h->lam_dev, h->tres_dev, h->lanes, s);
+            std::vector<double> r2(c);
+            ck(cudaMemcpyAsync(r2.data(), h->tres_dev, sizeof(double) * c, cudaMemcpyDeviceToHost, s));
+            sync(h);
+            for (int j = 0; j < c; ++j) h_true_resid[j] = std::sqrt(r2[order[j]]) / h->normL;
+        }
+        sync(h);
+        if (n_out) *n_out = c;
+    } catch (CudaError& e) {
+        return map_cuda(e.e);
+    }
+    return ISIRA_OK;
+}
+
+isira_status isira_apply_operator(isira_handle h, int precision, double sigma, int c, const double* d_V,
+                                  const void* d_x, void* d_y) {
+    if (!h || !d_x || !d_y || c < 0 || c >= kCMax || (c > 0 && !d_V) ||
+        (precision != ISIRA_FP64 && precision != ISIRA_MIXED))
+        return ISIRA_ERR_INVALID_ARG;
+    try {
+        cudaStream_t s = h->stream;
+        if (precision == ISIRA_MIXED) {
+            alloc_inner(h, h->fb);
+            float* Vt = nullptr;
+            if (c > 0) {
+                ck(cudaMalloc(&Vt, sizeof(float) * (size_t)h->ld * c));
+                for (int t = 0; t < c; ++t) copy_vcol<float>(d_V + (size_t)t * h->n, Vt + (size_t)t * h->ld, h->n, s);
+            }
+            InnerArgs<float> a = make_args<float>(h, h->fb, sigma, c, Vt, h->ld, 1e-3, 1);
+            ck(cudaMemcpyAsync(a.z0, d_x, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, s));
+            ck(cudaMemsetAsync(a.z0 + h->trim, 0, sizeof(float), s));   // x_i is treated as 0
+            inner_opstats<float>(a, a.z0, s);
+            inner_phase1<float>(a, h->lanes, s);
+            ck(cudaMemcpyAsync(d_y, a.Y, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, s));
+            sync(h);
+            if (Vt) cudaFree(Vt);
+        } else {
+            alloc_inner(h, h->db);
+            double* Vt = nullptr;
+            if (c > 0) {
+                ck(cudaMalloc(&Vt, sizeof(double) * (size_t)h->ld * c));
+                for (int t = 0; t < c; ++t)
+                    ck(cudaMemcpyAsync(Vt + (size_t)t * h->ld, d_V + (size_t)t * h->n, sizeof(double) * h->n,
+                                       cudaMemcpyDeviceToDevice, s));
+            }
+            InnerArgs<double> a = make_args<double>(h, h->db, sigma, c, Vt, h->ld, 1e-3, 1);
+            ck(cudaMemcpyAsync(a.z0, d_x, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+            ck(cudaMemsetAsync(a.z0 + h->trim, 0, sizeof(double), s));  // x_i is treated as 0
+            inner_opstats<double>(a, a.z0, s);
+            inner_phase1<double>(a, h->lanes, s);
+            ck(cudaMemcpyAsync(d_y, a.Y, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+            sync(h);
+            if (Vt) cudaFree(Vt);
+        }
+    } catch (CudaError& e) {
+        return map_cuda(e.e);
+    }
+    return ISIRA_OK;
+}
+
+isira_status isira_inner_solve(isira_handle h, int precision, double sigma, int c, const double* d_V,
+                               const double* d_r, double tau, int max_it, double* d_z, int* iters, double* relres) {
+    if (!h || !d_r || !d_z || c < 0 || c >= kCMax || (c > 0 && !d_V) || !(tau > 0.0) || max_it < 1 ||
+        (precision != ISIRA_FP64 && precision != ISIRA_MIXED))
+        return ISIRA_ERR_INVALID_ARG;
+    try {
+        cudaStream_t s = h->stream;
+        // the right-hand side goes through the residual buffer, its norm through the scalar area
+        ck(cudaMemcpyAsync(h->R, d_r, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+        const double one = 1.0;
+        ck(cudaMemcpyAsync(h->dscratch + 300, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+        int its = 0;
+        if (precision == ISIRA_MIXED) {
+            alloc_inner(h, h->fb);
+            float* Vt = nullptr;
+            if (c > 0) {
+                ck(cudaMalloc(&Vt, sizeof(float) * (size_t)h->ld * c));
+                for (int t = 0; t < c; ++t) copy_vcol<float>(d_V + (size_t)t * h->n, Vt + (size_t)t * h->ld, h->n, s);
+            }
+            its = run_inner<float>(h, h->fb, sigma, c, Vt, h->ld, tau, max_it, true, h->R, h->dscratch + 300);
+            if (Vt) cudaFree(Vt);
+        } else {
+            alloc_inner(h, h->db);
+            double* Vt = nullptr;
+            if (c > 0) {
+                ck(cudaMalloc(&Vt, sizeof(double) * (size_t)h->ld * c));
+                for (int t = 0; t < c; ++t)
+                    ck(cudaMemcpyAsync(Vt + (size_t)t * h->ld, d_V + (size_t)t * h->n, sizeof(double) * h->n,
+                                       cudaMemcpyDeviceToDevice, s));
+            }
+            its = run_inner<double>(h, h->db, sigma, c, Vt, h->ld, tau, max_it, true, h->R, h->dscratch + 300);
+            if (Vt) cudaFree(Vt);
+        }
+        // back-map (Eq. 2.5): remove the mean; the trimmed entry is already zero
+        OuterArgs oa = make_outer(h);
+        outer_cgs2(oa, 0, 0, s);   // with an empty basis the two passes only subtract the mean
+        sync(h);
+        ck(cudaMemcpyAsync(d_z, h->Z, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+        sync(h);
+        if (iters) *iters = its;
+        if (relres) *relres = hst(h)->inner_relres;
+    } catch (CudaError& e) {
+        return map_cuda(e.e);
+    }
+    return ISIRA_OK;
+}
+
+isira_status isira_sym_eig(int k, const double* d_H, double* d_theta, double* d_S, void* stream) {
+    if (k < 1 || k > kMMax || !d_H || !d_theta || !d_S) return ISIRA_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    outer_sym_eig(d_H, k, k, d_theta, d_S, k, nullptr, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? ISIRA_OK : ISIRA_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+"""End-to-end parity of isira_solve (Algorithm 2 on the GPU) with closed forms, the dense
+definition oracle and the FP64 algorithm oracle, in plain FP64 and mixed precision, plus
+the error paths of the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthgraphs as sg
+from tests import closed_forms as cf
+from tests.gpu_util import dev_graph, need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp64", "mixed"]
+
+
+@pytest.fixture(scope="module")
+def isira():
+    need_gpu()
+    import paper_1710_07080_gb300 as m
+    return m
+
+
+def _prec(isira, p):
+    return isira.ISIRA_FP64 if p == "fp64" else isira.ISIRA_MIXED
+
+
+def run(isira, g, d, prec, tol=None, rel_tol=1e-10, **opts):
+    rp, ci = dev_graph(g)
+    u0 = torch.from_numpy(sg.start_vector(g.n, 1)).cuda()
+    res = isira.solve(rp, ci, d, tol=tol, rel_tol=rel_tol, u0=u0, precision=_prec(isira, prec), **opts)
+    return res
+
+
+def check_pairs(g, res, d, rel_res=1e-8):
+    lam = res.eigvals.numpy()
+    V = res.eigvecs.cpu().numpy()
+    assert lam.shape == (d,) and V.shape == (g.n, d)
+    assert np.all(np.diff(lam) >= 0)
+    normL = 2.0 * g.degrees.max()
+    for j in range(d):   # true residual recomputed with the oracle's Laplacian
+        r = oracle.laplacian_apply(g.row_ptr, g.col_idx, V[:, j]) - lam[j] * V[:, j]
+        assert np.linalg.norm(r) / normL <= rel_res
+    np.testing.assert_allclose(res.true_resid.numpy(), [
+        np.linalg.norm(oracle.laplacian_apply(g.row_ptr, g.col_idx, V[:, j]) - lam[j] * V[:, j]) / normL
+        for j in range(d)], rtol=1e-6, atol=1e-16)
+    np.testing.assert_allclose(V.T @ V, np.eye(d), atol=1e-10)
+    np.testing.assert_allclose(V.sum(axis=0), 0.0, atol=1e-9 * math.sqrt(g.n))
+    return lam, V
+
+
+def cluster_subspace_check(lam_ref, X_ref, V, lam, rtol_gap=1e-6):
+    """Compare eigenvector subspaces of complete clusters of equal eigenvalues."""
+    d = V.shape[1]
+    j = 0
+    while j < d:
+        e = j
+        while e + 1 < len(lam_ref) and abs(lam_ref[e + 1] - lam_ref[j]) <= rtol_gap * lam_ref[j]:
+            e += 1
+        if e < d:   # the cluster j..e is inside the computed set
+            P_ref = X_ref[:, j:e + 1] @ X_ref[:, j:e + 1].T
+            P = V[:, j:e + 1] @ V[:, j:e + 1].T
+            assert np.linalg.norm(P - P_ref, 2) <= 1e-6
+        j = e + 1
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grid100_closed_form_and_oracle(isira, prec):
+    """2D 5-point grid 100 x 100, d = 5, tol 1e-10 (absolute, the paper's epsilon)."""
+    g = sg.grid2d(100, 100)
+    res = run(isira, g, 5, prec, tol=1e-10)
+    assert res.status == isira.ISIRA_OK
+    lam, V = check_pairs(g, res, 5)
+    ref = cf.grid2d(100, 100)[1:6]
+    np.testing.assert_allclose(lam, ref, rtol=1e-9)
+    lam_or, V_or, st = oracle.isira(g.row_ptr, g.col_idx, 5, sg.start_vector(g.n, 1), eps=1e-10, tau_inner=1e-3)
+    order = np.argsort(lam_or)
+    np.testing.assert_allclose(lam, lam_or[order], rtol=1e-9)
+    # complete clusters 2 + 1 + 2: compare invariant subspaces with the oracle's
+    cluster_subspace_check(lam_or[order], V_or[:, order], V, lam)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["path300", "cycle301", "grid3d_10_11_12", "hypercube8", "star5000",
+                                  "complete40"])
+def test_closed_forms(isira, prec, case):
+    g, ref, d = {
+        "path300": (sg.path(300), cf.path(300), 6),
+        "cycle301": (sg.cycle(301), cf.cycle(301), 6),
+        "grid3d_10_11_12": (sg.grid3d(10, 11, 12), cf.grid3d(10, 11, 12), 8),
+        "hypercube8": (sg.hypercube(8), cf.hypercube(8), 3),
+        "star5000": (sg.star(5000), cf.star(5000), 1),
+        "complete40": (sg.complete(40), cf.complete(40), 3),
+    }[case]
+    res = run(isira, g, d, prec, tol=1e-10 * 2 * g.degrees.max())
+    assert res.status == isira.ISIRA_OK
+    lam, _ = check_pairs(g, res, d)
+    np.testing.assert_allclose(lam, ref[1:1 + d], rtol=1e-9)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("g,d", [(sg.rmat(9), 10), (sg.erdos_renyi(250, 6.0, seed=2), 8),
+                                 (sg.watts_strogatz(300, 6, 0.1, seed=4), 6)], ids=lambda x: getattr(x, "name", ""))
+def test_small_graphs_vs_dense_definition(isira, prec, g, d):
+    res = run(isira, g, d, prec, tol=1e-11 * 2 * g.degrees.max())
+    assert res.status == isira.ISIRA_OK
+    lam, V = check_pairs(g, res, d)
+    lam_d, X_d = oracle.dense_laplacian_eig(g.row_ptr, g.col_idx)
+    np.testing.assert_allclose(lam, lam_d[1:1 + d], rtol=1e-9)
+    cluster_subspace_check(lam_d[1:], X_d[:, 1:], V, lam)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("scale", [12, 14])
+def test_rmat_vs_algorithm_oracle(isira, prec, scale):
+    """R-MAT LCC (heavy-tailed degrees): GPU vs the FP64 algorithm oracle and LAPACK/ARPACK."""
+    g = sg.rmat(scale)
+    normL = 2.0 * g.degrees.max()
+    tol = 1e-12 * normL
+    res = run(isira, g, 10, prec, tol=tol)
+    assert res.status == isira.ISIRA_OK
+    lam, V = check_pairs(g, res, 10, rel_res=1e-11)
+    lam_or, V_or, st = oracle.isira(g.row_ptr, g.col_idx, 10, sg.start_vector(g.n, 1), eps=tol, tau_inner=1e-3)
+    assert st["status"] == 0
+    np.testing.assert_allclose(lam, np.sort(lam_or), rtol=1e-9)
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import eigsh
+    A = sp.csr_matrix((np.ones(g.nnz), g.col_idx, g.row_ptr), shape=(g.n, g.n))
+    L = (sp.diags(np.asarray(A.sum(1)).ravel()) - A).tocsc()
+    w = np.sort(eigsh(L, k=12, sigma=-1e-3, which="LM", return_eigenvectors=False))
+    np.testing.assert_allclose(lam, w[1:11], rtol=1e-9)
+
+
+def test_mixed_matches_fp64_and_is_deterministic(isira):
+    g = sg.rmat(13)
+    tol = 1e-12 * 2 * g.degrees.max()
+    a = run(isira, g, 8, "fp64", tol=tol)
+    b = run(isira, g, 8, "mixed", tol=tol)
+    c = run(isira, g, 8, "mixed", tol=tol)
+    np.testing.assert_allclose(b.eigvals.numpy(), a.eigvals.numpy(), rtol=1e-9)
+    np.testing.assert_array_equal(b.eigvals.numpy(), c.eigvals.numpy())
+    assert b.stats["inner_iters"] == c.stats["inner_iters"]
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 8, 32])
+def test_every_lane_count_solves(isira, lanes):
+    g = sg.rmat(11)
+    tol = 1e-11 * 2 * g.degrees.max()
+    res = run(isira, g, 4, "mixed", tol=tol, spmv_lanes=lanes)
+    assert res.stats["spmv_lanes"] == lanes
+    check_pairs(g, res, 4)
+
+
+def test_options_trim_drop_rank1_restart(isira):
+    g = sg.grid2d(30, 29)
+    ref = cf.grid2d(30, 29)[1:7]
+    for kw in [dict(trim_index=0), dict(trim_index=g.n - 1), dict(drop_rank1=1), dict(m=12, q=7),
+               dict(delta=100.0), dict(inner_chunk=3), dict(tau_inner=1e-2)]:
+        res = run(isira, g, 6, "mixed", tol=1e-10, **kw)
+        assert res.status == isira.ISIRA_OK, kw
+        lam, _ = check_pairs(g, res, 6)
+        np.testing.assert_allclose(lam, ref, rtol=1e-9, err_msg=str(kw))
+    res = run(isira, g, 6, "mixed", tol=1e-10, m=12, q=7)
+    assert res.stats["restarts"] > 0
+
+
+def test_default_start_vector(isira):
+    g = sg.grid2d(20, 21)
+    rp, ci = dev_graph(g)
+    res = isira.solve(rp, ci, 4, tol=1e-10)
+    assert res.status == isira.ISIRA_OK
+    np.testing.assert_allclose(res.eigvals.numpy(), cf.grid2d(20, 21)[1:5], rtol=1e-9)
+
+
+def test_error_paths(isira):
+    g = sg.grid2d(10, 10)
+    rp, ci = dev_graph(g)
+    with isira.Solver(rp, ci) as s:
+        with pytest.raises(isira.IsiraError) as e:
+            s.eigpairs()
+        assert e.value.status == isira.ISIRA_ERR_NOT_SOLVED
+        assert s.solve(0, raise_on_error=False) == isira.ISIRA_ERR_INVALID_ARG
+        assert s.solve(33, raise_on_error=False) == isira.ISIRA_ERR_INVALID_ARG
+        assert s.solve(3, tol=-1.0, raise_on_error=False) == isira.ISIRA_ERR_INVALID_ARG
+    # outer cap: status NO_CONVERGENCE, locked pairs still available
+    res = run(isira, g, 5, "mixed", tol=1e-12, max_outer=9)
+    assert res.status == isira.ISIRA_ERR_NO_CONVERGENCE
+    assert res.eigvals.numel() == res.stats["n_locked"] < 5
+    with pytest.raises(isira.IsiraError):
+        isira.Solver(rp, ci, precision=7)
+
+
+def test_disconnected_graph_is_reported(isira):
+    a = sg.path(40)
+    u = np.concatenate([np.arange(39), 40 + np.arange(29)])
+    v = u + 1
+    rp, ci = sg.csr_from_edges(70, u, v)
+    g = sg.Graph(rp, ci, "two_paths")
+    res = run(isira, g, 2, "fp64", tol=1e-10)
+    assert res.status == isira.ISIRA_ERR_NOT_CONNECTED
+
+
+def test_validate_rejects_malformed_csr(isira):
+    g = sg.grid2d(6, 6)
+    ci = g.col_idx.copy()
+    ci[3] = (ci[3] + 7) % g.n              # breaks symmetry (and maybe the ordering)
+    rp_t, ci_t = torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(ci).cuda()
+    with pytest.raises(isira.IsiraError) as e:
+        isira.Solver(rp_t, ci_t, validate=1)
+    assert e.value.status == isira.ISIRA_ERR_BAD_GRAPH
+    rp_ok, ci_ok = dev_graph(g)
+    with isira.Solver(rp_ok, ci_ok, validate=1) as s:
+        assert s.stats()["n"] == g.n
