@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark: time to the k smallest positive Laplacian eigenpairs with iSIRA on one GB300.
+
+Workload (default): R-MAT scale 20 (edge factor 16, a,b,c,d = .57/.19/.19/.05, seed 1),
+symmetrised, deduplicated, loop-free, largest connected component; k = 10; convergence at
+relative residual ||L x - lambda x|| / ||L|| <= 1e-8 with ||L|| := 2 * max degree.  The
+headline value is the plain-FP64 solve; the mixed solve (FP32 inner, FP64 outer) is timed on
+the same graph and reported beside it.
+
+A step is one full isira_solve (all of Algorithm 2: inner solves, orthogonalisation,
+Rayleigh-Ritz, restarts, locking).  Inputs are resident in HBM; the L2 is flushed (a 512 MB
+write) between timed steps; each step is timed with CUDA events on the library's stream.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank solves its own copy of the workload (replicas: the method
+has no data-parallel split of one graph) and rank 0 prints the max over ranks.
+``--impl reference`` times the FP64 CPU oracle (Algorithm 2 as written, 1 thread) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to k eigenpairs at resid 1e-8 (mixed vs FP64); SpMV GB/s vs HBM peak"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="rmat20")
+    p.add_argument("--k", type=int, default=10)
+    p.add_argument("--rel-tol", type=float, default=1e-8)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--single-solve", choices=["fp64", "mixed"], default=None,
+                   help="create one solver and run one solve, nothing else (for profiler captures)")
+    return p.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload_config(name, g, k, rel_tol):
+    desc = {"rmat20": "R-MAT scale 20, edge factor 16, a,b,c,d=.57/.19/.19/.05, seed 1, symmetrised LCC"}
+    return {"workload": f"{name}-lcc k={k} fp64", "graph": desc.get(name, name), "n": g.n, "nnz": g.nnz,
+            "k": k, "resid_rel": rel_tol, "norm_L": "2*max_degree", "l2": "flushed (512 MB write) between steps",
+            "start_vector": "splitmix64 seed 1, centred, unit norm"}
+
+
+# --------------------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region, for the device in use."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0]:
+                continue
+            rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_median": statistics.median([float(r[3]) for r in rows if _isnum(r[3])]) if rows else None}
+
+
+def _isnum(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+# --------------------------------------------------------------------------------------------- roofline
+
+def phase1_bytes(n, Z, c_avg, word):
+    """Algorithmic DRAM bytes of one phase-1 launch (the fused SpMV + MINRES row update):
+    row_ptr 8(n+1), col_idx 4Z, z_k gathered once (word*n), z_{k-1}, w_{j-2}, w_{j-1} read,
+    x read+write, w_j and Y written (7 word*n), and c columns of Vh (word*c*n)."""
+    return 8 * (n + 1) + 4 * Z + word * n * 8 + word * c_avg * n
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for d in ["paper_1710_07080_gb300/csrc"]:
+        for f in sorted(os.listdir(os.path.join(ROOT, d))):
+            h.update(open(os.path.join(ROOT, d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == cur:
+            return float(parts[2])
+    return None
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            pk = json.load(open(path))
+            for key in ("hbm_gbs_sustained", "hbm_gbs"):
+                if key in pk and pk[key]:
+                    return float(pk[key]), f"measured ({key})"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# --------------------------------------------------------------------------------------------- oracle leg
+
+def oracle_sample(g, k, tol_abs, u0, max_outer):
+    import oracle
+    t0 = time.perf_counter()
+    lam, V, st = oracle.isira(g.row_ptr, g.col_idx, k, u0, eps=tol_abs, tau_inner=1e-3, max_outer=max_outer)
+    return time.perf_counter() - t0, st
+
+
+def oracle_outer_steps_reference(name):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_bench.json")
+    if os.path.exists(path):
+        return int(json.load(open(path))["oracle_stats"]["outer_steps"]), "oracle full run (tests/golden)"
+    return None, None
+
+
+def run_reference(args):
+    import numpy as np  # noqa: F401
+    import synthgraphs as sg
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    g = sg.workload(args.workload)
+    normL = 2.0 * float(g.degrees.max())
+    tol = args.rel_tol * normL
+    u0 = sg.start_vector(g.n, 1)
+    S = 2
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, st = oracle_sample(g, args.k, tol, u0, S)
+        if i >= args.warmup:
+            times.append(dt / max(1, st["outer_steps"]))
+    n_outer, src = oracle_outer_steps_reference(args.workload)
+    per_step = statistics.mean(times)
+    value = per_step * n_outer if n_outer else None
+    sample = (f"first {S} outer steps of Algorithm 2 (FP64 oracle, tau_inner 1e-3) on the full workload, "
+              f"{per_step:.3f} s per outer step, projected to {n_outer} outer steps ({src}); early steps "
+              f"have a small search space, so the projection understates the oracle's full time")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, g, args.k, args.rel_tol),
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import paper_1710_07080_gb300 as isira
+    import synthgraphs as sg
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    g = sg.workload(args.workload)
+    n, Z, k = g.n, g.nnz, args.k
+    normL = 2.0 * float(g.degrees.max())
+    tol = args.rel_tol * normL
+    if args.single_solve:
+        prec = isira.ISIRA_FP64 if args.single_solve == "fp64" else isira.ISIRA_MIXED
+        with isira.Solver(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev),
+                          precision=prec) as s:
+            s.solve(k, tol=tol, u0=torch.from_numpy(sg.start_vector(n, 1)).to(dev))
+            torch.cuda.synchronize()
+            print(json.dumps({"single_solve": args.single_solve, **s.stats()}), flush=True)
+        return
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    ci_h = torch.from_numpy(g.col_idx).pin_memory()
+    u0_h = torch.from_numpy(sg.start_vector(n, 1)).pin_memory()
+    rp = rp_h.to(dev)
+    ci = ci_h.to(dev)
+    u0 = u0_h.to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    uuid = str(torch.cuda.get_device_properties(dev).uuid) if hasattr(torch.cuda.get_device_properties(dev), "uuid") else ""
+
+    def timed_solves(solver, profile):
+        for _ in range(args.warmup):
+            solver.solve(k, tol=tol, u0=u0)
+        torch.cuda.synchronize()
+        solver.set_profiling(profile)
+        times, stats = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.solve(k, tol=tol, u0=u0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            stats.append(solver.stats())
+        solver.set_profiling(False)
+        return times, stats
+
+    clk = ClockSampler(uuid.replace("GPU-", "") if uuid else "")
+    s64 = isira.Solver(rp, ci, precision=isira.ISIRA_FP64)
+    smx = isira.Solver(rp, ci, precision=isira.ISIRA_MIXED)
+    clk.start()
+    t64, st64 = timed_solves(s64, True)
+    tmx, stmx = timed_solves(smx, True)
+    clocks = clk.stop()
+    lam64, vec64, res64 = s64.eigpairs()
+    lammx, vecmx, resmx = smx.eigpairs()
+
+    # accuracy of the benchmarked solves against a tight FP64 solve (untimed)
+    ref = isira.solve(rp, ci, k, tol=1e-12 * normL, u0=u0, precision=isira.ISIRA_FP64)
+    lam_ref = ref.eigvals.numpy()
+
+    def relerr(a):
+        return float(np.max(np.abs(a.numpy() - lam_ref) / np.abs(lam_ref)))
+
+    # end to end through the public API: pinned host CSR -> device, create, solve, eigenpairs -> host
+    e2e_times = []
+    h2d = rp_h.numel() * 8 + ci_h.numel() * 4 + u0_h.numel() * 8
+    d2h = n * k * 8 + k * 8 * 2
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rp_d = rp_h.to(dev, non_blocking=True)
+        ci_d = ci_h.to(dev, non_blocking=True)
+        u0_d = u0_h.to(dev, non_blocking=True)
+        with isira.Solver(rp_d, ci_d, precision=isira.ISIRA_FP64) as s:
+            s.solve(k, tol=tol, u0=u0_d)
+            lam_e, vec_e, res_e = s.eigpairs()
+            vec_host = vec_e.cpu()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_times.append(dt)
+    del vec_host
+
+    value = max_over_ranks(statistics.mean(t64))
+    value_mx = max_over_ranks(statistics.mean(tmx))
+    e2e = max_over_ranks(statistics.mean(e2e_times))
+
+    # roofline of the dominant kernel (phase 1 of the FP64 inner solve), from the live events
+    p1_ms = sum(s["inner_phase1_ms"] for s in st64)
+    p1_n = sum(s["inner_phase1_timed"] for s in st64)
+    p1_c = sum(s["inner_phase1_csum"] for s in st64) / max(1, p1_n)
+    avg_s = p1_ms / 1e3 / max(1, p1_n)
+    bytes_launch = phase1_bytes(n, Z, p1_c, 8)
+    peak, peak_src = hbm_peak()
+    achieved = bytes_launch / avg_s / 1e9 if avg_s > 0 else None
+    p1mx_ms = sum(s["inner_phase1_ms"] for s in stmx)
+    p1mx_n = sum(s["inner_phase1_timed"] for s in stmx)
+    p1mx_c = sum(s["inner_phase1_csum"] for s in stmx) / max(1, p1mx_n)
+    avgmx_s = p1mx_ms / 1e3 / max(1, p1mx_n)
+    achieved_mx = phase1_bytes(n, Z, p1mx_c, 4) / avgmx_s / 1e9 if avgmx_s > 0 else None
+    traffic = ncu_traffic("phase1_fp64_rmat20")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": workload_config(args.workload, g, k, args.rel_tol),
+        "mixed": {"value": value_mx, "unit": "s", "dtype": "f32 inner / f64 outer",
+                  "speedup_vs_fp64": value / value_mx if value_mx else None,
+                  "outer_steps": stmx[-1]["outer_steps"], "inner_iters": stmx[-1]["inner_iters"],
+                  "phase1_avg_us": avgmx_s * 1e6, "phase1_GBps": achieved_mx},
+        "fp64": {"outer_steps": st64[-1]["outer_steps"], "inner_iters": st64[-1]["inner_iters"],
+                 "restarts": st64[-1]["restarts"], "spmv_lanes": st64[-1]["spmv_lanes"],
+                 "phase1_avg_us": avg_s * 1e6, "phase1_launches_timed": p1_n},
+        "accuracy": {"max_rel_eig_err_fp64_vs_tight": relerr(lam64), "max_rel_eig_err_mixed_vs_tight": relerr(lammx),
+                     "max_true_resid_rel_fp64": float(res64.max()), "max_true_resid_rel_mixed": float(resmx.max()),
+                     "tight_tol_rel": 1e-12, "eigvals": [float(x) for x in lam_ref]},
+        "roofline": {"kernel": "k_phase1<double> (trimmed operator SpMV + MINRES row update)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "peak_source": peak_src,
+                     "bytes_per_launch": bytes_launch, "avg_deflation_rank": p1_c, "traffic": traffic},
+        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "pinned host CSR -> isira_create -> isira_solve -> isira_eigpairs -> host"},
+        "gpu_launches": int(sum(s["kernel_launches"] for s in st64)),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        S = 2
+        dt, st = oracle_sample(g, k, tol, u0_h.numpy(), S)
+        per = dt / max(1, st["outer_steps"])
+        n_outer = st64[-1]["outer_steps"]
+        line["cpu_baseline"] = {
+            "value": per * n_outer, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"first {st['outer_steps']} outer steps of Algorithm 2 (FP64 oracle, tau_inner 1e-3, 1 thread) "
+                       f"on the same graph: {per:.3f} s per outer step, projected to the {n_outer} outer steps of the "
+                       f"GPU FP64 run; early steps have a small search space, so this understates the oracle")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s64.close()
+    smx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

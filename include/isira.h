@@ -93,6 +93,8 @@ typedef struct {
     double solve_ms;          /* host wall time of the last isira_solve */
     double inner_phase1_ms;   /* summed device time of phase-1 launches (only with profiling on) */
     long long inner_phase1_timed; /* number of phase-1 launches timed */
+    long long inner_phase1_csum;  /* sum of the deflation rank c over the timed phase-1 launches */
+    long long kernel_launches;    /* kernels launched by the last isira_solve */
 } isira_stats;
 
 /* Fills *opts with the defaults listed above (precision = ISIRA_MIXED). */

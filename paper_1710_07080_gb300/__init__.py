@@ -45,7 +45,8 @@ class isira_stats(C.Structure):
                 ("n_heavy_rows", C.c_int), ("n_medium_rows", C.c_int), ("n_locked", C.c_int),
                 ("outer_steps", C.c_int), ("restarts", C.c_int), ("breakdowns", C.c_int),
                 ("inner_iters", C.c_longlong), ("inner_solves", C.c_longlong), ("spmv_launches", C.c_longlong),
-                ("solve_ms", C.c_double), ("inner_phase1_ms", C.c_double), ("inner_phase1_timed", C.c_longlong)]
+                ("solve_ms", C.c_double), ("inner_phase1_ms", C.c_double), ("inner_phase1_timed", C.c_longlong),
+                ("inner_phase1_csum", C.c_longlong), ("kernel_launches", C.c_longlong)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -145,6 +146,7 @@ class Solver:
         check(lib.isira_create(C.byref(h), self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col_idx),
                                C.byref(self.opts), self.stream), "isira_create")
         self.h = h
+        self._last_status = None
 
     def close(self):
         if getattr(self, "h", None):
@@ -177,6 +179,7 @@ class Solver:
         if tol is None:
             tol = rel_tol * self.stats()["norm_L"]
         st = lib.isira_solve(self.h, int(k), float(sigma), float(tol), _ptr(u0))
+        self._last_status = st
         if raise_on_error and st not in (ISIRA_OK,):
             raise IsiraError(st, "isira_solve")
         return st
@@ -185,6 +188,10 @@ class Solver:
         import torch
         st = self.stats()
         k = st["n_locked"]
+        if k == 0 and self._last_status == ISIRA_ERR_NO_CONVERGENCE:
+            empty = torch.empty(0, dtype=torch.float64)
+            vec = torch.empty((self.n, 0), dtype=torch.float64, device=self.row_ptr.device)
+            return empty, (vec if want_vectors else None), (empty if want_resid else None)
         lam = torch.empty(k, dtype=torch.float64)
         vec = torch.empty((k, self.n), dtype=torch.float64, device=self.row_ptr.device) if want_vectors else None
         res = torch.empty(k, dtype=torch.float64) if want_resid else None

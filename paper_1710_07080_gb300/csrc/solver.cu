@@ -162,9 +162,13 @@ int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* 
               int max_it, bool gram_dirty, const double* R, const double* rnorm_dev) {
     InnerArgs<T> a = make_args<T>(h, b, sigma, c, Vt, ldv, tau, max_it);
     cudaStream_t s = h->stream;
-    if (gram_dirty && c > 0) gram_setup<T>(a, h->Gm, h->Cinv, h->partial, s);
+    if (gram_dirty && c > 0) {
+        gram_setup<T>(a, h->Gm, h->Cinv, h->partial, s);
+        h->stats.kernel_launches += 1;
+    }
     inner_prep_launch<T>(a, R, rnorm_dev, s);
     inner_phase2<T>(a, 1, s);
+    h->stats.kernel_launches += 2;
     const int chunk = h->opts.inner_chunk > 0 ? h->opts.inner_chunk : 16;
     int launched = 0;
     while (true) {
@@ -176,6 +180,7 @@ int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* 
             inner_phase2<T>(a, 0, s);
         }
         h->stats.spmv_launches += chunk;
+        h->stats.kernel_launches += 2 * chunk;
         sync(h);
         const int itn = hst(h)->inner_iters;
         if (prof) {
@@ -185,6 +190,7 @@ int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* 
                 ck(cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]));
                 h->stats.inner_phase1_ms += ms;
                 h->stats.inner_phase1_timed += 1;
+                h->stats.inner_phase1_csum += c;
             }
         }
         launched += chunk;
@@ -192,6 +198,7 @@ int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* 
         if (launched > max_it + 2 * chunk) break;   // defensive: the device test caps at max_it
     }
     inner_finalize_to<T>(a, h->Z, s);
+    h->stats.kernel_launches += 1;
     h->stats.inner_solves += 1;
     const int its = hst(h)->inner_iters;
     h->stats.inner_iters += its;
@@ -226,14 +233,17 @@ bool expand_basis(isira_handle h, int k, int c) {
     cudaStream_t s = h->stream;
     for (int attempt = 0; attempt < 8; ++attempt) {
         outer_cgs2(oa, k, c, s);
+        h->stats.kernel_launches += 3;
         sync(h);
         const double zin = hst(h)->cgs_in, zout = hst(h)->cgs_out;
         if (zout > 1e-10 * zin && zout > 0.0 && std::isfinite(zout)) {
             outer_expand(oa, k, h->lanes, s);
+            h->stats.kernel_launches += 2;
             return true;
         }
         h->stats.breakdowns += 1;
         outer_random(oa, h->opts.seed, (uint64_t)(1 + h->stats.breakdowns), s);
+        h->stats.kernel_launches += 1;
     }
     return false;
 }
@@ -492,6 +502,8 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         h->stats.spmv_launches = 0;
         h->stats.inner_phase1_ms = 0.0;
         h->stats.inner_phase1_timed = 0;
+        h->stats.inner_phase1_csum = 0;
+        h->stats.kernel_launches = 0;
         (void)keep;
         h->lam.assign(d, 0.0);
         OuterArgs oa = make_outer(h);
@@ -499,6 +511,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         // start basis U_{k0}, k0 = 1 (Algorithm 2 REQUIRE): the given vector, or a SplitMix64 one
         if (d_u0) ck(cudaMemcpyAsync(h->Z, d_u0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
         else outer_random(oa, o.seed, 0, s);
+        h->stats.kernel_launches += d_u0 ? 0 : 1;
         if (!expand_basis(h, 0, 0)) throw StatusError{ISIRA_ERR_NO_CONVERGENCE};
         int k = 1, c = 0;
         double sig = sigma;
@@ -508,6 +521,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
             h->stats.outer_steps += 1;
             outer_sym_eig(h->H, kMMax, k, h->theta, h->S, kMMax, h->hs_dev, s);   // line 6
             outer_residual(oa, k, s);                                              // line 7
+            h->stats.kernel_launches += 2;
             sync(h);
             const double rn = hst(h)->rnorm, th1 = hst(h)->theta[0], th2 = hst(h)->theta[1];
             const bool exhausted = (int64_t)(k + c) >= h->n - 1;
@@ -515,8 +529,15 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 double* vcol = h->V + (size_t)c * h->ld;
                 const bool more = (c + 1 < d);
                 outer_rotate(oa, h->U, k, 1, more ? k - 1 : 0, vcol, s);           // v_j = U s1; purge (line 22)
-                if (more && k > 1) outer_rotate(oa, h->W, k, 1, k - 1, nullptr, s);
-                if (h->opts.precision == ISIRA_MIXED) copy_vcol<float>(vcol, h->Vt_f + (size_t)c * h->ld, h->n, s);
+                h->stats.kernel_launches += 1;
+                if (more && k > 1) {
+                    outer_rotate(oa, h->W, k, 1, k - 1, nullptr, s);
+                    h->stats.kernel_launches += 1;
+                }
+                if (h->opts.precision == ISIRA_MIXED) {
+                    copy_vcol<float>(vcol, h->Vt_f + (size_t)c * h->ld, h->n, s);
+                    h->stats.kernel_launches += 1;
+                }
                 h->lam[c] = th1;
                 ++c;
                 h->stats.n_locked = c;
@@ -524,11 +545,13 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 gram_dirty = true;
                 if (k >= 2) {                                                      // line 23: move sigma
                     outer_set_diag(oa, 1, k - 1, s);
+                    h->stats.kernel_launches += 1;
                     const double move = std::max(omega * (th2 - th1), 0.01 * th2);
                     sig = th2 - move;
                     k -= 1;
                 } else {
                     outer_random(oa, o.seed, (uint64_t)(1000003 + c), s);
+                    h->stats.kernel_launches += 1;
                     if (!expand_basis(h, 0, c)) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
                     k = 1;
                 }
@@ -538,6 +561,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 outer_rotate(oa, h->U, k, 0, q, nullptr, s);
                 outer_rotate(oa, h->W, k, 0, q, nullptr, s);
                 outer_set_diag(oa, 0, q, s);
+                h->stats.kernel_launches += 3;
                 k = q;
                 h->stats.restarts += 1;
             }

@@ -45,7 +45,7 @@ def check_pairs(g, res, d, rel_res=1e-8):
         assert np.linalg.norm(r) / normL <= rel_res
     np.testing.assert_allclose(res.true_resid.numpy(), [
         np.linalg.norm(oracle.laplacian_apply(g.row_ptr, g.col_idx, V[:, j]) - lam[j] * V[:, j]) / normL
-        for j in range(d)], rtol=1e-6, atol=1e-16)
+        for j in range(d)], rtol=1e-6, atol=1e-14)
     np.testing.assert_allclose(V.T @ V, np.eye(d), atol=1e-10)
     np.testing.assert_allclose(V.sum(axis=0), 0.0, atol=1e-9 * math.sqrt(g.n))
     return lam, V
