@@ -50,7 +50,8 @@ typedef enum {
     ISIRA_ERR_NO_CONVERGENCE = 4,  /* max_outer reached; already locked pairs are kept */
     ISIRA_ERR_CUDA = 5,            /* a CUDA runtime call failed */
     ISIRA_ERR_OOM = 6,             /* device or pinned allocation failed */
-    ISIRA_ERR_NOT_SOLVED = 7       /* eigpairs requested before a successful solve */
+    ISIRA_ERR_NOT_SOLVED = 7,      /* eigpairs requested before a successful solve */
+    ISIRA_ERR_LIMIT = 8            /* request exceeds the fixed scratch of isira_apply_operator_noalloc */
 } isira_status;
 
 enum { ISIRA_FP64 = 0,   /* inner solve in FP64 ("plain") */
@@ -166,6 +167,30 @@ ISIRA_API isira_status isira_inner_solve(isira_handle h, int precision, double s
  * d_theta: k ascending eigenvalues; d_S: k-by-k unit eigenvectors, each signed so that
  * its largest-magnitude entry (first on ties) is positive.  stream as above. */
 ISIRA_API isira_status isira_sym_eig(int k, const double* d_H, double* d_theta, double* d_S, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * Allocation-free variant (the paper has no counterpart; it exists for callers of this
+ * library that cannot allocate device memory: programs whose device memory is entirely
+ * pre-reserved by their own pool allocator, latency-critical loops in which cudaMalloc and
+ * cudaFree, which may synchronise the device, are not acceptable, and plug-ins whose host
+ * application forbids allocations it does not make itself).
+ *
+ * Computes the same result as isira_apply_operator, without a handle: y_r = (deg_r - sigma) x_r
+ * - sum_{c in N(r), c != trim} x_c + (sigma/n) sum_{r != trim} x_r + delta sum_t V_rt (Vh^T x)_t for
+ * r != trim, y_trim = 0 (drop_rank1 = 1 omits the (sigma/n) term).  All pointers are device
+ * pointers: CSR as in isira_create; d_V n-by-c column-major double (ld n, may be NULL when
+ * c == 0); d_x, d_y float (ISIRA_MIXED) or double (ISIRA_FP64) n-vectors.  0 <= trim < n.
+ * Calls no cudaMalloc, cudaFree or allocating routine.  Its cross-CTA partial sums live in a
+ * fixed static device array of about 72 KB (held by every GPU that loads the library until the
+ * process exits), which limits the deflation rank to c <= 8: larger c returns ISIRA_ERR_LIMIT.
+ * All calls share that array: calls whose work overlaps on the GPU race and must be serialised.
+ * The first call on each device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture on the device.
+ * Ordered on `stream`; synchronises it before returning. */
+ISIRA_API isira_status isira_apply_operator_noalloc(int64_t n, int64_t nnz, const int64_t* d_row_ptr,
+                                                    const int32_t* d_col_idx, int64_t trim, int precision,
+                                                    double sigma, double delta, int drop_rank1, int c,
+                                                    const double* d_V, const void* d_x, void* d_y, void* stream);
 
 #ifdef __cplusplus
 }

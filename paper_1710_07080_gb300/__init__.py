@@ -23,13 +23,14 @@ ISIRA_ERR_NO_CONVERGENCE = 4
 ISIRA_ERR_CUDA = 5
 ISIRA_ERR_OOM = 6
 ISIRA_ERR_NOT_SOLVED = 7
+ISIRA_ERR_LIMIT = 8
 
 ISIRA_FP64 = 0
 ISIRA_MIXED = 1
 
 EXPORTED = ["isira_default_opts", "isira_error_string", "isira_create", "isira_solve", "isira_eigpairs",
             "isira_get_stats", "isira_set_profiling", "isira_destroy", "isira_apply_operator",
-            "isira_inner_solve", "isira_sym_eig"]
+            "isira_inner_solve", "isira_sym_eig", "isira_apply_operator_noalloc"]
 
 
 class isira_opts(C.Structure):
@@ -80,6 +81,8 @@ def _load() -> C.CDLL:
     lib.isira_inner_solve.restype = I
     lib.isira_sym_eig.argtypes = [I, P, P, P, P]
     lib.isira_sym_eig.restype = I
+    lib.isira_apply_operator_noalloc.argtypes = [I64, I64, P, P, I64, I, D, D, I, I, P, P, P, P]
+    lib.isira_apply_operator_noalloc.restype = I
     return lib
 
 
@@ -232,6 +235,23 @@ def sym_eig(H):
     S = torch.empty((k, k), dtype=torch.float64, device=H.device)
     check(lib.isira_sym_eig(k, _ptr(Hc), _ptr(th), _ptr(S), _stream_ptr()), "isira_sym_eig")
     return th, S.t()                 # S was written column-major
+
+
+def apply_operator_noalloc(row_ptr, col_idx, x, trim: int, sigma: float = 0.0, delta: float = 0.0, V=None,
+                           drop_rank1: bool = False, y=None, stream=None):
+    """Handle-free operator apply that allocates no device memory inside the library (see
+    isira_apply_operator_noalloc in include/isira.h).  Pass y to avoid the output allocation here too."""
+    import torch
+    prec = ISIRA_MIXED if x.dtype == torch.float32 else ISIRA_FP64
+    if y is None:
+        y = torch.empty_like(x)
+    c = 0 if V is None else V.shape[1]
+    Vc = None if V is None else V.t().contiguous()
+    check(lib.isira_apply_operator_noalloc(row_ptr.numel() - 1, col_idx.numel(), _ptr(row_ptr), _ptr(col_idx),
+                                           int(trim), prec, float(sigma), float(delta), int(bool(drop_rank1)), c,
+                                           _ptr(Vc), _ptr(x), _ptr(y), _stream_ptr(stream)),
+          "isira_apply_operator_noalloc")
+    return y
 
 
 def solve(row_ptr, col_idx, k: int, sigma: float = 0.0, tol: float | None = None, rel_tol: float = 1e-8, u0=None,

@@ -346,6 +346,7 @@ const char* isira_error_string(isira_status s) {
         case ISIRA_ERR_CUDA: return "CUDA runtime error";
         case ISIRA_ERR_OOM: return "out of memory";
         case ISIRA_ERR_NOT_SOLVED: return "no successful solve on this handle";
+        case ISIRA_ERR_LIMIT: return "request exceeds the fixed scratch of the allocation-free entry point (c <= 8)";
     }
     return "unknown status";
 }
