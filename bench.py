@@ -51,7 +51,24 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--single-solve", choices=["fp64", "mixed"], default=None,
                    help="create one solver and run one solve, nothing else (for profiler captures)")
+    p.add_argument("--graph-cache", default=None,
+                   help="directory to keep the generated graph in (.npz), reused by later runs")
     return p.parse_args()
+
+
+def load_workload(args):
+    import numpy as np
+    import synthgraphs as sg
+    if args.graph_cache:
+        path = os.path.join(args.graph_cache, f"{args.workload}.npz")
+        if os.path.exists(path):
+            z = np.load(path)
+            return sg.Graph(z["row_ptr"], z["col_idx"], args.workload)
+        g = sg.workload(args.workload)
+        os.makedirs(args.graph_cache, exist_ok=True)
+        np.savez(path, row_ptr=g.row_ptr, col_idx=g.col_idx)
+        return g
+    return sg.workload(args.workload)
 
 
 def env_rank():
@@ -177,40 +194,61 @@ def oracle_sample(g, k, tol_abs, u0, max_outer):
     return time.perf_counter() - t0, st
 
 
-def oracle_outer_steps_reference(name):
+def oracle_full_counts(name):
+    """Work counts of the oracle's full run on this workload (written by tests/golden/make_golden.py)."""
     path = os.path.join(ROOT, "tests", "golden", f"{name}_bench.json")
     if os.path.exists(path):
-        return int(json.load(open(path))["oracle_stats"]["outer_steps"]), "oracle full run (tests/golden)"
-    return None, None
+        return json.load(open(path))["oracle_stats"]
+    return None
+
+
+def project_oracle(st_sample, full):
+    """Seconds of the oracle's full run, projected from a sample's per-unit costs: seconds per
+    recomputed W column (line 4), per inner MINRES iteration (line 17) and per outer step (the
+    rest), times the full run's counts of those units."""
+    per_col = st_sample["sec_w"] / max(1, st_sample["w_columns"])
+    per_it = st_sample["sec_inner"] / max(1, st_sample["inner_iters"])
+    rest = st_sample["sec_total"] - st_sample["sec_w"] - st_sample["sec_inner"]
+    per_step = rest / max(1, st_sample["outer_steps"])
+    return per_col * full["w_columns"] + per_it * full["inner_iters"] + per_step * full["outer_steps"]
+
+
+SAMPLE_STEPS = 6
+
+
+def sample_text(st, full):
+    return (f"first {st['outer_steps']} outer steps of Algorithm 2 (FP64 oracle, tau_inner 1e-3, 1 thread) on the "
+            f"same graph: {st['sec_w'] / max(1, st['w_columns']) * 1e3:.1f} ms per recomputed W column, "
+            f"{st['sec_inner'] / max(1, st['inner_iters']) * 1e3:.1f} ms per inner iteration; projected with the "
+            f"unit counts of the oracle's full run ({full['w_columns']} W columns, {full['inner_iters']} inner "
+            f"iterations, {full['outer_steps']} outer steps; tests/golden)")
 
 
 def run_reference(args):
-    import numpy as np  # noqa: F401
     import synthgraphs as sg
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    g = sg.workload(args.workload)
+    g = load_workload(args)
     normL = 2.0 * float(g.degrees.max())
     tol = args.rel_tol * normL
     u0 = sg.start_vector(g.n, 1)
-    S = 2
-    times = []
+    full = oracle_full_counts(args.workload)
+    if full is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no oracle work counts for this workload"}))
+        return
+    values, st = [], None
     for i in range(args.warmup + args.steps):
-        dt, st = oracle_sample(g, args.k, tol, u0, S)
+        _, st = oracle_sample(g, args.k, tol, u0, SAMPLE_STEPS)
         if i >= args.warmup:
-            times.append(dt / max(1, st["outer_steps"]))
-    n_outer, src = oracle_outer_steps_reference(args.workload)
-    per_step = statistics.mean(times)
-    value = per_step * n_outer if n_outer else None
-    sample = (f"first {S} outer steps of Algorithm 2 (FP64 oracle, tau_inner 1e-3) on the full workload, "
-              f"{per_step:.3f} s per outer step, projected to {n_outer} outer steps ({src}); early steps "
-              f"have a small search space, so the projection understates the oracle's full time")
+            values.append(project_oracle(st, full))
+    value = statistics.mean(values)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.workload, g, args.k, args.rel_tol),
-            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": sample_text(st, full)},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -247,7 +285,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    g = sg.workload(args.workload)
+    g = load_workload(args)
     n, Z, k = g.n, g.nnz, args.k
     normL = 2.0 * float(g.degrees.max())
     tol = args.rel_tol * normL
@@ -372,15 +410,11 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        S = 2
-        dt, st = oracle_sample(g, k, tol, u0_h.numpy(), S)
-        per = dt / max(1, st["outer_steps"])
-        n_outer = st64[-1]["outer_steps"]
-        line["cpu_baseline"] = {
-            "value": per * n_outer, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"first {st['outer_steps']} outer steps of Algorithm 2 (FP64 oracle, tau_inner 1e-3, 1 thread) "
-                       f"on the same graph: {per:.3f} s per outer step, projected to the {n_outer} outer steps of the "
-                       f"GPU FP64 run; early steps have a small search space, so this understates the oracle")}
+        full = oracle_full_counts(args.workload)
+        dt, st = oracle_sample(g, k, tol, u0_h.numpy(), SAMPLE_STEPS)
+        if full is not None:
+            line["cpu_baseline"] = {"value": project_oracle(st, full), "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": sample_text(st, full), "sample_seconds": dt}
     if rank == 0:
         print(json.dumps(line), flush=True)
     s64.close()

@@ -84,7 +84,8 @@ typedef struct {
     double delta;             /* the deflation constant actually used */
     double norm_L;            /* Gershgorin bound 2 * max degree, used to scale residuals */
     int spmv_lanes;           /* chosen light-row lanes per row */
-    int n_heavy_rows, n_medium_rows;
+    int64_t n_long_rows;      /* rows above the light-row degree threshold */
+    int64_t n_work_items;     /* warp work items the long rows are cut into */
     int n_locked;             /* eigenpairs locked by the last solve */
     int outer_steps;          /* Algorithm 2 while-loop iterations */
     int restarts, breakdowns;

@@ -46,7 +46,8 @@ class Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("n_locked", C.c_int), ("outer_steps", C.c_int),
                 ("inner_iters", C.c_longlong), ("restarts", C.c_int), ("breakdowns", C.c_int),
-                ("trim", C.c_int64), ("delta", C.c_double)]
+                ("trim", C.c_int64), ("delta", C.c_double), ("w_columns", C.c_longlong),
+                ("sec_w", C.c_double), ("sec_inner", C.c_double), ("sec_total", C.c_double)]
 
 
 def _load():

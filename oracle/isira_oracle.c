@@ -18,11 +18,19 @@
  *     replaces it;
  *   - H_k is symmetrised, (H + H^T)/2, before its eigen-decomposition.
  */
+#define _POSIX_C_SOURCE 199309L
 #include "isira_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
+
+static double wall_seconds(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 /* ---------------------------------------------------------------- small helpers */
 
@@ -426,6 +434,7 @@ static void rotate_basis(int64_t n, double* X, int k, const double* S, int c0, i
 int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, const or_params* p,
              double* lam, double* Vout, or_stats* st) {
     memset(st, 0, sizeof(*st));
+    const double t_start = wall_seconds();
     int d = p->d, m = p->m, q = p->q;
     if (n < 3 || d < 1 || d > n - 2 || q < d || m <= q || m < 2) { st->status = 2; return 2; }
 
@@ -465,6 +474,8 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
             if (st->outer_steps >= p->max_outer) { status = 1; goto finish; }
             st->outer_steps++;
             /* line 4: W_k = (L + delta V V^T) U_k,  H_k = U_k^T W_k */
+            const double t_w = wall_seconds();
+            st->w_columns += k;
             for (int a = 0; a < k; ++a) {
                 double* ua = U + (int64_t)a * n;
                 double* wa = W + (int64_t)a * n;
@@ -480,6 +491,7 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
                     double h = 0.5 * (H[a + (size_t)b * k] + H[b + (size_t)a * k]);
                     H[a + (size_t)b * k] = H[b + (size_t)a * k] = h;
                 }
+            st->sec_w += wall_seconds() - t_w;
             /* line 6: all eigenpairs of H_k, ascending, unit vectors */
             or_sym_eig(k, H, theta, S, 100);
             /* line 7: r = W_k s1 - theta1 U_k s1 */
@@ -510,9 +522,11 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
                 }
                 /* line 17: trimmed solve (Eq. 2.4 / 2.14) and the back-map (Eq. 2.5) */
                 double rr;
+                const double t_in = wall_seconds();
                 int its = or_inner_solve(n, rp, ci, trim, sigma, delta, V, c, p->drop_rank1, r,
                                          p->tau_inner, p->max_inner, z, &rr);
                 st->inner_iters += its;
+                st->sec_inner += wall_seconds() - t_in;
                 /* line 18: orthonormalise against U_k and V */
                 if (orthonormalize(n, U, k, V, c, z, p->seed, &st->breakdowns) < 0) { status = 1; goto finish; }
                 memcpy(U + (int64_t)k * n, z, sizeof(double) * (size_t)n);   /* line 19 */
@@ -540,6 +554,7 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
         }
     }
 finish:
+    st->sec_total = wall_seconds() - t_start;
     st->status = status;
     st->n_locked = c;
     free(U); free(W); free(H); free(S); free(theta); free(y); free(r); free(z); free(col); free(vtu);

@@ -85,6 +85,10 @@ typedef struct {
     int breakdowns;
     int64_t trim;
     double delta;
+    long long w_columns;   /* columns of W_k recomputed (line 4), summed over outer steps */
+    double sec_w;          /* wall seconds in line 4 (W_k, H_k) */
+    double sec_inner;      /* wall seconds in line 17 (inner solves) */
+    double sec_total;      /* wall seconds of the whole call */
 } or_stats;
 
 /* Algorithm 2.  u0: unit n-vector orthogonal to 1 (the k0 = 1 start basis).

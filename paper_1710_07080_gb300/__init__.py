@@ -43,7 +43,7 @@ class isira_opts(C.Structure):
 class isira_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("trim_index", C.c_int64), ("max_degree", C.c_int64),
                 ("delta", C.c_double), ("norm_L", C.c_double), ("spmv_lanes", C.c_int),
-                ("n_heavy_rows", C.c_int), ("n_medium_rows", C.c_int), ("n_locked", C.c_int),
+                ("n_long_rows", C.c_int64), ("n_work_items", C.c_int64), ("n_locked", C.c_int),
                 ("outer_steps", C.c_int), ("restarts", C.c_int), ("breakdowns", C.c_int),
                 ("inner_iters", C.c_longlong), ("inner_solves", C.c_longlong), ("spmv_launches", C.c_longlong),
                 ("solve_ms", C.c_double), ("inner_phase1_ms", C.c_double), ("inner_phase1_timed", C.c_longlong),

@@ -4,11 +4,9 @@
 //    writes its partial sums, the block that arrives last adds them in a fixed
 //    order, so a reduction needs no second launch and gives the same bits on
 //    every run;
-//  * a three-tier CSR row scheduler for skewed (power-law) degrees: rows of
-//    degree > kHeavyDeg get a whole CTA, rows above the light threshold get one
-//    warp, and all other rows are processed in tiles of 32 consecutive rows by
-//    G lanes per row, so that the per-row epilogue runs with one lane per row and
-//    coalesced vector accesses;
+//  * a CSR row scheduler for skewed (power-law) degrees (see "row scheduler" below):
+//    light rows in tiles of 32 consecutive rows with G lanes per row, longer rows cut
+//    into equal-size warp work items;
 //  * SplitMix64 (Vigna), the counter-based generator of replacement vectors.
 #pragma once
 #include <cuda_runtime.h>
@@ -20,7 +18,6 @@ constexpr int kThreads = 256;         // threads per CTA for every kernel here
 constexpr int kWarps = kThreads / 32;
 constexpr int kCMax = 32;             // max locked vectors (deflation rank) supported
 constexpr int kMMax = 64;             // max search-space dimension
-constexpr int kHeavyDeg = 4096;       // rows above this degree get a whole CTA
 constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------ host-visible status
@@ -114,65 +111,109 @@ __device__ __forceinline__ T block_sum0(T v) {
 }
 
 // ------------------------------------------------------------------ row scheduler
-// Grid layout of an SpMV-style launch: [heavy CTAs][medium CTAs][light CTAs].
+// Grid layout of an SpMV-style launch: [long-row CTAs][light-row CTAs].
+//  * light rows (degree <= light_deg) are processed in tiles of 32 consecutive rows by one
+//    warp, G lanes per row, so the per-row epilogue runs with one lane per row and coalesced
+//    vector accesses;
+//  * every longer row is cut into work items of at most kItemNnz stored entries, one warp per
+//    item; a row with several items gets its sum from the warp that finishes its last item,
+//    which adds the items' partial sums in item order (deterministic) and runs the epilogue.
+// The row `skip` (the trimmed vertex, or -1) is never gathered: its epilogue runs from the
+// light tiles with a zero sum.
+constexpr int kItemNnz = 1024;
+
 struct RowSched {
     const int64_t* __restrict__ rp;
     const int32_t* __restrict__ ci;
     int64_t n;
-    const int32_t* __restrict__ heavy;   // rows of degree > kHeavyDeg, ascending
-    const int32_t* __restrict__ medium;  // rows of degree in (light_deg, kHeavyDeg], ascending
-    int n_heavy, n_medium;
-    int medium_blocks, light_blocks;
+    const int32_t* __restrict__ item_row;   // row of each work item (rows ascending)
+    const int32_t* __restrict__ item_k;     // position of the item within its row
+    void* item_partial;                     // one partial sum per item (type of the launch)
+    unsigned* item_count;                   // arrival counters, used at each row's first item
+    int n_items;
+    int item_blocks, light_blocks;
     int light_deg;
-    __host__ __device__ int grid() const { return n_heavy + medium_blocks + light_blocks; }
+    __host__ __device__ int grid() const { return item_blocks + light_blocks; }
 };
 
-// Calls epi(row, degree, sum_{c in N(row)} x[c]) exactly once for every row 0..n-1.
-// G = lanes per light row (1, 2, 4, 8, 16 or 32).
+// Calls epi(row, degree, sum_{c in N(row)} x[c]) exactly once for every row 0..n-1 (with a
+// zero sum for row `skip`).  G = lanes per light row (1, 2, 4, 8, 16 or 32).
 template <typename T, int G, class Epi>
-__device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* __restrict__ x, Epi& epi) {
+__device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* __restrict__ x, Epi& epi,
+                                                    int64_t skip) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int b = blockIdx.x;
-    if (b < S.n_heavy) {                                   // one CTA per heavy row
-        const int64_t r = S.heavy[b];
-        const int64_t beg = S.rp[r], end = S.rp[r + 1];
-        T s0 = 0, s1 = 0;
-        int64_t e = beg + threadIdx.x;
-        for (; e + blockDim.x < end; e += 2 * blockDim.x) {
-            s0 += __ldg(x + __ldg(S.ci + e));
-            s1 += __ldg(x + __ldg(S.ci + e + blockDim.x));
-        }
-        if (e < end) s0 += __ldg(x + __ldg(S.ci + e));
-        T s = block_sum0(s0 + s1);
-        if (threadIdx.x == 0) epi(r, end - beg, s);
-        return;
-    }
-    b -= S.n_heavy;
-    if (b < S.medium_blocks) {                             // one warp per medium row
-        for (int64_t i = (int64_t)b * kWarps + warp; i < S.n_medium; i += (int64_t)S.medium_blocks * kWarps) {
-            const int64_t r = S.medium[i];
-            const int64_t beg = S.rp[r], end = S.rp[r + 1];
-            T s0 = 0, s1 = 0;
+    if (b < S.item_blocks) {                               // long rows: one warp per item
+        // Finished rows are collected one per lane and their epilogues run 32 at a time, so the
+        // epilogue arithmetic uses every lane of the warp.
+        T* part = static_cast<T*>(S.item_partial);
+        int64_t my_row = -1, my_deg = 0;
+        T my_sum = 0;
+        int nb = 0;                                        // rows collected (warp-uniform)
+        for (int64_t it = (int64_t)b * kWarps + warp; it < S.n_items; it += (int64_t)S.item_blocks * kWarps) {
+            const int64_t r = S.item_row[it];
+            if (r == skip) continue;
+            const int kpos = S.item_k[it];
+            const int64_t rb = S.rp[r], re = S.rp[r + 1];
+            const int64_t beg = rb + (int64_t)kpos * kItemNnz;
+            const int64_t end = beg + kItemNnz < re ? beg + kItemNnz : re;
+            T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
             int64_t e = beg + lane;
-            for (; e + 32 < end; e += 64) {
-                s0 += __ldg(x + __ldg(S.ci + e));
-                s1 += __ldg(x + __ldg(S.ci + e + 32));
+            for (; e + 96 < end; e += 128) {
+                const int32_t c0 = __ldg(S.ci + e), c1 = __ldg(S.ci + e + 32);
+                const int32_t c2 = __ldg(S.ci + e + 64), c3 = __ldg(S.ci + e + 96);
+                s0 += __ldg(x + c0);
+                s1 += __ldg(x + c1);
+                s2 += __ldg(x + c2);
+                s3 += __ldg(x + c3);
             }
-            if (e < end) s0 += __ldg(x + __ldg(S.ci + e));
-            T s = warp_sum(s0 + s1);
-            if (lane == 0) epi(r, end - beg, s);
+            for (; e < end; e += 32) s0 += __ldg(x + __ldg(S.ci + e));
+            T s = warp_sum((s0 + s1) + (s2 + s3));
+            const int nit = (int)((re - rb + kItemNnz - 1) / kItemNnz);
+            int done = 1;
+            if (nit > 1) {
+                // several items: the warp that finishes the row's last item adds all partials in order
+                int last = 0;
+                if (lane == 0) {
+                    const int64_t first = it - kpos;
+                    part[it] = s;
+                    __threadfence();
+                    const unsigned prev = atomicAdd(S.item_count + first, 1u);
+                    if (prev == (unsigned)(nit - 1)) {
+                        __threadfence();
+                        T tot = 0;
+                        for (int q = 0; q < nit; ++q) tot += __ldcg(part + first + q);
+                        S.item_count[first] = 0u;
+                        s = tot;
+                        last = 1;
+                    }
+                }
+                done = __shfl_sync(kFull, last, 0);
+                s = __shfl_sync(kFull, s, 0);
+            }
+            if (done) {
+                if (lane == nb) { my_row = r; my_deg = re - rb; my_sum = s; }
+                if (++nb == 32) {
+                    epi(my_row, my_deg, my_sum);
+                    my_row = -1;
+                    nb = 0;
+                }
+            }
         }
+        if (my_row >= 0) epi(my_row, my_deg, my_sum);
         return;
     }
-    b -= S.medium_blocks;
+    b -= S.item_blocks;
     constexpr int RPS = 32 / G;                            // rows per sub-pass
     const int64_t ntiles = (S.n + 31) >> 5;
     for (int64_t tile = (int64_t)b * kWarps + warp; tile < ntiles; tile += (int64_t)S.light_blocks * kWarps) {
         const int64_t row = tile * 32 + lane;
         const bool valid = row < S.n;
-        const int64_t beg = valid ? S.rp[row] : 0;
-        const int64_t end = valid ? S.rp[row + 1] : 0;
-        const int light = valid && (end - beg) <= S.light_deg;
+        int64_t beg = valid ? S.rp[row] : 0;
+        int64_t end = valid ? S.rp[row + 1] : 0;
+        const int64_t deg = end - beg;
+        const int light = valid && (deg <= S.light_deg || row == skip);
+        if (row == skip) end = beg;                        // the skipped row gathers nothing
         T mine = 0;
 #pragma unroll
         for (int sub = 0; sub < G; ++sub) {
@@ -180,18 +221,24 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
             const int64_t sb = __shfl_sync(kFull, beg, src);
             const int64_t se = __shfl_sync(kFull, end, src);
             const int sl = __shfl_sync(kFull, light, src);
-            T s = 0;
+            T s0 = 0, s1 = 0;
             if (sl) {
                 int64_t e = sb + (lane % G);
-                for (; e + G < se; e += 2 * G) s += __ldg(x + __ldg(S.ci + e)) + __ldg(x + __ldg(S.ci + e + G));
-                if (e < se) s += __ldg(x + __ldg(S.ci + e));
+                for (; e + 3 * G < se; e += 4 * G) {
+                    const int32_t c0 = __ldg(S.ci + e), c1 = __ldg(S.ci + e + G);
+                    const int32_t c2 = __ldg(S.ci + e + 2 * G), c3 = __ldg(S.ci + e + 3 * G);
+                    s0 += __ldg(x + c0) + __ldg(x + c1);
+                    s1 += __ldg(x + c2) + __ldg(x + c3);
+                }
+                for (; e < se; e += G) s0 += __ldg(x + __ldg(S.ci + e));
             }
+            T s = s0 + s1;
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
             const T t = __shfl_sync(kFull, s, (lane % RPS) * G);
             if (lane / RPS == sub) mine = t;
         }
-        if (light) epi(row, end - beg, mine);
+        if (light) epi(row, deg, mine);
     }
 }
 

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
     for (int t = 0; t < 1 + NC; ++t) epi.acc[t] = T(0);
     __syncthreads();
 
-    for_each_row_gather<T, G>(a.rs, epi.zc, epi);
+    for_each_row_gather<T, G>(a.rs, epi.zc, epi, a.trim);
 
     if (block_partials_arrive<T, 1 + NC>(epi.acc, 1 + a.c, a.partial, a.pstride, a.counter)) {
         last_block_sum(a.partial, a.pstride, gridDim.x, 1 + a.c, red, a.counter);

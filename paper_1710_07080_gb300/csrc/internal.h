@@ -96,8 +96,9 @@ void outer_true_residual(const OuterArgs& a, int d, const double* lam_dev, doubl
 void outer_laplacian(const OuterArgs& a, const double* x, double* y, int lanes, cudaStream_t s);
 
 // setup
-struct DegreeInfo { int64_t max_degree, argmax; int64_t n_heavy, n_medium; };
-void setup_degrees(const int64_t* rp, int64_t n, int light_deg, int32_t* heavy, int32_t* medium,
+struct DegreeInfo { int64_t max_degree, argmax; int64_t n_long, n_items; };
+// Counts (and, when item_row is given and n_items <= cap, fills) the long-row work items.
+void setup_degrees(const int64_t* rp, int64_t n, int light_deg, int32_t* item_row, int32_t* item_k, int64_t cap,
                    int64_t* scratch, DegreeInfo* out, cudaStream_t s);
 int validate_csr(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int* d_flag, cudaStream_t s);
 

@@ -46,136 +46,228 @@ void outer_residual(const OuterArgs& a, int k, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ symmetric eigensolver (line 6)
-// Parallel cyclic Jacobi with the round-robin ordering: in each of K-1 rounds the
-// K indices (K = k rounded up to even) form K/2 disjoint pairs, whose rotations are
-// applied together (rows, then columns).  The 2x2 symmetric Schur rotation is the
-// one of Golub & Van Loan Sec. 8.5.2.  Ascending order, sign rule: largest-magnitude
-// entry of each eigenvector positive (first index on ties).
+// All eigenpairs of the small symmetric H_k in one CTA.  One SM's FP64 pipe is slow on this
+// part, so the bulk of the work runs in FP32 and FP64 only finishes it:
+//   1. parallel cyclic Jacobi in FP32 (round-robin ordering: in each of K-1 rounds the K
+//      indices form K/2 disjoint pairs, rotated together; K = k rounded up to even) until the
+//      off-diagonal norm is ~1e-6 of the matrix norm, accumulating Q;
+//   2. in FP64: Q re-orthonormalised by two Newton-Schulz steps Q <- Q (3I - Q^T Q) / 2,
+//      then B = Q^T H Q;
+//   3. FP64 Jacobi sweeps on the nearly diagonal B until every off-diagonal entry is
+//      negligible against its diagonal entries, accumulating into Q.
+// Each rotation is the symmetric 2x2 Schur rotation of Golub & Van Loan Sec. 8.5.2; a round
+// applies A <- J^T A J and Q <- Q J in one pass (every new entry from at most four old ones).
+// Output: eigenvalues ascending, unit eigenvectors signed so that the entry of largest
+// magnitude (first index on ties) is positive.
 
 constexpr int kEigLd = kMMax + 1;
 
-__global__ void __launch_bounds__(kThreads) k_sym_eig(const double* H, int ldh, int k, double* theta, double* S,
-                                                      int lds, HostStatus* hs) {
-    extern __shared__ double eig_sm[];
-    double* A = eig_sm;                    // [kMMax][kEigLd]
-    double* Q = eig_sm + kMMax * kEigLd;   // [kMMax][kEigLd]
-    __shared__ double cs_[kMMax / 2], sn_[kMMax / 2];
-    __shared__ int pp_[kMMax / 2], qq_[kMMax / 2];
-    __shared__ double offsum[kWarps];
-    __shared__ int perm[kMMax];
-    const int K = k + (k & 1);
-    const int tid = threadIdx.x;
-    for (int idx = tid; idx < K * K; idx += blockDim.x) {
+template <typename T>
+struct JacobiSmem {
+    T* A; T* A2; T* Q; T* Q2;       // [kMMax][kEigLd] each, column-major
+    int* partner; T* alpha; T* beta; int* zero_pq;   // per index
+    double* red;                    // [kWarps]
+};
+
+template <typename T>
+__device__ double jacobi_off(const T* A, int K, double* red) {
+    double off = 0.0;
+    for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
         const int i = idx % K, j = idx / K;
-        A[i + j * kEigLd] = (i < k && j < k) ? 0.5 * (H[i + j * ldh] + H[j + i * ldh]) : 0.0;
-        Q[i + j * kEigLd] = (i == j) ? 1.0 : 0.0;
+        if (i < j) off += 2.0 * (double)A[i + j * kEigLd] * (double)A[i + j * kEigLd];
     }
+    off = warp_sum(off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off;
     __syncthreads();
-    int sweeps = -1;
-    for (int sw = 0; sw < 60 && K >= 2; ++sw) {
-        double off = 0.0;
-        for (int idx = tid; idx < K * K; idx += blockDim.x) {
-            const int i = idx % K, j = idx / K;
-            if (i != j) off += A[i + j * kEigLd] * A[i + j * kEigLd];
-        }
-        off = warp_sum(off);
-        if ((tid & 31) == 0) offsum[tid >> 5] = off;
-        __syncthreads();
-        double tot = 0.0;
-        for (int w = 0; w < kWarps; ++w) tot += offsum[w];
-        __syncthreads();
-        if (tot == 0.0) { sweeps = sw; break; }
+    double tot = 0.0;
+    for (int w = 0; w < kWarps; ++w) tot += red[w];
+    __syncthreads();
+    return tot;
+}
+
+template <typename T>
+__device__ double jacobi_frob(const T* A, int K, double* red) {
+    double f = 0.0;
+    for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
+        const int i = idx % K, j = idx / K;
+        f += (double)A[i + j * kEigLd] * (double)A[i + j * kEigLd];
+    }
+    f = warp_sum(f);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < kWarps; ++w) tot += red[w];
+    __syncthreads();
+    return tot;
+}
+
+// Sweeps until off(A)^2 <= stop2 (or, with drop_negligible, until all entries are dropped or
+// rotated to zero).  A and Q ping-pong between (A, A2) and (Q, Q2); returns the sweeps used
+// (-1: no convergence) and leaves the current buffers in sm.A / sm.Q.
+template <typename T>
+__device__ int jacobi_sweeps(JacobiSmem<T>& sm, int K, int max_sweeps, double stop2, bool drop_negligible) {
+    const int tid = threadIdx.x;
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        const double off = jacobi_off(sm.A, K, sm.red);
+        if (off == 0.0 || off <= stop2) return sw;
         for (int rnd = 0; rnd < K - 1; ++rnd) {
             if (tid < K / 2) {
                 int p, q;
                 if (tid == 0) { p = K - 1; q = rnd; }
                 else { p = (rnd + tid) % (K - 1); q = (rnd - tid + (K - 1)) % (K - 1); }
-                if (p > q) { int t = p; p = q; q = t; }
-                double c = 1.0, s = 0.0;
-                const double apq = A[p + q * kEigLd];
-                if (apq != 0.0) {
-                    const double app = A[p + p * kEigLd], aqq = A[q + q * kEigLd];
-                    const bool negligible = sw > 2 && fabs(app) + 100.0 * fabs(apq) == fabs(app) &&
-                                            fabs(aqq) + 100.0 * fabs(apq) == fabs(aqq);
-                    if (!negligible) {
-                        const double tau = (aqq - app) / (2.0 * apq);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                if (p > q) { const int t = p; p = q; q = t; }
+                T c = T(1), s = T(0);
+                int zero = 0;
+                const T apq = sm.A[p + q * kEigLd];
+                if (apq != T(0)) {
+                    const T app = sm.A[p + p * kEigLd], aqq = sm.A[q + q * kEigLd];
+                    const bool negligible = drop_negligible && fabs((double)app) + 100.0 * fabs((double)apq) == fabs((double)app) &&
+                                            fabs((double)aqq) + 100.0 * fabs((double)apq) == fabs((double)aqq);
+                    if (negligible) {
+                        zero = 1;
+                    } else {
+                        const T tau = (aqq - app) / (T(2) * apq);
+                        const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                        c = T(1) / sqrt(T(1) + t * t);
                         s = t * c;
+                        zero = 1;
                     }
                 }
-                cs_[tid] = c; sn_[tid] = s; pp_[tid] = p; qq_[tid] = q;
+                // new column p = c col_p - s col_q, new column q = s col_p + c col_q
+                sm.partner[p] = q; sm.alpha[p] = c; sm.beta[p] = -s; sm.zero_pq[p] = zero;
+                sm.partner[q] = p; sm.alpha[q] = c; sm.beta[q] = s; sm.zero_pq[q] = zero;
             }
             __syncthreads();
-            // rows p, q of A: A <- J^T A
-            for (int idx = tid; idx < (K / 2) * K; idx += blockDim.x) {
-                const int pr = idx / K, col = idx % K;
-                const double c = cs_[pr], s = sn_[pr];
-                if (s == 0.0) continue;
-                const int p = pp_[pr], q = qq_[pr];
-                const double ap = A[p + col * kEigLd], aq = A[q + col * kEigLd];
-                A[p + col * kEigLd] = c * ap - s * aq;
-                A[q + col * kEigLd] = s * ap + c * aq;
-            }
-            __syncthreads();
-            // columns p, q of A and of Q: A <- A J, Q <- Q J
-            for (int idx = tid; idx < (K / 2) * K; idx += blockDim.x) {
-                const int pr = idx / K, row = idx % K;
-                const double c = cs_[pr], s = sn_[pr];
-                const int p = pp_[pr], q = qq_[pr];
-                if (s == 0.0) {
-                    if (row == 0 && A[p + q * kEigLd] != 0.0 && c == 1.0) {
-                        // negligible entry: drop it (both triangles)
-                        A[p + q * kEigLd] = 0.0;
-                        A[q + p * kEigLd] = 0.0;
+            // A2 = J^T A J (upper triangle computed, mirrored), Q2 = Q J
+            for (int idx = tid; idx < K * K; idx += blockDim.x) {
+                const int i = idx % K, j = idx / K;
+                const int pj = sm.partner[j];
+                const T aj = sm.alpha[j], bj = sm.beta[j];
+                if (i <= j) {
+                    const int pi = sm.partner[i];
+                    const T ai = sm.alpha[i], bi = sm.beta[i];
+                    T v;
+                    if (pi == j && sm.zero_pq[i]) {
+                        v = T(0);
+                    } else {
+                        v = ai * (aj * sm.A[i + j * kEigLd] + bj * sm.A[i + pj * kEigLd]) +
+                            bi * (aj * sm.A[pi + j * kEigLd] + bj * sm.A[pi + pj * kEigLd]);
                     }
-                    continue;
+                    sm.A2[i + j * kEigLd] = v;
+                    sm.A2[j + i * kEigLd] = v;
                 }
-                const double ap = A[row + p * kEigLd], aq = A[row + q * kEigLd];
-                A[row + p * kEigLd] = c * ap - s * aq;
-                A[row + q * kEigLd] = s * ap + c * aq;
-                const double qp = Q[row + p * kEigLd], qq = Q[row + q * kEigLd];
-                Q[row + p * kEigLd] = c * qp - s * qq;
-                Q[row + q * kEigLd] = s * qp + c * qq;
+                sm.Q2[i + j * kEigLd] = aj * sm.Q[i + j * kEigLd] + bj * sm.Q[i + pj * kEigLd];
             }
             __syncthreads();
-            if (tid < K / 2 && sn_[tid] != 0.0) {
-                const int p = pp_[tid], q = qq_[tid];
-                A[p + q * kEigLd] = 0.0;
-                A[q + p * kEigLd] = 0.0;
-            }
-            __syncthreads();
+            T* t = sm.A; sm.A = sm.A2; sm.A2 = t;
+            t = sm.Q; sm.Q = sm.Q2; sm.Q2 = t;
         }
     }
-    if (K < 2) sweeps = 0;
-    if (tid == 0) {
-        // ascending selection order over the k real indices (stable on ties)
-        for (int i = 0; i < k; ++i) perm[i] = i;
-        for (int i = 0; i < k; ++i) {
-            int best = i;
-            for (int j = i + 1; j < k; ++j)
-                if (A[perm[j] + perm[j] * kEigLd] < A[perm[best] + perm[best] * kEigLd]) best = j;
-            const int t = perm[best];
-            for (int j = best; j > i; --j) perm[j] = perm[j - 1];
-            perm[i] = t;
-        }
-        if (hs) hs->eig_sweeps = sweeps;
+    return jacobi_off(sm.A, K, sm.red) == 0.0 ? max_sweeps : -1;
+}
+
+// C = op(X) * Y for K-by-K blocks in shared memory (ld kEigLd); op = transpose if tx.
+__device__ void small_gemm(const double* X, const double* Y, double* C, int K, bool tx) {
+    for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
+        const int i = idx % K, j = idx / K;
+        double s = 0.0;
+        if (tx) for (int r = 0; r < K; ++r) s += X[r + i * kEigLd] * Y[r + j * kEigLd];
+        else for (int r = 0; r < K; ++r) s += X[i + r * kEigLd] * Y[r + j * kEigLd];
+        C[i + j * kEigLd] = s;
     }
     __syncthreads();
-    if (tid < k) {
-        const int src = perm[tid];
-        theta[tid] = A[src + src * kEigLd];
-        int imax = 0;
-        for (int r = 1; r < k; ++r)
-            if (fabs(Q[r + src * kEigLd]) > fabs(Q[imax + src * kEigLd])) imax = r;
-        const double sg = Q[imax + src * kEigLd] < 0.0 ? -1.0 : 1.0;
-        for (int r = 0; r < k; ++r) S[r + tid * lds] = sg * Q[r + src * kEigLd];
+}
+
+__global__ void __launch_bounds__(kThreads) k_sym_eig(const double* H, int ldh, int k, double* theta, double* S,
+                                                      int lds, HostStatus* hs) {
+    extern __shared__ double eig_sm[];
+    __shared__ int partner_[kMMax], zero_[kMMax], perm[kMMax];
+    __shared__ double alpha_[kMMax], beta_[kMMax], red_[kWarps];
+    __shared__ float alphaf_[kMMax], betaf_[kMMax];
+    const int K = k + (k & 1);
+    const int tid = threadIdx.x;
+    const int blk = kMMax * kEigLd;
+    double* D0 = eig_sm;            // H (kept)
+    double* D1 = eig_sm + blk;
+    double* D2 = eig_sm + 2 * blk;
+    double* D3 = eig_sm + 3 * blk;
+    // FP32 phase buffers alias D2, D3 (unused until the FP64 phase)
+    float* F = reinterpret_cast<float*>(D2);
+    JacobiSmem<float> fs{F, F + blk, F + 2 * blk, F + 3 * blk, partner_, alphaf_, betaf_, zero_, red_};
+    for (int idx = tid; idx < K * K; idx += blockDim.x) {
+        const int i = idx % K, j = idx / K;
+        const double h = (i < k && j < k) ? 0.5 * (H[i + j * ldh] + H[j + i * ldh]) : 0.0;
+        D0[i + j * kEigLd] = h;
+        fs.A[i + j * kEigLd] = (float)h;
+        fs.Q[i + j * kEigLd] = (i == j) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    int sweeps32 = 0, sweeps64 = 0;
+    if (K >= 2) {
+        const double frob = jacobi_frob(fs.A, K, red_);
+        sweeps32 = jacobi_sweeps<float>(fs, K, 40, 4e-12 * frob, false);
+        // FP64: Q from the FP32 rotations, re-orthonormalised (two Newton-Schulz steps)
+        for (int idx = tid; idx < K * K; idx += blockDim.x) {
+            const int i = idx % K, j = idx / K;
+            D1[i + j * kEigLd] = (double)fs.Q[i + j * kEigLd];
+        }
+        __syncthreads();
+        for (int it = 0; it < 2; ++it) {
+            small_gemm(D1, D1, D2, K, true);                       // G = Q^T Q
+            for (int idx = tid; idx < K * K; idx += blockDim.x) {   // G <- (3I - G) / 2
+                const int i = idx % K, j = idx / K;
+                D2[i + j * kEigLd] = ((i == j) ? 1.5 : 0.0) - 0.5 * D2[i + j * kEigLd];
+            }
+            __syncthreads();
+            small_gemm(D1, D2, D3, K, false);                      // Q <- Q G
+            for (int idx = tid; idx < K * K; idx += blockDim.x) {
+                const int i = idx % K, j = idx / K;
+                D1[i + j * kEigLd] = D3[i + j * kEigLd];
+            }
+            __syncthreads();
+        }
+        small_gemm(D0, D1, D2, K, false);                          // T = H Q
+        small_gemm(D1, D2, D3, K, true);                           // B = Q^T T
+        JacobiSmem<double> ds{D3, D2, D1, D0, partner_, alpha_, beta_, zero_, red_};
+        sweeps64 = jacobi_sweeps<double>(ds, K, 12, 0.0, true);
+        // eigenvalues on the diagonal of ds.A, eigenvectors in the columns of ds.Q
+        double* Af = ds.A;
+        double* Qf = ds.Q;
+        if (tid == 0) {
+            for (int i = 0; i < k; ++i) perm[i] = i;
+            for (int i = 0; i < k; ++i) {
+                int best = i;
+                for (int j = i + 1; j < k; ++j)
+                    if (Af[perm[j] + perm[j] * kEigLd] < Af[perm[best] + perm[best] * kEigLd]) best = j;
+                const int t = perm[best];
+                for (int j = best; j > i; --j) perm[j] = perm[j - 1];
+                perm[i] = t;
+            }
+            if (hs) hs->eig_sweeps = (sweeps32 < 0 || sweeps64 < 0) ? -1 : sweeps32 + sweeps64;
+        }
+        __syncthreads();
+        if (tid < k) {
+            const int src = perm[tid];
+            theta[tid] = Af[src + src * kEigLd];
+            int imax = 0;
+            for (int r = 1; r < k; ++r)
+                if (fabs(Qf[r + src * kEigLd]) > fabs(Qf[imax + src * kEigLd])) imax = r;
+            const double sg = Qf[imax + src * kEigLd] < 0.0 ? -1.0 : 1.0;
+            for (int r = 0; r < k; ++r) S[r + tid * lds] = sg * Qf[r + src * kEigLd];
+        }
+        return;
+    }
+    // k == 1
+    if (tid == 0) {
+        theta[0] = D0[0];
+        S[0] = 1.0;
+        if (hs) hs->eig_sweeps = 0;
     }
 }
 
 void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, int lds, HostStatus* hs,
                    cudaStream_t s) {
-    const int bytes = (int)(sizeof(double) * 2 * kMMax * kEigLd);
+    const int bytes = (int)(sizeof(double) * 4 * kMMax * kEigLd);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -355,7 +447,7 @@ __global__ void __launch_bounds__(kThreads) k_expand(OuterArgs a, int k) {
     e.w = a.W + (int64_t)k * a.ld;
     const double nz = a.dscratch[2];
     e.inv = nz > 0.0 ? 1.0 / nz : 0.0;
-    for_each_row_gather<double, G>(a.rs, a.Z, e);
+    for_each_row_gather<double, G>(a.rs, a.Z, e, -1);
 }
 
 struct LapEpi {
@@ -368,7 +460,7 @@ struct LapEpi {
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_laplacian(RowSched rs, const double* x, double* y) {
     LapEpi e{x, y};
-    for_each_row_gather<double, G>(rs, x, e);
+    for_each_row_gather<double, G>(rs, x, e, -1);
 }
 
 #define ISIRA_LANES_DISPATCH(lanes, F) \
@@ -485,7 +577,7 @@ __global__ void __launch_bounds__(kThreads) k_true_residual(OuterArgs a, const d
     e.v = v;
     e.lam = lam_dev[j];
     e.acc[0] = 0.0;
-    for_each_row_gather<double, G>(a.rs, v, e);
+    for_each_row_gather<double, G>(a.rs, v, e, -1);
     if (block_partials_arrive<double, 1>(e.acc, 1, a.partial, a.pstride, a.counter)) {
         last_block_sum(a.partial, a.pstride, gridDim.x, 1, red, a.counter);
         if (threadIdx.x == 0) out[j] = red[0];
@@ -505,20 +597,25 @@ void outer_true_residual(const OuterArgs& a, int d, const double* lam_dev, doubl
 
 constexpr int kSetupBlocks = 1024;
 
-// per block: max degree + smallest argmax over its row chunk, and row-class counts
+__device__ __forceinline__ int64_t items_of(int64_t deg, int light_deg) {
+    return deg > light_deg ? (deg + kItemNnz - 1) / kItemNnz : 0;
+}
+
+// per block: max degree + smallest argmax over its row chunk, long rows and their work items
 __global__ void __launch_bounds__(kThreads) k_deg_count(const int64_t* rp, int64_t n, int64_t chunk, int light_deg,
                                                         int64_t* sc) {
     const int64_t beg = (int64_t)blockIdx.x * chunk;
     const int64_t end = beg + chunk < n ? beg + chunk : n;
-    int64_t best = -1, barg = 0, nh = 0, nm = 0;
+    int64_t best = -1, barg = 0, nl = 0, ni = 0;
     for (int64_t r = beg + threadIdx.x; r < end; r += blockDim.x) {
         const int64_t d = rp[r + 1] - rp[r];
         if (d > best) { best = d; barg = r; }
-        if (d > kHeavyDeg) ++nh;
-        else if (d > light_deg) ++nm;
+        const int64_t q = items_of(d, light_deg);
+        nl += q > 0;
+        ni += q;
     }
-    __shared__ int64_t sb[kThreads], sa[kThreads], sh[kThreads], sm[kThreads];
-    sb[threadIdx.x] = best; sa[threadIdx.x] = barg; sh[threadIdx.x] = nh; sm[threadIdx.x] = nm;
+    __shared__ int64_t sb[kThreads], sa[kThreads], sl[kThreads], si[kThreads];
+    sb[threadIdx.x] = best; sa[threadIdx.x] = barg; sl[threadIdx.x] = nl; si[threadIdx.x] = ni;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
@@ -527,83 +624,91 @@ __global__ void __launch_bounds__(kThreads) k_deg_count(const int64_t* rp, int64
                 sb[threadIdx.x] = sb[q];
                 sa[threadIdx.x] = sa[q];
             }
-            sh[threadIdx.x] += sh[q];
-            sm[threadIdx.x] += sm[q];
+            sl[threadIdx.x] += sl[q];
+            si[threadIdx.x] += si[q];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         sc[blockIdx.x] = sb[0];
         sc[kSetupBlocks + blockIdx.x] = sa[0];
-        sc[2 * kSetupBlocks + blockIdx.x] = sh[0];
-        sc[3 * kSetupBlocks + blockIdx.x] = sm[0];
+        sc[2 * kSetupBlocks + blockIdx.x] = sl[0];
+        sc[3 * kSetupBlocks + blockIdx.x] = si[0];
     }
 }
 
-// one block: totals, max/argmax, exclusive prefix offsets of the row classes
+// one thread: totals, max/argmax (smallest id on ties), exclusive prefix of the item counts
 __global__ void k_deg_scan(int64_t* sc, int nb) {
-    if (threadIdx.x != 0) return;
-    int64_t best = -1, barg = 0, oh = 0, om = 0;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t best = -1, barg = 0, nl = 0, oi = 0;
     for (int b = 0; b < nb; ++b) {
         const int64_t d = sc[b], r = sc[kSetupBlocks + b];
         if (d > best || (d == best && r < barg)) { best = d; barg = r; }
-        const int64_t h = sc[2 * kSetupBlocks + b], m = sc[3 * kSetupBlocks + b];
-        sc[2 * kSetupBlocks + b] = oh;
-        sc[3 * kSetupBlocks + b] = om;
-        oh += h;
-        om += m;
+        nl += sc[2 * kSetupBlocks + b];
+        const int64_t m = sc[3 * kSetupBlocks + b];
+        sc[3 * kSetupBlocks + b] = oi;
+        oi += m;
     }
     sc[4 * kSetupBlocks + 0] = best;
     sc[4 * kSetupBlocks + 1] = barg;
-    sc[4 * kSetupBlocks + 2] = oh;
-    sc[4 * kSetupBlocks + 3] = om;
+    sc[4 * kSetupBlocks + 2] = nl;
+    sc[4 * kSetupBlocks + 3] = oi;
 }
 
-// ordered compaction: each block walks its chunk in tiles of blockDim rows
+// ordered fill of the work items: each block walks its chunk in tiles of blockDim rows and
+// places the items of a tile with a block-wide exclusive scan of the per-row item counts
 __global__ void __launch_bounds__(kThreads) k_deg_fill(const int64_t* rp, int64_t n, int64_t chunk, int light_deg,
-                                                       const int64_t* sc, int32_t* heavy, int32_t* medium) {
+                                                       const int64_t* sc, int32_t* item_row, int32_t* item_k) {
     const int64_t beg = (int64_t)blockIdx.x * chunk;
     const int64_t end = beg + chunk < n ? beg + chunk : n;
-    int64_t oh = sc[2 * kSetupBlocks + blockIdx.x], om = sc[3 * kSetupBlocks + blockIdx.x];
-    __shared__ int wh[kWarps], wm[kWarps];
+    int64_t off = sc[3 * kSetupBlocks + blockIdx.x];
+    __shared__ int64_t wsum[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t t0 = beg; t0 < end; t0 += blockDim.x) {
         const int64_t r = t0 + threadIdx.x;
-        int64_t d = 0;
-        if (r < end) d = rp[r + 1] - rp[r];
-        const bool ih = r < end && d > kHeavyDeg;
-        const bool im = r < end && d > light_deg && d <= kHeavyDeg;
-        const unsigned bh = __ballot_sync(kFull, ih), bm = __ballot_sync(kFull, im);
-        if (lane == 0) { wh[warp] = __popc(bh); wm[warp] = __popc(bm); }
-        __syncthreads();
-        int ph = 0, pm = 0, th = 0, tm = 0;
-        for (int w = 0; w < kWarps; ++w) {
-            if (w < warp) { ph += wh[w]; pm += wm[w]; }
-            th += wh[w];
-            tm += wm[w];
+        const int64_t cnt = r < end ? items_of(rp[r + 1] - rp[r], light_deg) : 0;
+        int64_t v = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += t;
         }
-        const unsigned lower = (1u << lane) - 1u;
-        if (ih) heavy[oh + ph + __popc(bh & lower)] = (int32_t)r;
-        if (im) medium[om + pm + __popc(bm & lower)] = (int32_t)r;
-        oh += th;
-        om += tm;
+        if (lane == 31) wsum[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = lane < kWarps ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t t = __shfl_up_sync(kFull, w, o);
+                if (lane >= o) w += t;
+            }
+            if (lane < kWarps) wsum[lane] = w;
+        }
+        __syncthreads();
+        const int64_t excl = v - cnt + (warp > 0 ? wsum[warp - 1] : 0);
+        for (int64_t q = 0; q < cnt; ++q) {
+            item_row[off + excl + q] = (int32_t)r;
+            item_k[off + excl + q] = (int32_t)q;
+        }
+        off += wsum[kWarps - 1];
         __syncthreads();
     }
 }
 
-void setup_degrees(const int64_t* rp, int64_t n, int light_deg, int32_t* heavy, int32_t* medium, int64_t* scratch,
-                   DegreeInfo* out, cudaStream_t s) {
+void setup_degrees(const int64_t* rp, int64_t n, int light_deg, int32_t* item_row, int32_t* item_k, int64_t cap,
+                   int64_t* scratch, DegreeInfo* out, cudaStream_t s) {
     const int64_t chunk = (n + kSetupBlocks - 1) / kSetupBlocks;
     k_deg_count<<<kSetupBlocks, kThreads, 0, s>>>(rp, n, chunk, light_deg, scratch);
     k_deg_scan<<<1, 32, 0, s>>>(scratch, kSetupBlocks);
-    k_deg_fill<<<kSetupBlocks, kThreads, 0, s>>>(rp, n, chunk, light_deg, scratch, heavy, medium);
     int64_t tot[4];
     cudaMemcpyAsync(tot, scratch + 4 * kSetupBlocks, sizeof(tot), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     out->max_degree = tot[0];
     out->argmax = tot[1];
-    out->n_heavy = tot[2];
-    out->n_medium = tot[3];
+    out->n_long = tot[2];
+    out->n_items = tot[3];
+    if (item_row && tot[3] <= cap)
+        k_deg_fill<<<kSetupBlocks, kThreads, 0, s>>>(rp, n, chunk, light_deg, scratch, item_row, item_k);
 }
 
 // flag bits: 1 row_ptr not monotone / bad ends, 2 column out of range, 4 self loop,

@@ -52,9 +52,11 @@ struct isira_handle_s {
     // setup (Remark 4.1)
     int64_t max_degree = 0, trim = 0;
     double delta = 0.0, normL = 0.0;
-    int32_t* heavy = nullptr;
-    int32_t* medium = nullptr;
-    int n_heavy = 0, n_medium = 0;
+    int32_t* item_row = nullptr;
+    int32_t* item_k = nullptr;
+    double* item_partial = nullptr;
+    unsigned* item_count = nullptr;
+    int64_t n_long = 0, n_items = 0;
     RowSched rs{};
     int lanes = 8;
     int ew_blocks = 0, ts_blocks = 0;
@@ -298,7 +300,7 @@ void choose_lanes(isira_handle h) {
 
 void free_handle(isira_handle h) {
     if (!h) return;
-    void* ptrs[] = {h->heavy, h->medium, h->U, h->W, h->V, h->H, h->theta, h->S, h->R, h->Z, h->dscratch,
+    void* ptrs[] = {h->item_row, h->item_k, h->item_partial, h->item_count, h->U, h->W, h->V, h->H, h->theta, h->S, h->R, h->Z, h->dscratch,
                     h->partial, h->counter, h->Gm, h->Cinv, h->lam_dev, h->tres_dev, h->fb.base, h->fb.st,
                     h->db.base, h->db.st, h->Vt_f};
     for (void* p : ptrs)
@@ -381,34 +383,41 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         }
         // Remark 4.1: degrees, maximum degree, trimmed index, delta; row classes of the scheduler
         const int light_deg = 64;
-        ck(cudaMalloc(&h->heavy, sizeof(int32_t) * (size_t)n));
-        ck(cudaMalloc(&h->medium, sizeof(int32_t) * (size_t)n));
         int64_t* scratch = nullptr;
         ck(cudaMalloc(&scratch, sizeof(int64_t) * 5 * 1024));
         DegreeInfo di{};
-        setup_degrees(d_row_ptr, n, light_deg, h->heavy, h->medium, scratch, &di, s);
+        setup_degrees(d_row_ptr, n, light_deg, nullptr, nullptr, 0, scratch, &di, s);   // counts
+        const size_t ni = (size_t)std::max<int64_t>(1, di.n_items);
+        ck(cudaMalloc(&h->item_row, sizeof(int32_t) * ni));
+        ck(cudaMalloc(&h->item_k, sizeof(int32_t) * ni));
+        ck(cudaMalloc(&h->item_partial, sizeof(double) * ni));
+        ck(cudaMalloc(&h->item_count, sizeof(unsigned) * ni));
+        ck(cudaMemsetAsync(h->item_count, 0, sizeof(unsigned) * ni, s));
+        setup_degrees(d_row_ptr, n, light_deg, h->item_row, h->item_k, di.n_items, scratch, &di, s);   // fill
+        sync(h);
         cudaFree(scratch);
-        ck(cudaGetLastError());
         h->max_degree = di.max_degree;
         if (di.max_degree < 1) throw StatusError{ISIRA_ERR_BAD_GRAPH};
         h->trim = (h->opts.trim_index >= 0 && h->opts.trim_index < n) ? h->opts.trim_index : di.argmax;
         h->delta = h->opts.delta > 0.0 ? h->opts.delta : 2.0 * (double)di.max_degree;
         h->normL = 2.0 * (double)di.max_degree;
-        h->n_heavy = (int)di.n_heavy;
-        h->n_medium = (int)di.n_medium;
+        h->n_long = di.n_long;
+        h->n_items = di.n_items;
+        if (di.n_items > INT32_MAX) throw StatusError{ISIRA_ERR_INVALID_ARG};
         RowSched& rs = h->rs;
         rs.rp = d_row_ptr;
         rs.ci = d_col_idx;
         rs.n = n;
-        rs.heavy = h->heavy;
-        rs.medium = h->medium;
-        rs.n_heavy = h->n_heavy;
-        rs.n_medium = h->n_medium;
+        rs.item_row = h->item_row;
+        rs.item_k = h->item_k;
+        rs.item_partial = h->item_partial;
+        rs.item_count = h->item_count;
+        rs.n_items = (int)di.n_items;
         rs.light_deg = light_deg;
         const int64_t ntiles = (n + 31) / 32;
-        rs.medium_blocks = h->n_medium > 0 ? (int)std::min<int64_t>((h->n_medium + 4 * kWarps - 1) / (4 * kWarps),
-                                                                      (int64_t)h->nsm * 4)
-                                           : 0;
+        rs.item_blocks = di.n_items > 0 ? (int)std::min<int64_t>((di.n_items + kWarps - 1) / kWarps,
+                                                                   (int64_t)h->nsm * 8)
+                                        : 0;
         rs.light_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + kWarps - 1) / kWarps,
                                                                       (int64_t)h->nsm * 8));
         h->ew_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)h->nsm * 4));
@@ -445,8 +454,8 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         h->stats.delta = h->delta;
         h->stats.norm_L = h->normL;
         h->stats.spmv_lanes = h->lanes;
-        h->stats.n_heavy_rows = h->n_heavy;
-        h->stats.n_medium_rows = h->n_medium;
+        h->stats.n_long_rows = h->n_long;
+        h->stats.n_work_items = h->n_items;
     } catch (CudaError& e) {
         isira_status st = map_cuda(e.e);
         free_handle(h);
