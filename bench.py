@@ -51,9 +51,19 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--single-solve", choices=["fp64", "mixed"], default=None,
                    help="create one solver and run one solve, nothing else (for profiler captures)")
+    p.add_argument("--opt", action="append", default=[],
+                   help="solver option key=value applied to every solver (e.g. reorder=1)")
     p.add_argument("--graph-cache", default=None,
                    help="directory to keep the generated graph in (.npz), reused by later runs")
     return p.parse_args()
+
+
+def solver_opts(args):
+    out = {}
+    for kv in args.opt:
+        k, v = kv.split("=", 1)
+        out[k] = float(v) if "." in v or "e" in v else int(v)
+    return out
 
 
 def load_workload(args):
@@ -81,6 +91,13 @@ def workload_config(name, g, k, rel_tol):
     return {"workload": f"{name}-lcc k={k} fp64", "graph": desc.get(name, name), "n": g.n, "nnz": g.nnz,
             "k": k, "resid_rel": rel_tol, "norm_L": "2*max_degree", "l2": "flushed (512 MB write) between steps",
             "start_vector": "splitmix64 seed 1, centred, unit norm"}
+
+
+def config_with_opts(cfg, args):
+    if args.opt:
+        cfg = dict(cfg)
+        cfg["solver_opts"] = solver_opts(args)
+    return cfg
 
 
 # --------------------------------------------------------------------------------------------- clocks
@@ -148,6 +165,19 @@ def phase1_bytes(n, Z, c_avg, word):
     row_ptr 8(n+1), col_idx 4Z, z_k gathered once (word*n), z_{k-1}, w_{j-2}, w_{j-1} read,
     x read+write, w_j and Y written (7 word*n), and c columns of Vh (word*c*n)."""
     return 8 * (n + 1) + 4 * Z + word * n * 8 + word * c_avg * n
+
+
+def phase1_fp64_ops(n, Z, c_avg):
+    """FP64 lane operations of one FP64 phase-1 launch: one add per gathered entry, and about
+    16 + 3c per row for the operator epilogue, the MINRES row update and the reductions."""
+    return Z + n * (16 + 3 * c_avg)
+
+
+def fp64_peak_ops(sm_max_mhz):
+    """FP64 lane operations per second: 152 SMs x 2 lanes per clock (the FP64 pipe issues one warp
+    instruction per 16 cycles per SM on this part; 1.25 TFLOP/s nominal counts an FMA as 2) x clock."""
+    mhz = sm_max_mhz or 2070.0
+    return 152 * 2 * mhz * 1e6
 
 
 def source_hash():
@@ -292,7 +322,7 @@ def main():
     if args.single_solve:
         prec = isira.ISIRA_FP64 if args.single_solve == "fp64" else isira.ISIRA_MIXED
         with isira.Solver(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev),
-                          precision=prec) as s:
+                          precision=prec, **solver_opts(args)) as s:
             s.solve(k, tol=tol, u0=torch.from_numpy(sg.start_vector(n, 1)).to(dev))
             torch.cuda.synchronize()
             print(json.dumps({"single_solve": args.single_solve, **s.stats()}), flush=True)
@@ -330,17 +360,21 @@ def main():
         return times, stats
 
     clk = ClockSampler(uuid.replace("GPU-", "") if uuid else "")
-    s64 = isira.Solver(rp, ci, precision=isira.ISIRA_FP64)
-    smx = isira.Solver(rp, ci, precision=isira.ISIRA_MIXED)
+    s64 = isira.Solver(rp, ci, precision=isira.ISIRA_FP64, **solver_opts(args))
+    smx = isira.Solver(rp, ci, precision=isira.ISIRA_MIXED, **solver_opts(args))
     clk.start()
-    t64, st64 = timed_solves(s64, True)
-    tmx, stmx = timed_solves(smx, True)
+    # headline: the default device-driven inner loop (one CUDA-graph launch per inner solve)
+    t64, st64 = timed_solves(s64, False)
+    tmx, stmx = timed_solves(smx, False)
+    # kernel timing: the same solves with CUDA events around every phase-1 launch (chunked launches)
+    tp64, sp64 = timed_solves(s64, True)
+    tpmx, spmx = timed_solves(smx, True)
     clocks = clk.stop()
     lam64, vec64, res64 = s64.eigpairs()
     lammx, vecmx, resmx = smx.eigpairs()
 
     # accuracy of the benchmarked solves against a tight FP64 solve (untimed)
-    ref = isira.solve(rp, ci, k, tol=1e-12 * normL, u0=u0, precision=isira.ISIRA_FP64)
+    ref = isira.solve(rp, ci, k, tol=1e-12 * normL, u0=u0, precision=isira.ISIRA_FP64, **solver_opts(args))
     lam_ref = ref.eigvals.numpy()
 
     def relerr(a):
@@ -357,7 +391,7 @@ def main():
         rp_d = rp_h.to(dev, non_blocking=True)
         ci_d = ci_h.to(dev, non_blocking=True)
         u0_d = u0_h.to(dev, non_blocking=True)
-        with isira.Solver(rp_d, ci_d, precision=isira.ISIRA_FP64) as s:
+        with isira.Solver(rp_d, ci_d, precision=isira.ISIRA_FP64, **solver_opts(args)) as s:
             s.solve(k, tol=tol, u0=u0_d)
             lam_e, vec_e, res_e = s.eigpairs()
             vec_host = vec_e.cpu()
@@ -372,37 +406,46 @@ def main():
     e2e = max_over_ranks(statistics.mean(e2e_times))
 
     # roofline of the dominant kernel (phase 1 of the FP64 inner solve), from the live events
-    p1_ms = sum(s["inner_phase1_ms"] for s in st64)
-    p1_n = sum(s["inner_phase1_timed"] for s in st64)
-    p1_c = sum(s["inner_phase1_csum"] for s in st64) / max(1, p1_n)
+    p1_ms = sum(s["inner_phase1_ms"] for s in sp64)
+    p1_n = sum(s["inner_phase1_timed"] for s in sp64)
+    p1_c = sum(s["inner_phase1_csum"] for s in sp64) / max(1, p1_n)
     avg_s = p1_ms / 1e3 / max(1, p1_n)
     bytes_launch = phase1_bytes(n, Z, p1_c, 8)
     peak, peak_src = hbm_peak()
     achieved = bytes_launch / avg_s / 1e9 if avg_s > 0 else None
-    p1mx_ms = sum(s["inner_phase1_ms"] for s in stmx)
-    p1mx_n = sum(s["inner_phase1_timed"] for s in stmx)
-    p1mx_c = sum(s["inner_phase1_csum"] for s in stmx) / max(1, p1mx_n)
+    p1mx_ms = sum(s["inner_phase1_ms"] for s in spmx)
+    p1mx_n = sum(s["inner_phase1_timed"] for s in spmx)
+    p1mx_c = sum(s["inner_phase1_csum"] for s in spmx) / max(1, p1mx_n)
     avgmx_s = p1mx_ms / 1e3 / max(1, p1mx_n)
     achieved_mx = phase1_bytes(n, Z, p1mx_c, 4) / avgmx_s / 1e9 if avgmx_s > 0 else None
     traffic = ncu_traffic("phase1_fp64_rmat20")
+    ops_peak = fp64_peak_ops(clocks.get("sm_max_mhz"))
+    ops_achieved = phase1_fp64_ops(n, Z, p1_c) / avg_s if avg_s > 0 else None
 
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": workload_config(args.workload, g, k, args.rel_tol),
+        "dtype": "f64", "data": "synthetic", "config": config_with_opts(workload_config(args.workload, g, k, args.rel_tol), args),
         "mixed": {"value": value_mx, "unit": "s", "dtype": "f32 inner / f64 outer",
                   "speedup_vs_fp64": value / value_mx if value_mx else None,
+                  "roofline": {"kernel": "k_phase1<float>", "bound": "hbm", "achieved": achieved_mx, "peak": peak,
+                               "unit": "GB/s", "frac": (achieved_mx / peak) if achieved_mx else None,
+                               "bytes_per_launch": phase1_bytes(n, Z, p1mx_c, 4), "avg_deflation_rank": p1mx_c},
                   "outer_steps": stmx[-1]["outer_steps"], "inner_iters": stmx[-1]["inner_iters"],
                   "phase1_avg_us": avgmx_s * 1e6, "phase1_GBps": achieved_mx},
         "fp64": {"outer_steps": st64[-1]["outer_steps"], "inner_iters": st64[-1]["inner_iters"],
                  "restarts": st64[-1]["restarts"], "spmv_lanes": st64[-1]["spmv_lanes"],
-                 "phase1_avg_us": avg_s * 1e6, "phase1_launches_timed": p1_n},
+                 "phase1_avg_us": avg_s * 1e6, "phase1_launches_timed": p1_n,
+                 "timed_with_events_s": statistics.mean(tp64)},
         "accuracy": {"max_rel_eig_err_fp64_vs_tight": relerr(lam64), "max_rel_eig_err_mixed_vs_tight": relerr(lammx),
                      "max_true_resid_rel_fp64": float(res64.max()), "max_true_resid_rel_mixed": float(resmx.max()),
                      "tight_tol_rel": 1e-12, "eigvals": [float(x) for x in lam_ref]},
-        "roofline": {"kernel": "k_phase1<double> (trimmed operator SpMV + MINRES row update)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "peak_source": peak_src,
+        "roofline": {"kernel": "k_phase1<double> (trimmed operator SpMV + MINRES row update)", "bound": "alu",
+                     "achieved": ops_achieved / 1e9 if ops_achieved else None, "peak": ops_peak / 1e9,
+                     "unit": "G FP64 lane-ops/s", "frac": (ops_achieved / ops_peak) if ops_achieved else None,
+                     "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x max SM clock (1.25 TFLOP/s nominal)",
+                     "ops_per_launch": phase1_fp64_ops(n, Z, p1_c), "hbm_achieved_GBps": achieved,
+                     "hbm_frac": (achieved / peak) if achieved else None, "hbm_peak": peak, "hbm_peak_source": peak_src,
                      "bytes_per_launch": bytes_launch, "avg_deflation_rank": p1_c, "traffic": traffic},
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "pinned host CSR -> isira_create -> isira_solve -> isira_eigpairs -> host"},

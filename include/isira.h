@@ -74,7 +74,14 @@ typedef struct {
     uint64_t seed;        /* SplitMix64 seed of replacement vectors after an orthogonalisation
                              breakdown and of the default start vector */
     int spmv_lanes;       /* lanes per row of the light-row SpMV (1,2,4,8,16,32); <= 0: autotune */
-    int inner_chunk;      /* inner iterations launched between convergence checks; <= 0: 16 */
+    int inner_chunk;      /* chunked mode: inner iterations launched between convergence checks; <= 0: 16 */
+    int inner_graph;      /* 1: each inner solve is one CUDA-graph launch whose WHILE node repeats the
+                             iteration until the device-side stopping test fires (no host round trip);
+                             0: chunked launches with a host check after each chunk */
+    int reorder;          /* 1: relabel the vertices internally by descending degree (stable), which
+                             packs the vectors' entries of high-degree vertices together for cache
+                             reuse in the SpMV; vectors at the API stay in the caller's numbering;
+                             0: use the caller's numbering */
 } isira_opts;
 
 typedef struct {
@@ -168,6 +175,41 @@ ISIRA_API isira_status isira_inner_solve(isira_handle h, int precision, double s
  * d_theta: k ascending eigenvalues; d_S: k-by-k unit eigenvectors, each signed so that
  * its largest-magnitude entry (first on ties) is positive.  stream as above. */
 ISIRA_API isira_status isira_sym_eig(int k, const double* d_H, double* d_theta, double* d_S, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * Batched solves: many independent graphs of uneven size (Algorithm 2 for each graph).
+ * Every graph gets its own solver (as isira_create) and its own CUDA stream; a pool of host
+ * threads drives the solvers concurrently, largest graphs first, so the kernels of different
+ * graphs overlap on the GPU.  Each inner solve is one device-driven CUDA-graph launch
+ * (opts->inner_graph).  The caller owns the G CSR graphs (device pointers, as in isira_create)
+ * until isira_batch_destroy.
+ */
+typedef struct isira_batch_s* isira_batch;
+
+/* G >= 1 graphs; h_n, h_nnz: host arrays of G sizes; d_row_ptr, d_col_idx: host arrays of G
+ * device pointers.  opts as in isira_create (NULL = defaults), applied to every graph. */
+ISIRA_API isira_status isira_batch_create(isira_batch* out, int G, const int64_t* h_n, const int64_t* h_nnz,
+                                          const int64_t* const* d_row_ptr, const int32_t* const* d_col_idx,
+                                          const isira_opts* opts);
+
+/* Solves every graph for its k smallest positive eigenpairs with initial shift sigma and the
+ * absolute tolerance tol_rel * (2 * max degree of that graph).  n_threads host threads
+ * (<= 0: min(G, 16)).  Returns ISIRA_OK if every graph succeeded, else the first failing
+ * status; per-graph statuses via isira_batch_status. */
+ISIRA_API isira_status isira_batch_solve(isira_batch b, int k, double sigma, double tol_rel, int n_threads);
+
+/* Status of graph g's last solve. */
+ISIRA_API isira_status isira_batch_status(isira_batch b, int g);
+
+/* Results of graph g, as isira_eigpairs. */
+ISIRA_API isira_status isira_batch_eigpairs(isira_batch b, int g, double* h_eigvals, double* d_eigvecs,
+                                            double* h_true_resid, int* n_out);
+
+/* Counters of graph g, as isira_get_stats. */
+ISIRA_API isira_status isira_batch_get_stats(isira_batch b, int g, isira_stats* out);
+
+/* Releases every solver of the batch.  NULL is ignored. */
+ISIRA_API void isira_batch_destroy(isira_batch b);
 
 /* ---------------------------------------------------------------------------------
  * Allocation-free variant (the paper has no counterpart; it exists for callers of this

@@ -30,14 +30,17 @@ ISIRA_MIXED = 1
 
 EXPORTED = ["isira_default_opts", "isira_error_string", "isira_create", "isira_solve", "isira_eigpairs",
             "isira_get_stats", "isira_set_profiling", "isira_destroy", "isira_apply_operator",
-            "isira_inner_solve", "isira_sym_eig", "isira_apply_operator_noalloc"]
+            "isira_inner_solve", "isira_sym_eig", "isira_apply_operator_noalloc", "isira_batch_create",
+            "isira_batch_solve", "isira_batch_status", "isira_batch_eigpairs", "isira_batch_get_stats",
+            "isira_batch_destroy"]
 
 
 class isira_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("m", C.c_int), ("q", C.c_int), ("tau_inner", C.c_double),
                 ("max_inner", C.c_int), ("max_outer", C.c_int), ("trim_index", C.c_int64), ("delta", C.c_double),
                 ("sigma_omega", C.c_double), ("drop_rank1", C.c_int), ("validate", C.c_int), ("seed", C.c_uint64),
-                ("spmv_lanes", C.c_int), ("inner_chunk", C.c_int)]
+                ("spmv_lanes", C.c_int), ("inner_chunk", C.c_int), ("inner_graph", C.c_int),
+                ("reorder", C.c_int)]
 
 
 class isira_stats(C.Structure):
@@ -83,6 +86,18 @@ def _load() -> C.CDLL:
     lib.isira_sym_eig.restype = I
     lib.isira_apply_operator_noalloc.argtypes = [I64, I64, P, P, I64, I, D, D, I, I, P, P, P, P]
     lib.isira_apply_operator_noalloc.restype = I
+    lib.isira_batch_create.argtypes = [C.POINTER(P), I, P, P, P, P, C.POINTER(isira_opts)]
+    lib.isira_batch_create.restype = I
+    lib.isira_batch_solve.argtypes = [P, I, D, D, I]
+    lib.isira_batch_solve.restype = I
+    lib.isira_batch_status.argtypes = [P, I]
+    lib.isira_batch_status.restype = I
+    lib.isira_batch_eigpairs.argtypes = [P, I, P, P, P, C.POINTER(I)]
+    lib.isira_batch_eigpairs.restype = I
+    lib.isira_batch_get_stats.argtypes = [P, I, C.POINTER(isira_stats)]
+    lib.isira_batch_get_stats.restype = I
+    lib.isira_batch_destroy.argtypes = [P]
+    lib.isira_batch_destroy.restype = None
     return lib
 
 
@@ -252,6 +267,60 @@ def apply_operator_noalloc(row_ptr, col_idx, x, trim: int, sigma: float = 0.0, d
                                            _ptr(Vc), _ptr(x), _ptr(y), _stream_ptr(stream)),
           "isira_apply_operator_noalloc")
     return y
+
+
+class Batch:
+    """Many independent graphs solved concurrently (isira_batch_*): one solver and one CUDA stream
+    per graph, driven by a pool of host threads inside the library."""
+
+    def __init__(self, graphs, **opts):
+        """graphs: list of (row_ptr int64 CUDA tensor, col_idx int32 CUDA tensor)."""
+        import numpy as np
+        self.graphs = [(rp.contiguous(), ci.contiguous()) for rp, ci in graphs]
+        G = len(self.graphs)
+        self.n = [rp.numel() - 1 for rp, _ in self.graphs]
+        n = np.array(self.n, dtype=np.int64)
+        nnz = np.array([ci.numel() for _, ci in self.graphs], dtype=np.int64)
+        rps = (C.c_void_p * G)(*[rp.data_ptr() for rp, _ in self.graphs])
+        cis = (C.c_void_p * G)(*[ci.data_ptr() for _, ci in self.graphs])
+        self.opts = default_opts(**opts)
+        h = C.c_void_p()
+        check(lib.isira_batch_create(C.byref(h), G, n.ctypes.data, nnz.ctypes.data, C.cast(rps, C.c_void_p),
+                                     C.cast(cis, C.c_void_p), C.byref(self.opts)), "isira_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.isira_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, k: int, sigma: float = 0.0, rel_tol: float = 1e-8, n_threads: int = 0) -> int:
+        return lib.isira_batch_solve(self.h, int(k), float(sigma), float(rel_tol), int(n_threads))
+
+    def status(self, g: int) -> int:
+        return lib.isira_batch_status(self.h, g)
+
+    def stats(self, g: int) -> dict:
+        st = isira_stats()
+        check(lib.isira_batch_get_stats(self.h, g, C.byref(st)), "isira_batch_get_stats")
+        return st.as_dict()
+
+    def eigpairs(self, g: int):
+        import torch
+        k = self.stats(g)["n_locked"]
+        lam = torch.empty(k, dtype=torch.float64)
+        vec = torch.empty((k, self.n[g]), dtype=torch.float64, device=self.graphs[g][0].device)
+        res = torch.empty(k, dtype=torch.float64)
+        nout = C.c_int(0)
+        check(lib.isira_batch_eigpairs(self.h, g, _ptr(lam), _ptr(vec), _ptr(res), C.byref(nout)),
+              "isira_batch_eigpairs")
+        return lam, vec.t(), res
 
 
 def solve(row_ptr, col_idx, k: int, sigma: float = 0.0, tol: float | None = None, rel_tol: float = 1e-8, u0=None,

@@ -122,6 +122,12 @@ __device__ __forceinline__ T block_sum0(T v) {
 // light tiles with a zero sum.
 constexpr int kItemNnz = 1024;
 
+// Work units are the items (0 .. n_items-1) followed by the light tiles; setup cuts the unit
+// list into n_warps ranges of equal estimated cost (one launch wave), warp w walking units
+// [warp_start[w], warp_start[w+1]).  The static partition keeps every reduction deterministic.
+constexpr int kTileRowCost = 12;   // estimated cost of one row epilogue, in gathered entries
+constexpr int kItemCost = 32;      // fixed cost of one work item
+
 struct RowSched {
     const int64_t* __restrict__ rp;
     const int32_t* __restrict__ ci;
@@ -130,10 +136,11 @@ struct RowSched {
     const int32_t* __restrict__ item_k;     // position of the item within its row
     void* item_partial;                     // one partial sum per item (type of the launch)
     unsigned* item_count;                   // arrival counters, used at each row's first item
+    const int32_t* __restrict__ warp_start; // n_warps + 1 unit boundaries
     int n_items;
-    int item_blocks, light_blocks;
+    int n_warps;
     int light_deg;
-    __host__ __device__ int grid() const { return item_blocks + light_blocks; }
+    __host__ __device__ int grid() const { return n_warps / kWarps; }
 };
 
 // Calls epi(row, degree, sum_{c in N(row)} x[c]) exactly once for every row 0..n-1 (with a
@@ -141,73 +148,74 @@ struct RowSched {
 template <typename T, int G, class Epi>
 __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* __restrict__ x, Epi& epi,
                                                     int64_t skip) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int b = blockIdx.x;
-    if (b < S.item_blocks) {                               // long rows: one warp per item
-        // Finished rows are collected one per lane and their epilogues run 32 at a time, so the
-        // epilogue arithmetic uses every lane of the warp.
-        T* part = static_cast<T*>(S.item_partial);
-        int64_t my_row = -1, my_deg = 0;
-        T my_sum = 0;
-        int nb = 0;                                        // rows collected (warp-uniform)
-        for (int64_t it = (int64_t)b * kWarps + warp; it < S.n_items; it += (int64_t)S.item_blocks * kWarps) {
-            const int64_t r = S.item_row[it];
-            if (r == skip) continue;
-            const int kpos = S.item_k[it];
-            const int64_t rb = S.rp[r], re = S.rp[r + 1];
-            const int64_t beg = rb + (int64_t)kpos * kItemNnz;
-            const int64_t end = beg + kItemNnz < re ? beg + kItemNnz : re;
-            T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-            int64_t e = beg + lane;
-            for (; e + 96 < end; e += 128) {
-                const int32_t c0 = __ldg(S.ci + e), c1 = __ldg(S.ci + e + 32);
-                const int32_t c2 = __ldg(S.ci + e + 64), c3 = __ldg(S.ci + e + 96);
-                s0 += __ldg(x + c0);
-                s1 += __ldg(x + c1);
-                s2 += __ldg(x + c2);
-                s3 += __ldg(x + c3);
-            }
-            for (; e < end; e += 32) s0 += __ldg(x + __ldg(S.ci + e));
-            T s = warp_sum((s0 + s1) + (s2 + s3));
-            const int nit = (int)((re - rb + kItemNnz - 1) / kItemNnz);
-            int done = 1;
-            if (nit > 1) {
-                // several items: the warp that finishes the row's last item adds all partials in order
-                int last = 0;
-                if (lane == 0) {
-                    const int64_t first = it - kpos;
-                    part[it] = s;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int u_beg = S.warp_start[gw], u_end = S.warp_start[gw + 1];
+    // long rows: finished rows are collected one per lane and their epilogues run 32 at a time,
+    // so the epilogue arithmetic uses every lane of the warp
+    T* part = static_cast<T*>(S.item_partial);
+    int64_t my_row = -1, my_deg = 0;
+    T my_sum = 0;
+    int nb = 0;                                            // rows collected (warp-uniform)
+    const int it_end = u_end < S.n_items ? u_end : S.n_items;
+    for (int it = u_beg; it < it_end; ++it) {
+        const int64_t r = S.item_row[it];
+        if (r == skip) continue;
+        const int kpos = S.item_k[it];
+        const int64_t rb = S.rp[r], re = S.rp[r + 1];
+        const int64_t beg = rb + (int64_t)kpos * kItemNnz;
+        const int64_t end = beg + kItemNnz < re ? beg + kItemNnz : re;
+        T s0 = 0, s1 = 0;
+        for (int64_t e = beg + lane; e < end; e += 256) {
+            // a predicated batch of 8 independent index loads, then 8 independent gathers
+            int32_t c[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) c[q] = (e + 32 * q < end) ? __ldg(S.ci + e + 32 * q) : -1;
+            T v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = c[q] >= 0 ? __ldg(x + c[q]) : T(0);
+            s0 += (v[0] + v[1]) + (v[2] + v[3]);
+            s1 += (v[4] + v[5]) + (v[6] + v[7]);
+        }
+        T s = warp_sum(s0 + s1);
+        const int nit = (int)((re - rb + kItemNnz - 1) / kItemNnz);
+        int done = 1;
+        if (nit > 1) {
+            // several items: the warp that finishes the row's last item adds all partials in order
+            int last = 0;
+            if (lane == 0) {
+                const int64_t first = it - kpos;
+                part[it] = s;
+                __threadfence();
+                const unsigned prev = atomicAdd(S.item_count + first, 1u);
+                if (prev == (unsigned)(nit - 1)) {
                     __threadfence();
-                    const unsigned prev = atomicAdd(S.item_count + first, 1u);
-                    if (prev == (unsigned)(nit - 1)) {
-                        __threadfence();
-                        T tot = 0;
-                        for (int q = 0; q < nit; ++q) tot += __ldcg(part + first + q);
-                        S.item_count[first] = 0u;
-                        s = tot;
-                        last = 1;
-                    }
+                    T tot = 0;
+                    for (int q = 0; q < nit; ++q) tot += __ldcg(part + first + q);
+                    S.item_count[first] = 0u;
+                    s = tot;
+                    last = 1;
                 }
-                done = __shfl_sync(kFull, last, 0);
-                s = __shfl_sync(kFull, s, 0);
             }
-            if (done) {
-                if (lane == nb) { my_row = r; my_deg = re - rb; my_sum = s; }
-                if (++nb == 32) {
-                    epi(my_row, my_deg, my_sum);
-                    my_row = -1;
-                    nb = 0;
-                }
+            done = __shfl_sync(kFull, last, 0);
+            s = __shfl_sync(kFull, s, 0);
+        }
+        if (done) {
+            if (lane == nb) { my_row = r; my_deg = re - rb; my_sum = s; }
+            if (++nb == 32) {
+                epi(my_row, my_deg, my_sum);
+                my_row = -1;
+                nb = 0;
             }
         }
-        if (my_row >= 0) epi(my_row, my_deg, my_sum);
-        return;
     }
-    b -= S.item_blocks;
+    if (my_row >= 0) epi(my_row, my_deg, my_sum);
+    // light tiles: 32 consecutive rows, G lanes per row, one lane per row for the epilogue
     constexpr int RPS = 32 / G;                            // rows per sub-pass
-    const int64_t ntiles = (S.n + 31) >> 5;
-    for (int64_t tile = (int64_t)b * kWarps + warp; tile < ntiles; tile += (int64_t)S.light_blocks * kWarps) {
-        const int64_t row = tile * 32 + lane;
+    const int t_beg = (u_beg > S.n_items ? u_beg : S.n_items) - S.n_items;
+    const int t_end = u_end - S.n_items;
+    for (int tile = t_beg; tile < t_end; ++tile) {
+        const int64_t row = (int64_t)tile * 32 + lane;
         const bool valid = row < S.n;
         int64_t beg = valid ? S.rp[row] : 0;
         int64_t end = valid ? S.rp[row + 1] : 0;
@@ -221,18 +229,18 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
             const int64_t sb = __shfl_sync(kFull, beg, src);
             const int64_t se = __shfl_sync(kFull, end, src);
             const int sl = __shfl_sync(kFull, light, src);
-            T s0 = 0, s1 = 0;
+            T s = 0;
             if (sl) {
-                int64_t e = sb + (lane % G);
-                for (; e + 3 * G < se; e += 4 * G) {
-                    const int32_t c0 = __ldg(S.ci + e), c1 = __ldg(S.ci + e + G);
-                    const int32_t c2 = __ldg(S.ci + e + 2 * G), c3 = __ldg(S.ci + e + 3 * G);
-                    s0 += __ldg(x + c0) + __ldg(x + c1);
-                    s1 += __ldg(x + c2) + __ldg(x + c3);
+                for (int64_t e = sb + (lane % G); e < se; e += 8 * G) {
+                    int32_t c[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) c[q] = (e + q * G < se) ? __ldg(S.ci + e + q * G) : -1;
+                    T v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = c[q] >= 0 ? __ldg(x + c[q]) : T(0);
+                    s += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
                 }
-                for (; e < se; e += G) s0 += __ldg(x + __ldg(S.ci + e));
             }
-            T s = s0 + s1;
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
             const T t = __shfl_sync(kFull, s, (lane % RPS) * G);

@@ -19,6 +19,8 @@
 // Vectors per row and iteration: z_k (gathered), z_{k-1}, Y, three rotating w
 // buffers, x, and c columns of Vh.
 #pragma once
+#include <mutex>
+
 #include "internal.h"
 
 namespace isira {
@@ -60,15 +62,10 @@ struct Phase1Epi {
         const T degT = (T)deg;
         const T zr = zc[r];
         const T D = precond_diag(degT, sigma);
-        T vr[NC > 0 ? NC : 1];
         T vdot = 0;
 #pragma unroll
-        for (int t = 0; t < NC; ++t) {
-            if (t < c) {
-                vr[t] = Vt[(int64_t)t * ldv + r];
-                vdot += vr[t] * u1s[t];
-            }
-        }
+        for (int t = 0; t < NC; ++t)
+            if (t < c) vdot += Vt[(int64_t)t * ldv + r] * u1s[t];
         T y1 = ((degT - sigma) * zr - gsum + s_term) * inv_beta + vdot;
         if (has_prev) {
             const T zpr = zp[r];
@@ -83,23 +80,24 @@ struct Phase1Epi {
         acc[0] += zr * inv_beta * y1;
         const T yd = y1 / D;
 #pragma unroll
-        for (int t = 0; t < NC; ++t)
-            if (t < c) acc[1 + t] += vr[t] * yd;
+        for (int t = 0; t < NC; ++t)   // second read of the row of Vh: an L1 hit
+            if (t < c) acc[1 + t] += Vt[(int64_t)t * ldv + r] * yd;
     }
 };
 
 template <typename T, int G, int NC>
-__global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, 4) k_phase1(InnerArgs<T> a) {
     InnerState<T>* st = a.st;
     if (st->done) return;
     const int k = st->itn + 1;
+    const int c = st->p_c;
     __shared__ T u1s[NC > 0 ? NC : 1];
     __shared__ T red[1 + NC];
     Phase1Epi<T, NC> epi;
     epi.trim = a.trim;
     epi.ldv = a.ldv;
-    epi.sigma = a.sigma;
-    epi.c = a.c;
+    epi.sigma = st->p_sigma;
+    epi.c = c;
     epi.Vt = a.Vt;
     epi.Y = a.Y;
     epi.x = a.x;
@@ -110,7 +108,7 @@ __global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
     epi.has_prev = k >= 2;
     epi.cprev = epi.has_prev ? beta / oldb : T(0);
     epi.inv_oldb = epi.has_prev ? T(1) / oldb : T(0);
-    epi.s_term = a.sig_n * st->s_cur;
+    epi.s_term = st->p_sig_n * st->s_cur;
     const int j = k - 1;                    // iteration whose w/x update is deferred to here
     epi.wo2 = wbuf(a, j + 1);               // w_{j-2}
     epi.wo1 = wbuf(a, j + 2);               // w_{j-1}
@@ -119,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
     epi.dlt = st->w_dlt;
     epi.inv_gamma = st->w_inv_gamma;
     epi.phi = st->w_phi;
-    for (int t = threadIdx.x; t < a.c; t += blockDim.x) u1s[t] = st->u1[t];
+    for (int t = threadIdx.x; t < c; t += blockDim.x) u1s[t] = st->u1[t];
     epi.u1s = u1s;
 #pragma unroll
     for (int t = 0; t < 1 + NC; ++t) epi.acc[t] = T(0);
@@ -127,14 +125,13 @@ __global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
 
     for_each_row_gather<T, G>(a.rs, epi.zc, epi, a.trim);
 
-    if (block_partials_arrive<T, 1 + NC>(epi.acc, 1 + a.c, a.partial, a.pstride, a.counter)) {
-        last_block_sum(a.partial, a.pstride, gridDim.x, 1 + a.c, red, a.counter);
+    if (block_partials_arrive<T, 1 + NC>(epi.acc, 1 + c, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, 1 + c, red, a.counter);
         // alpha_k and the SMW coefficient of phase 2:
         //   Vh^T D^{-1} y = h1 - (alpha/beta) (g + delta G g),  tv = C^{-1} (that)
         __shared__ double rhs[kCMax];
         const T alpha = red[0];
         const double coef = (double)alpha / (double)beta;
-        const int c = a.c;
         for (int t = threadIdx.x; t < c; t += blockDim.x) {
             double gg = 0.0;
             for (int s = 0; s < c; ++s) gg += a.Gm[t + s * c] * (double)st->g_cur[s];
@@ -154,16 +151,23 @@ __global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
 // ------------------------------------------------------------------ phase 2
 
 template <typename T, int NC>
-__global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init) {
+__global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, cudaGraphConditionalHandle cond,
+                                                     int has_cond) {
     InnerState<T>* st = a.st;
-    if (!init && st->done) return;
+    if (!init && st->done) {
+        // nothing left to do: make sure a surrounding WHILE node stops
+        if (has_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
     const int k = init ? 0 : st->itn + 1;
+    const int c = st->p_c;
+    const T sigma = st->p_sigma;
     const T* zc = ((k - 1) & 1) ? a.z1 : a.z0;
     T* zn = (k & 1) ? a.z1 : a.z0;
     const T coef = init ? T(0) : st->alpha / st->beta;
     __shared__ T qvs[NC > 0 ? NC : 1], tvs[NC > 0 ? NC : 1];
     __shared__ T red[2 + NC];
-    for (int t = threadIdx.x; t < a.c; t += blockDim.x) {
+    for (int t = threadIdx.x; t < c; t += blockDim.x) {
         qvs[t] = init ? T(0) : st->qv[t];
         tvs[t] = st->tv[t];
     }
@@ -178,15 +182,14 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init) {
             continue;
         }
         const T degT = (T)(a.rs.rp[r + 1] - a.rs.rp[r]);
-        const T D = precond_diag(degT, a.sigma);
-        T vr[NC > 0 ? NC : 1];
+        const T D = precond_diag(degT, sigma);
         T q1 = 0, q2 = 0;
 #pragma unroll
         for (int t = 0; t < NC; ++t) {
-            if (t < a.c) {
-                vr[t] = a.Vt[(int64_t)t * a.ldv + r];
-                q1 += vr[t] * qvs[t];
-                q2 += vr[t] * tvs[t];
+            if (t < c) {
+                const T v = a.Vt[(int64_t)t * a.ldv + r];
+                q1 += v * qvs[t];
+                q2 += v * tvs[t];
             }
         }
         T y = a.Y[r];
@@ -196,11 +199,11 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init) {
         acc[0] += y * z;
         acc[1] += z;
 #pragma unroll
-        for (int t = 0; t < NC; ++t)
-            if (t < a.c) acc[2 + t] += vr[t] * z;
+        for (int t = 0; t < NC; ++t)   // second read of the row of Vh: an L1 hit
+            if (t < c) acc[2 + t] += a.Vt[(int64_t)t * a.ldv + r] * z;
     }
-    if (block_partials_arrive<T, 2 + NC>(acc, 2 + a.c, a.partial, a.pstride, a.counter)) {
-        last_block_sum(a.partial, a.pstride, gridDim.x, 2 + a.c, red, a.counter);
+    if (block_partials_arrive<T, 2 + NC>(acc, 2 + c, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, 2 + c, red, a.counter);
         __shared__ T bnew_s, bold_s;
         if (threadIdx.x == 0) {
             const T bb = red[0];
@@ -251,6 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init) {
             }
             st->s_cur = red[1];
             st->done = done;
+            if (has_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
             a.hs->inner_done = done;
             a.hs->inner_iters = st->itn;
             a.hs->inner_relres = st->beta1 > T(0) ? (double)(st->phibar / st->beta1) : 0.0;
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init) {
         // c-vectors for the next phase 1: g_prev <- g_cur, g_cur <- Vh^T z_{k+1},
         // u1 = delta (g_cur / beta_{k+1} - (beta_{k+1} / beta_k) g_prev)
         const T bnew = bnew_s, bold = bold_s;
-        for (int t = threadIdx.x; t < a.c; t += blockDim.x) {
+        for (int t = threadIdx.x; t < c; t += blockDim.x) {
             const T gp = init ? T(0) : st->g_cur[t];
             const T gn = red[2 + t];
             st->g_prev[t] = gp;
@@ -279,6 +283,11 @@ __global__ void __launch_bounds__(kThreads) k_prep(InnerArgs<T> a, const double*
     __shared__ T red[NC > 0 ? NC : 1];
     const double rn = *rnorm_dev;
     const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->p_sigma = a.sigma;
+        a.st->p_sig_n = a.sig_n;
+        a.st->p_c = a.c;
+    }
     T acc[NC > 0 ? NC : 1];
 #pragma unroll
     for (int t = 0; t < (NC > 0 ? NC : 1); ++t) acc[t] = T(0);
@@ -346,6 +355,11 @@ __global__ void __launch_bounds__(kThreads) k_finalize(InnerArgs<T> a, double* Z
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_opstats(InnerArgs<T> a, const T* x) {
     __shared__ T red[1 + NC];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->p_sigma = a.sigma;
+        a.st->p_sig_n = a.sig_n;
+        a.st->p_c = a.c;
+    }
     T acc[1 + NC];
 #pragma unroll
     for (int t = 0; t < 1 + NC; ++t) acc[t] = T(0);
@@ -495,11 +509,14 @@ __global__ void k_copy_vcol(const double* src, T* dst, int64_t n) {
 
 // ------------------------------------------------------------------ launchers
 
+// deflation-rank buckets: the kernels keep NC per-thread accumulators, so small buckets save registers
 #define ISIRA_NC_DISPATCH(c, F) \
     do {                        \
         if ((c) == 0) { F(0); } \
         else if ((c) <= 8) { F(8); } \
+        else if ((c) <= 12) { F(12); } \
         else if ((c) <= 16) { F(16); } \
+        else if ((c) <= 24) { F(24); } \
         else { F(32); }         \
     } while (0)
 
@@ -525,9 +542,16 @@ void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s) {
 
 template <typename T>
 void inner_phase2(const InnerArgs<T>& a, int init, cudaStream_t s) {
-#define L2(NC) k_phase2<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a, init)
+#define L2(NC) k_phase2<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a, init, 0, 0)
     ISIRA_NC_DISPATCH(a.c, L2);
 #undef L2
+}
+
+template <typename T>
+void inner_phase2_cond(const InnerArgs<T>& a, cudaGraphConditionalHandle cond, cudaStream_t s) {
+#define L2C(NC) k_phase2<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a, 0, cond, 1)
+    ISIRA_NC_DISPATCH(a.c, L2C);
+#undef L2C
 }
 
 template <typename T>
@@ -553,12 +577,11 @@ template <typename T>
 void gram_setup(const InnerArgs<T>& a, double* G_out, double* Cinv_out, double* partial, cudaStream_t s) {
     if (a.c <= 0) return;
     const size_t smem = sizeof(double) * (size_t)a.c * (kGramTile + 1);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag once;
+    std::call_once(once, [] {
         cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(double) * kCMax * (kGramTile + 1)));
-        attr_set = true;
-    }
+    });
     k_gram<T><<<a.ew_blocks, kThreads, smem, s>>>(a, G_out, Cinv_out, partial, a.pstride);
 }
 
@@ -570,6 +593,7 @@ void copy_vcol(const double* src, T* dst, int64_t n, cudaStream_t s) {
 #define ISIRA_INSTANTIATE_INNER(T)                                                                        \
     template void inner_phase1<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
     template void inner_phase2<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
+    template void inner_phase2_cond<T>(const InnerArgs<T>&, cudaGraphConditionalHandle, cudaStream_t);   \
     template void inner_prep_launch<T>(const InnerArgs<T>&, const double*, const double*, cudaStream_t); \
     template void inner_finalize_to<T>(const InnerArgs<T>&, double*, cudaStream_t);                      \
     template void inner_opstats<T>(const InnerArgs<T>&, const T*, cudaStream_t);                         \

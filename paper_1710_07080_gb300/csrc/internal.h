@@ -24,7 +24,9 @@ struct InnerState {
     T u1[kCMax];                             // phase-1 coefficient of Vh_r (see inner_impl.cuh)
     T qv[kCMax];                             // phase-2: (alpha/beta) delta g_cur
     T tv[kCMax];                             // phase-2: SMW coefficient C^{-1} Vh^T D^{-1} y
-    int itn, done, pending, pad;
+    T p_sigma, p_sig_n;                      // shift and (sigma / n or 0) of the current solve
+    int p_c;                                 // deflation rank of the current solve
+    int itn, done, pending;
 };
 
 // Per-handle, per-precision buffers and parameters of the inner solve.
@@ -52,6 +54,9 @@ template <typename T> void inner_prep_launch(const InnerArgs<T>& a, const double
                                              cudaStream_t s);
 template <typename T> void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s);
 template <typename T> void inner_phase2(const InnerArgs<T>& a, int init, cudaStream_t s);
+// phase 2 inside a CUDA graph whose WHILE node is driven by `cond` (set to 0 once the solve stops)
+template <typename T> void inner_phase2_cond(const InnerArgs<T>& a, cudaGraphConditionalHandle cond,
+                                             cudaStream_t s);
 template <typename T> void inner_finalize_to(const InnerArgs<T>& a, double* Z, cudaStream_t s);
 template <typename T> void inner_opstats(const InnerArgs<T>& a, const T* x, cudaStream_t s);
 template <typename T> void gram_setup(const InnerArgs<T>& a, double* G_out, double* Cinv_out, double* scratch,
@@ -100,6 +105,15 @@ struct DegreeInfo { int64_t max_degree, argmax; int64_t n_long, n_items; };
 // Counts (and, when item_row is given and n_items <= cap, fills) the long-row work items.
 void setup_degrees(const int64_t* rp, int64_t n, int light_deg, int32_t* item_row, int32_t* item_k, int64_t cap,
                    int64_t* scratch, DegreeInfo* out, cudaStream_t s);
+// Equal-cost ranges of work units (items, then light tiles) for n_warps warps.
+void setup_partition(const int64_t* rp, int64_t n, const int32_t* item_row, const int32_t* item_k, int64_t n_items,
+                     int light_deg, int n_warps, int64_t* cost_tmp, int64_t* prefix_tmp, int32_t* warp_start,
+                     cudaStream_t s);
+// vertex relabelling by descending degree (reorder.cu)
+cudaError_t build_reordered_graph(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int64_t maxdeg,
+                                  int64_t* rp2, int32_t* ci2, int32_t* perm, int32_t* inv, cudaStream_t s);
+template <typename T> void to_internal(const T* src, const int32_t* perm, int64_t n, T* dst, cudaStream_t s);
+template <typename T> void to_external(const T* src, const int32_t* perm, int64_t n, T* dst, cudaStream_t s);
 int validate_csr(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int* d_flag, cudaStream_t s);
 
 }  // namespace isira

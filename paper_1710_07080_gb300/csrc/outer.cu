@@ -10,6 +10,8 @@
 // The tall-skinny kernels stage a tile of basis rows in shared memory once and use
 // it twice (row-wise update, column-wise dot products), so U and V are read once
 // per Gram-Schmidt pass.
+#include <mutex>
+
 #include "internal.h"
 
 namespace isira {
@@ -268,11 +270,8 @@ __global__ void __launch_bounds__(kThreads) k_sym_eig(const double* H, int ldh, 
 void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, int lds, HostStatus* hs,
                    cudaStream_t s) {
     const int bytes = (int)(sizeof(double) * 4 * kMMax * kEigLd);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        attr = true;
-    }
+    static std::once_flag once;
+    std::call_once(once, [bytes] { cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
     k_sym_eig<<<1, kThreads, bytes, s>>>(H, ldh, k, theta, S, lds, hs);
 }
 
@@ -407,13 +406,13 @@ __global__ void __launch_bounds__(kThreads) k_tall_skinny(OuterArgs a, int k, in
 }
 
 static void ts_smem_attr() {
-    static bool done = false;
-    if (done) return;
-    const int bytes = (int)(sizeof(double) * ((size_t)kTsMaxCols * kTsRows + kTsRows + kTsMaxCols + 1));
-    cudaFuncSetAttribute(k_tall_skinny<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_tall_skinny<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_tall_skinny<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    done = true;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const int bytes = (int)(sizeof(double) * ((size_t)kTsMaxCols * kTsRows + kTsRows + kTsMaxCols + 1));
+        cudaFuncSetAttribute(k_tall_skinny<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k_tall_skinny<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k_tall_skinny<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    });
 }
 
 static size_t ts_smem(int nq) { return sizeof(double) * ((size_t)nq * kTsRows + kTsRows + nq + 1); }
@@ -529,12 +528,11 @@ __global__ void __launch_bounds__(kThreads) k_rotate(OuterArgs a, double* X, int
 }
 
 void outer_rotate(const OuterArgs& a, double* X, int kk, int c0, int ncol, double* vout, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag once;
+    std::call_once(once, [] {
         cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(double) * ((size_t)kMMax * kRotRows + (size_t)kMMax * (kMMax + 1))));
-        attr = true;
-    }
+    });
     const size_t smem = sizeof(double) * ((size_t)kk * kRotRows + (size_t)kk * (ncol + 1));
     k_rotate<<<a.ts_blocks, kThreads, smem, s>>>(a, X, kk, c0, ncol, vout);
 }
@@ -709,6 +707,83 @@ void setup_degrees(const int64_t* rp, int64_t n, int light_deg, int32_t* item_ro
     out->n_items = tot[3];
     if (item_row && tot[3] <= cap)
         k_deg_fill<<<kSetupBlocks, kThreads, 0, s>>>(rp, n, chunk, light_deg, scratch, item_row, item_k);
+}
+
+// ------------------------------------------------------------------ balanced work partition
+
+__global__ void __launch_bounds__(kThreads) k_unit_cost(const int64_t* rp, int64_t n, const int32_t* item_row,
+                                                        const int32_t* item_k, int64_t n_items, int64_t n_units,
+                                                        int light_deg, int64_t* cost) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c;
+        if (u < n_items) {
+            const int64_t r = item_row[u];
+            const int64_t rb = rp[r], re = rp[r + 1];
+            const int64_t beg = rb + (int64_t)item_k[u] * kItemNnz;
+            const int64_t end = beg + kItemNnz < re ? beg + kItemNnz : re;
+            c = (end - beg) + kItemCost;
+        } else {
+            const int64_t t = u - n_items;
+            c = 0;
+            for (int64_t r = t * 32; r < t * 32 + 32 && r < n; ++r) {
+                const int64_t d = rp[r + 1] - rp[r];
+                c += d <= light_deg ? d + kTileRowCost : 1;
+            }
+        }
+        cost[u] = c;
+    }
+}
+
+// exclusive prefix sum of N values in one CTA: prefix[0..N]
+__global__ void __launch_bounds__(kThreads) k_scan_costs(const int64_t* cost, int64_t N, int64_t* prefix) {
+    __shared__ int64_t part[kThreads];
+    const int64_t chunk = (N + blockDim.x - 1) / blockDim.x;
+    const int64_t b = threadIdx.x * chunk;
+    const int64_t e = b + chunk < N ? b + chunk : N;
+    int64_t s = 0;
+    for (int64_t u = b; u < e; ++u) s += cost[u];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int q = 0; q < (int)blockDim.x; ++q) {
+            const int64_t v = part[q];
+            part[q] = acc;
+            acc += v;
+        }
+        prefix[N] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[threadIdx.x];
+    for (int64_t u = b; u < e; ++u) {
+        prefix[u] = acc;
+        acc += cost[u];
+    }
+}
+
+// warp w starts at the first unit whose prefix reaches w * total / W
+__global__ void k_warp_starts(const int64_t* prefix, int64_t N, int W, int32_t* ws) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w > W) return;
+    if (w == W) { ws[W] = (int32_t)N; return; }
+    const int64_t total = prefix[N];
+    const int64_t target = (int64_t)(((__int128)total * w) / W);
+    int64_t lo = 0, hi = N;                                  // first u in [0, N] with prefix[u] >= target
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (prefix[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    ws[w] = (int32_t)lo;
+}
+
+void setup_partition(const int64_t* rp, int64_t n, const int32_t* item_row, const int32_t* item_k, int64_t n_items,
+                     int light_deg, int n_warps, int64_t* cost_tmp, int64_t* prefix_tmp, int32_t* warp_start,
+                     cudaStream_t s) {
+    const int64_t n_units = n_items + (n + 31) / 32;
+    k_unit_cost<<<1024, kThreads, 0, s>>>(rp, n, item_row, item_k, n_items, n_units, light_deg, cost_tmp);
+    k_scan_costs<<<1, kThreads, 0, s>>>(cost_tmp, n_units, prefix_tmp);
+    k_warp_starts<<<(n_warps + 1 + kThreads - 1) / kThreads, kThreads, 0, s>>>(prefix_tmp, n_units, n_warps,
+                                                                              warp_start);
 }
 
 // flag bits: 1 row_ptr not monotone / bad ends, 2 column out of range, 4 self loop,

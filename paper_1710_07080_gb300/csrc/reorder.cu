@@ -1,0 +1,108 @@
+// reorder.cu -- optional relabelling of the vertices by descending degree (stable: equal degrees
+// keep their original order).  On power-law graphs most stored entries point at the few
+// high-degree vertices; numbering them first packs their vector entries into a small block that
+// stays in L1/L2, so the gathers of the SpMV mostly hit cache.  The relabelled CSR is owned by
+// the solver; vectors cross the API in the caller's numbering.
+#include <cub/cub.cuh>
+
+#include "internal.h"
+
+namespace isira {
+
+__global__ void k_reorder_keys(const int64_t* rp, int64_t n, int64_t maxdeg, uint32_t* keys, int32_t* vals) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        keys[v] = (uint32_t)(maxdeg - (rp[v + 1] - rp[v]));
+        vals[v] = (int32_t)v;
+    }
+}
+
+__global__ void k_new_degrees(const int64_t* rp, const int32_t* perm, int64_t n, int64_t* deg_new, int32_t* inv) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i == n) {
+            deg_new[n] = 0;
+        } else {
+            const int64_t o = perm[i];
+            deg_new[i] = rp[o + 1] - rp[o];
+            inv[o] = (int32_t)i;
+        }
+    }
+}
+
+// one warp per new row: copy the old row's neighbours, renamed
+__global__ void __launch_bounds__(kThreads) k_permute_cols(const int64_t* rp, const int32_t* ci, const int32_t* perm,
+                                                           const int32_t* inv, const int64_t* rp2, int64_t n,
+                                                           int32_t* ci2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n; i += nw) {
+        const int64_t o = perm[i];
+        const int64_t b = rp[o], d = rp[o + 1] - b, b2 = rp2[i];
+        for (int64_t j = lane; j < d; j += 32) ci2[b2 + j] = inv[ci[b + j]];
+    }
+}
+
+template <typename T>
+__global__ void k_gather_perm(const T* src, const int32_t* perm, int64_t n, T* dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[perm[i]];
+}
+
+template <typename T>
+__global__ void k_scatter_perm(const T* src, const int32_t* perm, int64_t n, T* dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[perm[i]] = src[i];
+}
+
+cudaError_t build_reordered_graph(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int64_t maxdeg,
+                                  int64_t* rp2, int32_t* ci2, int32_t* perm, int32_t* inv, cudaStream_t s) {
+    uint32_t *k0 = nullptr, *k1 = nullptr;
+    int32_t* v0 = nullptr;
+    int64_t* deg = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0, scan_bytes = 0;
+    cudaError_t e = cudaSuccess;
+    const int grid = 1024;
+#define CK(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
+    CK(cudaMalloc(&k0, sizeof(uint32_t) * n));
+    CK(cudaMalloc(&k1, sizeof(uint32_t) * n));
+    CK(cudaMalloc(&v0, sizeof(int32_t) * n));
+    CK(cudaMalloc(&deg, sizeof(int64_t) * (n + 1)));
+    k_reorder_keys<<<grid, kThreads, 0, s>>>(rp, n, maxdeg, k0, v0);
+    CK(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k0, k1, v0, perm, (int)n, 0, 32, s));
+    CK(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, deg, rp2, (int)(n + 1), s));
+    if (scan_bytes > tmp_bytes) tmp_bytes = scan_bytes;
+    CK(cudaMalloc(&tmp, tmp_bytes));
+    CK(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k0, k1, v0, perm, (int)n, 0, 32, s));
+    k_new_degrees<<<grid, kThreads, 0, s>>>(rp, perm, n, deg, inv);
+    CK(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, deg, rp2, (int)(n + 1), s));
+    k_permute_cols<<<grid, kThreads, 0, s>>>(rp, ci, perm, inv, rp2, n, ci2);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+#undef CK
+done:
+    if (k0) cudaFree(k0);
+    if (k1) cudaFree(k1);
+    if (v0) cudaFree(v0);
+    if (deg) cudaFree(deg);
+    if (tmp) cudaFree(tmp);
+    (void)nnz;
+    return e;
+}
+
+template <typename T>
+void to_internal(const T* src, const int32_t* perm, int64_t n, T* dst, cudaStream_t s) {
+    k_gather_perm<T><<<608, kThreads, 0, s>>>(src, perm, n, dst);
+}
+
+template <typename T>
+void to_external(const T* src, const int32_t* perm, int64_t n, T* dst, cudaStream_t s) {
+    k_scatter_perm<T><<<608, kThreads, 0, s>>>(src, perm, n, dst);
+}
+
+template void to_internal<float>(const float*, const int32_t*, int64_t, float*, cudaStream_t);
+template void to_internal<double>(const double*, const int32_t*, int64_t, double*, cudaStream_t);
+template void to_external<float>(const float*, const int32_t*, int64_t, float*, cudaStream_t);
+template void to_external<double>(const double*, const int32_t*, int64_t, double*, cudaStream_t);
+
+}  // namespace isira

@@ -56,6 +56,13 @@ struct isira_handle_s {
     int32_t* item_k = nullptr;
     double* item_partial = nullptr;
     unsigned* item_count = nullptr;
+    int32_t* warp_start = nullptr;
+    // optional internal relabelling (opts.reorder): owned CSR, perm[new] = old, inv[old] = new
+    int64_t* own_rp = nullptr;
+    int32_t* own_ci = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* inv = nullptr;
+    int64_t trim_user = 0;
     int64_t n_long = 0, n_items = 0;
     RowSched rs{};
     int lanes = 8;
@@ -91,6 +98,10 @@ struct isira_handle_s {
     isira_stats stats{};
     int profiling = 0;
     std::vector<cudaEvent_t> ev;
+    // device-driven inner loop: one instantiated graph per deflation-rank bucket (c = 0, <=8, <=12, <=16, <=24, <=32)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t inner_graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int pending_inner_stats = 0;
 };
 
 namespace {
@@ -158,10 +169,40 @@ void sync(isira_handle h) {
 
 volatile HostStatus* hst(isira_handle h) { return h->hs; }
 
-// One inner solve on R (right-hand side) into Z (FP64, back-mapped).  Returns iterations.
+int nc_bucket(int c) { return c == 0 ? 0 : (c <= 8 ? 1 : (c <= 12 ? 2 : (c <= 16 ? 3 : (c <= 24 ? 4 : 5)))); }
+
+// WHILE(cond) { phase 1; phase 2 } with phase 2's last CTA setting cond = !done.  The kernels
+// read the per-solve shift and rank from device state, so one graph serves every solve of a bucket.
+template <typename T>
+cudaGraphExec_t build_inner_graph(isira_handle h, const InnerArgs<T>& a) {
+    if (!h->cap_stream) ck(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    ck(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hc;
+    ck(cudaGraphConditionalHandleCreate(&hc, g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hc;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    ck(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    ck(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    inner_phase1<T>(a, h->lanes, h->cap_stream);
+    inner_phase2_cond<T>(a, hc, h->cap_stream);
+    ck(cudaStreamEndCapture(h->cap_stream, &body));
+    cudaGraphExec_t ex = nullptr;
+    ck(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    return ex;
+}
+
+// One inner solve on R (right-hand side) into Z (FP64, back-mapped).  Chunked mode returns the
+// iteration count; graph mode returns -1 (the count is read at the next synchronisation).
 template <typename T>
 int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* Vt, int64_t ldv, double tau,
-              int max_it, bool gram_dirty, const double* R, const double* rnorm_dev) {
+              int max_it, bool gram_dirty, const double* R, const double* rnorm_dev, bool allow_graph = false) {
     InnerArgs<T> a = make_args<T>(h, b, sigma, c, Vt, ldv, tau, max_it);
     cudaStream_t s = h->stream;
     if (gram_dirty && c > 0) {
@@ -171,6 +212,16 @@ int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* 
     inner_prep_launch<T>(a, R, rnorm_dev, s);
     inner_phase2<T>(a, 1, s);
     h->stats.kernel_launches += 2;
+    if (allow_graph && h->opts.inner_graph && !h->profiling) {
+        const int bkt = nc_bucket(c);
+        if (!h->inner_graph[bkt]) h->inner_graph[bkt] = build_inner_graph<T>(h, a);
+        ck(cudaGraphLaunch(h->inner_graph[bkt], s));
+        inner_finalize_to<T>(a, h->Z, s);
+        h->stats.kernel_launches += 1;
+        h->stats.inner_solves += 1;
+        h->pending_inner_stats = 1;
+        return -1;
+    }
     const int chunk = h->opts.inner_chunk > 0 ? h->opts.inner_chunk : 16;
     int launched = 0;
     while (true) {
@@ -237,6 +288,13 @@ bool expand_basis(isira_handle h, int k, int c) {
         outer_cgs2(oa, k, c, s);
         h->stats.kernel_launches += 3;
         sync(h);
+        if (h->pending_inner_stats) {   // the graph-driven inner solve has finished by now
+            const int its = hst(h)->inner_iters;
+            h->stats.inner_iters += its;
+            h->stats.spmv_launches += its;
+            h->stats.kernel_launches += 2 * its;
+            h->pending_inner_stats = 0;
+        }
         const double zin = hst(h)->cgs_in, zout = hst(h)->cgs_out;
         if (zout > 1e-10 * zin && zout > 0.0 && std::isfinite(zout)) {
             outer_expand(oa, k, h->lanes, s);
@@ -300,19 +358,65 @@ void choose_lanes(isira_handle h) {
 
 void free_handle(isira_handle h) {
     if (!h) return;
-    void* ptrs[] = {h->item_row, h->item_k, h->item_partial, h->item_count, h->U, h->W, h->V, h->H, h->theta, h->S, h->R, h->Z, h->dscratch,
+    void* ptrs[] = {h->own_rp, h->own_ci, h->perm, h->inv, h->item_row, h->item_k, h->item_partial,
+                    h->item_count, h->warp_start, h->U, h->W, h->V, h->H, h->theta, h->S, h->R, h->Z, h->dscratch,
                     h->partial, h->counter, h->Gm, h->Cinv, h->lam_dev, h->tres_dev, h->fb.base, h->fb.st,
                     h->db.base, h->db.st, h->Vt_f};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->hs) cudaFreeHost(h->hs);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    for (cudaGraphExec_t g : h->inner_graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 
 isira_status map_cuda(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) return ISIRA_ERR_OOM;
     return ISIRA_ERR_CUDA;
+}
+
+}  // namespace
+
+namespace {
+
+// V (caller's numbering, n-by-c, ld n) into the solver's numbering, ld h->ld, precision T
+template <typename T>
+T* internal_V(isira_handle h, const double* d_V, int c, cudaStream_t s) {
+    if (c <= 0) return nullptr;
+    double* Vd = nullptr;
+    ck(cudaMalloc(&Vd, sizeof(double) * (size_t)h->ld * c));
+    for (int t = 0; t < c; ++t) {
+        if (h->perm) to_internal<double>(d_V + (size_t)t * h->n, h->perm, h->n, Vd + (size_t)t * h->ld, s);
+        else ck(cudaMemcpyAsync(Vd + (size_t)t * h->ld, d_V + (size_t)t * h->n, sizeof(double) * h->n,
+                                cudaMemcpyDeviceToDevice, s));
+    }
+    if (sizeof(T) == sizeof(double)) return reinterpret_cast<T*>(Vd);
+    float* Vf = nullptr;
+    ck(cudaMalloc(&Vf, sizeof(float) * (size_t)h->ld * c));
+    for (int t = 0; t < c; ++t) copy_vcol<float>(Vd + (size_t)t * h->ld, Vf + (size_t)t * h->ld, h->n, s);
+    ck(cudaStreamSynchronize(s));
+    cudaFree(Vd);
+    return reinterpret_cast<T*>(Vf);
+}
+
+template <typename T>
+void apply_operator_t(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const double* d_V, const T* d_x,
+                      T* d_y) {
+    cudaStream_t s = h->stream;
+    alloc_inner(h, b);
+    T* Vt = internal_V<T>(h, d_V, c, s);
+    InnerArgs<T> a = make_args<T>(h, b, sigma, c, Vt, h->ld, 1e-3, 1);
+    if (h->perm) to_internal<T>(d_x, h->perm, h->n, a.z0, s);
+    else ck(cudaMemcpyAsync(a.z0, d_x, sizeof(T) * h->n, cudaMemcpyDeviceToDevice, s));
+    ck(cudaMemsetAsync(a.z0 + h->trim, 0, sizeof(T), s));   // x_i is treated as 0
+    inner_opstats<T>(a, a.z0, s);
+    inner_phase1<T>(a, h->lanes, s);
+    if (h->perm) to_external<T>(a.Y, h->perm, h->n, d_y, s);
+    else ck(cudaMemcpyAsync(d_y, a.Y, sizeof(T) * h->n, cudaMemcpyDeviceToDevice, s));
+    sync(h);
+    if (Vt) cudaFree(Vt);
 }
 
 }  // namespace
@@ -336,6 +440,8 @@ void isira_default_opts(isira_opts* o) {
     o->seed = 1;
     o->spmv_lanes = 0;
     o->inner_chunk = 16;
+    o->inner_graph = 1;
+    o->reorder = 0;
 }
 
 const char* isira_error_string(isira_status s) {
@@ -386,6 +492,26 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         int64_t* scratch = nullptr;
         ck(cudaMalloc(&scratch, sizeof(int64_t) * 5 * 1024));
         DegreeInfo di{};
+        int64_t user_trim = -1;
+        if (h->opts.reorder) {
+            setup_degrees(d_row_ptr, n, light_deg, nullptr, nullptr, 0, scratch, &di, s);   // max degree
+            ck(cudaMalloc(&h->own_rp, sizeof(int64_t) * (size_t)(n + 1)));
+            ck(cudaMalloc(&h->own_ci, sizeof(int32_t) * (size_t)nnz));
+            ck(cudaMalloc(&h->perm, sizeof(int32_t) * (size_t)n));
+            ck(cudaMalloc(&h->inv, sizeof(int32_t) * (size_t)n));
+            ck(build_reordered_graph(d_row_ptr, d_col_idx, n, nnz, di.max_degree, h->own_rp, h->own_ci, h->perm,
+                                     h->inv, s));
+            if (h->opts.trim_index >= 0 && h->opts.trim_index < n) {
+                int32_t t = 0;
+                ck(cudaMemcpy(&t, h->inv + h->opts.trim_index, sizeof(int32_t), cudaMemcpyDeviceToHost));
+                user_trim = h->opts.trim_index;
+                h->opts.trim_index = t;
+            }
+            d_row_ptr = h->own_rp;
+            d_col_idx = h->own_ci;
+            h->rp = d_row_ptr;
+            h->ci = d_col_idx;
+        }
         setup_degrees(d_row_ptr, n, light_deg, nullptr, nullptr, 0, scratch, &di, s);   // counts
         const size_t ni = (size_t)std::max<int64_t>(1, di.n_items);
         ck(cudaMalloc(&h->item_row, sizeof(int32_t) * ni));
@@ -399,6 +525,13 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         h->max_degree = di.max_degree;
         if (di.max_degree < 1) throw StatusError{ISIRA_ERR_BAD_GRAPH};
         h->trim = (h->opts.trim_index >= 0 && h->opts.trim_index < n) ? h->opts.trim_index : di.argmax;
+        h->trim_user = h->trim;
+        if (h->perm) {
+            int32_t t = 0;
+            ck(cudaMemcpy(&t, h->perm + h->trim, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            h->trim_user = t;
+            if (user_trim >= 0) h->opts.trim_index = user_trim;
+        }
         h->delta = h->opts.delta > 0.0 ? h->opts.delta : 2.0 * (double)di.max_degree;
         h->normL = 2.0 * (double)di.max_degree;
         h->n_long = di.n_long;
@@ -414,12 +547,24 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         rs.item_count = h->item_count;
         rs.n_items = (int)di.n_items;
         rs.light_deg = light_deg;
-        const int64_t ntiles = (n + 31) / 32;
-        rs.item_blocks = di.n_items > 0 ? (int)std::min<int64_t>((di.n_items + kWarps - 1) / kWarps,
-                                                                   (int64_t)h->nsm * 8)
-                                        : 0;
-        rs.light_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + kWarps - 1) / kWarps,
-                                                                      (int64_t)h->nsm * 8));
+        // one launch wave of warps (4 CTAs per SM), each with an equal share of the estimated cost
+        const int64_t n_units = di.n_items + (n + 31) / 32;
+        if (n_units > INT32_MAX) throw StatusError{ISIRA_ERR_INVALID_ARG};
+        rs.n_warps = (int)std::max<int64_t>(kWarps, std::min<int64_t>((int64_t)h->nsm * 4 * kWarps,
+                                                                      (n_units + kWarps - 1) / kWarps * kWarps));
+        ck(cudaMalloc(&h->warp_start, sizeof(int32_t) * (size_t)(rs.n_warps + 1)));
+        {
+            int64_t* cost = nullptr;
+            int64_t* prefix = nullptr;
+            ck(cudaMalloc(&cost, sizeof(int64_t) * (size_t)n_units));
+            ck(cudaMalloc(&prefix, sizeof(int64_t) * (size_t)(n_units + 1)));
+            setup_partition(d_row_ptr, n, h->item_row, h->item_k, di.n_items, light_deg, rs.n_warps, cost, prefix,
+                            h->warp_start, s);
+            sync(h);
+            cudaFree(cost);
+            cudaFree(prefix);
+        }
+        rs.warp_start = h->warp_start;
         h->ew_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)h->nsm * 4));
         h->ts_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64, (int64_t)h->nsm * 2));
         // shared scratch for block partial sums: 512 slots x the largest grid
@@ -449,7 +594,7 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         choose_lanes(h);
         h->stats.n = n;
         h->stats.nnz = nnz;
-        h->stats.trim_index = h->trim;
+        h->stats.trim_index = h->trim_user;
         h->stats.max_degree = h->max_degree;
         h->stats.delta = h->delta;
         h->stats.norm_L = h->normL;
@@ -519,7 +664,8 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         OuterArgs oa = make_outer(h);
         ck(cudaMemsetAsync(h->H, 0, sizeof(double) * kMMax * kMMax, s));
         // start basis U_{k0}, k0 = 1 (Algorithm 2 REQUIRE): the given vector, or a SplitMix64 one
-        if (d_u0) ck(cudaMemcpyAsync(h->Z, d_u0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+        if (d_u0 && h->perm) to_internal<double>(d_u0, h->perm, h->n, h->Z, s);
+        else if (d_u0) ck(cudaMemcpyAsync(h->Z, d_u0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
         else outer_random(oa, o.seed, 0, s);
         h->stats.kernel_launches += d_u0 ? 0 : 1;
         if (!expand_basis(h, 0, 0)) throw StatusError{ISIRA_ERR_NO_CONVERGENCE};
@@ -577,9 +723,11 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
             }
             // line 17: inner solve of Eq. 2.14 and back-map Eq. 2.5 -> Z
             if (h->opts.precision == ISIRA_MIXED)
-                run_inner<float>(h, h->fb, sig, c, h->Vt_f, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch);
+                run_inner<float>(h, h->fb, sig, c, h->Vt_f, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch,
+                                 true);
             else
-                run_inner<double>(h, h->db, sig, c, h->V, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch);
+                run_inner<double>(h, h->db, sig, c, h->V, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch,
+                                  true);
             gram_dirty = false;
             // lines 18-19: orthonormalise against [U V 1] and expand U, W, H
             if (!expand_basis(h, k, c)) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
@@ -612,9 +760,13 @@ isira_status isira_eigpairs(isira_handle h, double* h_eigvals, double* d_eigvecs
         if (h_eigvals)
             for (int j = 0; j < c; ++j) h_eigvals[j] = h->lam[order[j]];
         if (d_eigvecs)
-            for (int j = 0; j < c; ++j)
-                ck(cudaMemcpyAsync(d_eigvecs + (size_t)j * h->n, h->V + (size_t)order[j] * h->ld,
-                                   sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+            for (int j = 0; j < c; ++j) {
+                if (h->perm)
+                    to_external<double>(h->V + (size_t)order[j] * h->ld, h->perm, h->n, d_eigvecs + (size_t)j * h->n, s);
+                else
+                    ck(cudaMemcpyAsync(d_eigvecs + (size_t)j * h->n, h->V + (size_t)order[j] * h->ld,
+                                       sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+            }
         if (h_true_resid) {
             ck(cudaMemcpyAsync(h->lam_dev, h->lam.data(), sizeof(double) * c, cudaMemcpyHostToDevice, s));
             OuterArgs oa = make_outer(h);
@@ -638,40 +790,11 @@ isira_status isira_apply_operator(isira_handle h, int precision, double sigma, i
         (precision != ISIRA_FP64 && precision != ISIRA_MIXED))
         return ISIRA_ERR_INVALID_ARG;
     try {
-        cudaStream_t s = h->stream;
-        if (precision == ISIRA_MIXED) {
-            alloc_inner(h, h->fb);
-            float* Vt = nullptr;
-            if (c > 0) {
-                ck(cudaMalloc(&Vt, sizeof(float) * (size_t)h->ld * c));
-                for (int t = 0; t < c; ++t) copy_vcol<float>(d_V + (size_t)t * h->n, Vt + (size_t)t * h->ld, h->n, s);
-            }
-            InnerArgs<float> a = make_args<float>(h, h->fb, sigma, c, Vt, h->ld, 1e-3, 1);
-            ck(cudaMemcpyAsync(a.z0, d_x, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, s));
-            ck(cudaMemsetAsync(a.z0 + h->trim, 0, sizeof(float), s));   // x_i is treated as 0
-            inner_opstats<float>(a, a.z0, s);
-            inner_phase1<float>(a, h->lanes, s);
-            ck(cudaMemcpyAsync(d_y, a.Y, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, s));
-            sync(h);
-            if (Vt) cudaFree(Vt);
-        } else {
-            alloc_inner(h, h->db);
-            double* Vt = nullptr;
-            if (c > 0) {
-                ck(cudaMalloc(&Vt, sizeof(double) * (size_t)h->ld * c));
-                for (int t = 0; t < c; ++t)
-                    ck(cudaMemcpyAsync(Vt + (size_t)t * h->ld, d_V + (size_t)t * h->n, sizeof(double) * h->n,
-                                       cudaMemcpyDeviceToDevice, s));
-            }
-            InnerArgs<double> a = make_args<double>(h, h->db, sigma, c, Vt, h->ld, 1e-3, 1);
-            ck(cudaMemcpyAsync(a.z0, d_x, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
-            ck(cudaMemsetAsync(a.z0 + h->trim, 0, sizeof(double), s));  // x_i is treated as 0
-            inner_opstats<double>(a, a.z0, s);
-            inner_phase1<double>(a, h->lanes, s);
-            ck(cudaMemcpyAsync(d_y, a.Y, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
-            sync(h);
-            if (Vt) cudaFree(Vt);
-        }
+        if (precision == ISIRA_MIXED)
+            apply_operator_t<float>(h, h->fb, sigma, c, d_V, static_cast<const float*>(d_x), static_cast<float*>(d_y));
+        else
+            apply_operator_t<double>(h, h->db, sigma, c, d_V, static_cast<const double*>(d_x),
+                                     static_cast<double*>(d_y));
     } catch (CudaError& e) {
         return map_cuda(e.e);
     }
@@ -686,36 +809,29 @@ isira_status isira_inner_solve(isira_handle h, int precision, double sigma, int 
     try {
         cudaStream_t s = h->stream;
         // the right-hand side goes through the residual buffer, its norm through the scalar area
-        ck(cudaMemcpyAsync(h->R, d_r, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+        if (h->perm) to_internal<double>(d_r, h->perm, h->n, h->R, s);
+        else ck(cudaMemcpyAsync(h->R, d_r, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
         const double one = 1.0;
         ck(cudaMemcpyAsync(h->dscratch + 300, &one, sizeof(double), cudaMemcpyHostToDevice, s));
         int its = 0;
         if (precision == ISIRA_MIXED) {
             alloc_inner(h, h->fb);
-            float* Vt = nullptr;
-            if (c > 0) {
-                ck(cudaMalloc(&Vt, sizeof(float) * (size_t)h->ld * c));
-                for (int t = 0; t < c; ++t) copy_vcol<float>(d_V + (size_t)t * h->n, Vt + (size_t)t * h->ld, h->n, s);
-            }
+            float* Vt = internal_V<float>(h, d_V, c, s);
             its = run_inner<float>(h, h->fb, sigma, c, Vt, h->ld, tau, max_it, true, h->R, h->dscratch + 300);
+            sync(h);
             if (Vt) cudaFree(Vt);
         } else {
             alloc_inner(h, h->db);
-            double* Vt = nullptr;
-            if (c > 0) {
-                ck(cudaMalloc(&Vt, sizeof(double) * (size_t)h->ld * c));
-                for (int t = 0; t < c; ++t)
-                    ck(cudaMemcpyAsync(Vt + (size_t)t * h->ld, d_V + (size_t)t * h->n, sizeof(double) * h->n,
-                                       cudaMemcpyDeviceToDevice, s));
-            }
+            double* Vt = internal_V<double>(h, d_V, c, s);
             its = run_inner<double>(h, h->db, sigma, c, Vt, h->ld, tau, max_it, true, h->R, h->dscratch + 300);
+            sync(h);
             if (Vt) cudaFree(Vt);
         }
         // back-map (Eq. 2.5): remove the mean; the trimmed entry is already zero
         OuterArgs oa = make_outer(h);
         outer_cgs2(oa, 0, 0, s);   // with an empty basis the two passes only subtract the mean
-        sync(h);
-        ck(cudaMemcpyAsync(d_z, h->Z, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+        if (h->perm) to_external<double>(h->Z, h->perm, h->n, d_z, s);
+        else ck(cudaMemcpyAsync(d_z, h->Z, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
         sync(h);
         if (iters) *iters = its;
         if (relres) *relres = hst(h)->inner_relres;

@@ -328,3 +328,83 @@ def workload(name: str) -> Graph:
     if name == "rgg4M":
         return rgg(4_000_000, 12.0, seed=1)
     raise KeyError(name)
+
+
+# --------------------------------------------------------------------------- GPU generation (large graphs)
+
+def _splitmix64_torch(seed: int, counter):
+    """splitmix64(seed, counter) on int64 torch tensors: wrapping multiply, logical right shifts."""
+    import torch
+
+    def u64(v):  # reinterpret an unsigned 64-bit constant as int64
+        return v - (1 << 64) if v >= (1 << 63) else v
+
+    def lsr(z, s):
+        return (z >> s) & ((1 << (64 - s)) - 1)
+
+    z = torch.full_like(counter, u64(seed & 0xFFFFFFFFFFFFFFFF)) + (counter + 1) * u64(0x9E3779B97F4A7C15)
+    z = (z ^ lsr(z, 30)) * u64(0xBF58476D1CE4E5B9)
+    z = (z ^ lsr(z, 27)) * u64(0x94D049BB133111EB)
+    return z ^ lsr(z, 31)
+
+
+def _uniform01_torch(seed: int, counter):
+    return _splitmix64_torch(seed, counter).__rshift__(11).bitwise_and((1 << 53) - 1).double() * (1.0 / 9007199254740992.0)
+
+
+def rmat_gpu(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+             seed: int = 1, device: str = "cuda", batch: int = 1 << 25):
+    """The graph of rmat(scale, ...) (same draws, same symmetrisation, deduplication, largest
+    component and relabelling) built with torch on the GPU.  Returns (row_ptr, col_idx) as
+    device tensors (int64, int32)."""
+    import torch
+    n = 1 << scale
+    E = edge_factor * n
+    ab, abc = a + b, a + b + c
+    keys = []
+    for e0 in range(0, E, batch):
+        e = torch.arange(e0, min(E, e0 + batch), dtype=torch.int64, device=device)
+        u = torch.zeros_like(e)
+        v = torch.zeros_like(e)
+        for lvl in range(scale):
+            x = _uniform01_torch(seed, e * scale + lvl)
+            bit = 1 << (scale - 1 - lvl)
+            down = x >= ab
+            right = ((x >= a) & (x < ab)) | (x >= abc)
+            u += down.to(torch.int64) * bit
+            v += right.to(torch.int64) * bit
+        keep = u != v
+        u, v = u[keep], v[keep]
+        keys.append(u * n + v)
+        keys.append(v * n + u)
+        del e, x, down, right
+    key = torch.unique(torch.cat(keys))          # sorted, deduplicated
+    del keys
+    rows = key // n
+    cols = key - rows * n
+    del key
+    # connected components by min-label propagation (labels converge to the component minimum)
+    lab = torch.arange(n, dtype=torch.int64, device=device)
+    while True:
+        nl = lab.clone()
+        nl.scatter_reduce_(0, rows, lab[cols], reduce="amin")
+        nl = torch.minimum(nl, nl[nl])           # pointer jumping
+        if torch.equal(nl, lab):
+            break
+        lab = nl
+    present = torch.zeros(n, dtype=torch.bool, device=device)
+    present[rows] = True
+    counts = torch.bincount(lab[present], minlength=n)
+    best = int(torch.argmax(counts).item())      # largest component; ties -> smallest label (= smallest id)
+    keepv = lab == best
+    keepv &= present if counts[best] > 1 else keepv
+    newid = torch.full((n,), -1, dtype=torch.int64, device=device)
+    kept = torch.nonzero(keepv).flatten()
+    newid[kept] = torch.arange(kept.numel(), dtype=torch.int64, device=device)
+    sel = keepv[rows]
+    r2 = newid[rows[sel]]
+    c2 = newid[cols[sel]]
+    m = kept.numel()
+    rp = torch.zeros(m + 1, dtype=torch.int64, device=device)
+    rp[1:] = torch.cumsum(torch.bincount(r2, minlength=m), 0)
+    return rp, c2.to(torch.int32)

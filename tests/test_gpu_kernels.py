@@ -50,13 +50,13 @@ def test_operator_fp64_integer_inputs_bit_exact(isira, name, lanes):
 
 
 @pytest.mark.parametrize("name", list(graphs().keys()))
-@pytest.mark.parametrize("lanes", [1, 4, 32])
+@pytest.mark.parametrize("lanes,reorder", [(1, 0), (4, 0), (32, 0), (4, 1)])
 @pytest.mark.parametrize("sigma,c", [(0.0, 0), (0.37, 0), (0.21, 3), (1.7, 9)])
-def test_operator_fp64_matches_oracle(isira, name, lanes, sigma, c):
+def test_operator_fp64_matches_oracle(isira, name, lanes, reorder, sigma, c):
     g = graphs()[name]
     rp, ci = dev_graph(g)
     rng = np.random.default_rng(lanes + c)
-    with isira.Solver(rp, ci, precision=isira.ISIRA_FP64, spmv_lanes=lanes) as s:
+    with isira.Solver(rp, ci, precision=isira.ISIRA_FP64, spmv_lanes=lanes, reorder=reorder) as s:
         st = s.stats()
         trim, delta = st["trim_index"], st["delta"]
         x = rng.standard_normal(g.n)
@@ -134,12 +134,11 @@ def test_sym_eig_degenerate_and_diagonal(isira):
 
 
 @pytest.mark.parametrize("name", ["grid31x33", "rmat12", "er3000"])
-@pytest.mark.parametrize("sigma,c", [(0.0, 0), (0.15, 2)])
-def test_inner_solve_fp64_matches_oracle(isira, name, sigma, c):
+@pytest.mark.parametrize("sigma,c,reorder", [(0.0, 0, 0), (0.15, 2, 0), (0.15, 2, 1)])
+def test_inner_solve_fp64_matches_oracle(isira, name, sigma, c, reorder):
     g = graphs()[name]
     rp, ci = dev_graph(g)
-    L = None
-    with isira.Solver(rp, ci, precision=isira.ISIRA_FP64) as s:
+    with isira.Solver(rp, ci, precision=isira.ISIRA_FP64, reorder=reorder) as s:
         st = s.stats()
         trim, delta = st["trim_index"], st["delta"]
         rng = np.random.default_rng(1)

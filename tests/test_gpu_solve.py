@@ -122,13 +122,14 @@ def test_small_graphs_vs_dense_definition(isira, prec, g, d):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("scale", [12, 14])
-def test_rmat_vs_algorithm_oracle(isira, prec, scale):
-    """R-MAT LCC (heavy-tailed degrees): GPU vs the FP64 algorithm oracle and LAPACK/ARPACK."""
+@pytest.mark.parametrize("scale,reorder", [(12, 0), (14, 0), (12, 1), (14, 1)])
+def test_rmat_vs_algorithm_oracle(isira, prec, scale, reorder):
+    """R-MAT LCC (heavy-tailed degrees): GPU vs the FP64 algorithm oracle and LAPACK/ARPACK, in the
+    caller's vertex numbering and with the solver's internal degree-descending relabelling."""
     g = sg.rmat(scale)
     normL = 2.0 * g.degrees.max()
     tol = 1e-12 * normL
-    res = run(isira, g, 10, prec, tol=tol)
+    res = run(isira, g, 10, prec, tol=tol, reorder=reorder)
     assert res.status == isira.ISIRA_OK
     lam, V = check_pairs(g, res, 10, rel_res=1e-11)
     lam_or, V_or, st = oracle.isira(g.row_ptr, g.col_idx, 10, sg.start_vector(g.n, 1), eps=tol, tau_inner=1e-3)
@@ -166,9 +167,12 @@ def test_options_trim_drop_rank1_restart(isira):
     g = sg.grid2d(30, 29)
     ref = cf.grid2d(30, 29)[1:7]
     for kw in [dict(trim_index=0), dict(trim_index=g.n - 1), dict(drop_rank1=1), dict(m=12, q=7),
-               dict(delta=100.0), dict(inner_chunk=3), dict(tau_inner=1e-2)]:
+               dict(delta=100.0), dict(inner_chunk=3, inner_graph=0), dict(tau_inner=1e-2), dict(reorder=1),
+               dict(reorder=1, trim_index=5)]:
         res = run(isira, g, 6, "mixed", tol=1e-10, **kw)
         assert res.status == isira.ISIRA_OK, kw
+        if "trim_index" in kw:
+            assert res.stats["trim_index"] == kw["trim_index"]
         lam, _ = check_pairs(g, res, 6)
         np.testing.assert_allclose(lam, ref, rtol=1e-9, err_msg=str(kw))
     res = run(isira, g, 6, "mixed", tol=1e-10, m=12, q=7)
