@@ -46,8 +46,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="rmat20")
-    p.add_argument("--k", type=int, default=10)
-    p.add_argument("--rel-tol", type=float, default=1e-8)
+    p.add_argument("--k", type=int, default=0, help="eigenpairs (0: the workload's k)")
+    p.add_argument("--rel-tol", type=float, default=0.0, help="relative residual (0: the workload's)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--single-solve", choices=["fp64", "mixed"], default=None,
                    help="create one solver and run one solve, nothing else (for profiler captures)")
@@ -69,6 +69,9 @@ def solver_opts(args):
 def load_workload(args):
     import numpy as np
     import synthgraphs as sg
+    if args.workload == "rmat24":
+        rp, ci = sg.rmat_gpu(24)
+        return sg.Graph(rp.cpu().numpy(), ci.cpu().numpy(), "rmat24")
     if args.graph_cache:
         path = os.path.join(args.graph_cache, f"{args.workload}.npz")
         if os.path.exists(path):
@@ -81,16 +84,42 @@ def load_workload(args):
     return sg.workload(args.workload)
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """Max of a per-rank scalar over all ranks (replicas: each rank solved its own copy)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+# the five configurations: k, the precision of the headline value, tolerance
+WORKLOADS = {
+    "rmat20": dict(k=10, prec="fp64", tol=("rel", 1e-8),
+                   desc="R-MAT scale 20, edge factor 16, a,b,c,d=.57/.19/.19/.05, seed 1, symmetrised LCC"),
+    "grid100x100": dict(k=5, prec="fp64", tol=("abs", 1e-10), desc="2-D 5-point grid 100 x 100"),
+    "grid128^3": dict(k=20, prec="mixed", tol=("rel", 1e-8), desc="3-D 7-point grid 128^3"),
+    "rgg4M": dict(k=20, prec="mixed", tol=("rel", 1e-8),
+                  desc="random geometric graph, unit square, n = 4e6, r = sqrt(12/(pi n)), seed 1, LCC"),
+    "rmat24": dict(k=10, prec="mixed", tol=("rel", 1e-8),
+                   desc="R-MAT scale 24, edge factor 16, same a,b,c,d, seed 1, symmetrised LCC (GPU generator)"),
+    "batch256": dict(k=8, prec="mixed", tol=("rel", 1e-8),
+                     desc="256 graphs, n log-uniform in [1e3, 2e5]: ER mean degree 8 / 2-D grid / WS k=10 p=0.1"),
+}
+
+
 def workload_config(name, g, k, rel_tol):
-    desc = {"rmat20": "R-MAT scale 20, edge factor 16, a,b,c,d=.57/.19/.19/.05, seed 1, symmetrised LCC"}
-    return {"workload": f"{name}-lcc k={k} fp64", "graph": desc.get(name, name), "n": g.n, "nnz": g.nnz,
-            "k": k, "resid_rel": rel_tol, "norm_L": "2*max_degree", "l2": "flushed (512 MB write) between steps",
-            "start_vector": "splitmix64 seed 1, centred, unit norm"}
+    spec = WORKLOADS[name]
+    kind, t = spec["tol"]
+    return {"workload": f"{name} k={k} {spec['prec']}", "graph": spec["desc"], "n": g.n, "nnz": g.nnz,
+            "k": k, ("resid_rel" if kind == "rel" else "tol_abs"): t, "norm_L": "2*max_degree",
+            "l2": "flushed (512 MB write) between steps", "start_vector": "splitmix64 seed 1, centred, unit norm"}
 
 
 def config_with_opts(cfg, args):
@@ -259,9 +288,14 @@ def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return
+    if args.workload not in ("rmat20",):
+        print(json.dumps({"impl": "reference", "unavailable": "oracle work counts exist only for rmat20"}))
+        return
+    spec = WORKLOADS[args.workload]
+    k = args.k if args.k > 0 else spec["k"]
     g = load_workload(args)
     normL = 2.0 * float(g.degrees.max())
-    tol = args.rel_tol * normL
+    tol = (args.rel_tol if args.rel_tol > 0 else spec["tol"][1]) * normL
     u0 = sg.start_vector(g.n, 1)
     full = oracle_full_counts(args.workload)
     if full is None:
@@ -269,18 +303,60 @@ def run_reference(args):
         return
     values, st = [], None
     for i in range(args.warmup + args.steps):
-        _, st = oracle_sample(g, args.k, tol, u0, SAMPLE_STEPS)
+        _, st = oracle_sample(g, k, tol, u0, SAMPLE_STEPS)
         if i >= args.warmup:
             values.append(project_oracle(st, full))
     value = statistics.mean(values)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.workload, g, args.k, args.rel_tol),
+            "config": workload_config(args.workload, g, k, tol / normL),
             "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
                              "sample": sample_text(st, full)},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------------- batch
+
+def run_batch(args):
+    """256 graphs of uneven size solved together through isira_batch_* (one step = the whole batch)."""
+    import numpy as np
+    import torch
+
+    import paper_1710_07080_gb300 as isira
+    import synthgraphs as sg
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = WORKLOADS["batch256"]
+    k = args.k if args.k > 0 else spec["k"]
+    rel = args.rel_tol if args.rel_tol > 0 else spec["tol"][1]
+    graphs = sg.batch_family(256, 1000, 200000, seed=1)
+    dg = [(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev)) for g in graphs]
+    b = isira.Batch(dg, precision=isira.ISIRA_MIXED, **solver_opts(args))
+    times = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = b.solve(k, rel_tol=rel)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    iters = [b.stats(g)["inner_iters"] for g in range(len(graphs))]
+    res = [float(b.eigpairs(g)[2].max()) for g in range(len(graphs))]
+    value = statistics.mean(times)
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+            "config": {"workload": f"batch256 k={k} mixed", "graph": spec["desc"], "graphs": len(graphs),
+                       "sum_n": int(sum(g.n for g in graphs)), "sum_nnz": int(sum(g.nnz for g in graphs)),
+                       "resid_rel": rel},
+            "batch": {"status": st, "max_true_resid_rel": max(res), "inner_iters_max": max(iters),
+                      "inner_iters_sum": int(sum(iters))}}
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------------------------- our arm
@@ -308,17 +384,20 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def reduce_max(x):
+        return max_over_ranks(x, dist, dev)
 
+    if args.workload == "batch256":
+        run_batch(args)
+        return
+    spec = WORKLOADS[args.workload]
     g = load_workload(args)
-    n, Z, k = g.n, g.nnz, args.k
+    n, Z = g.n, g.nnz
+    k = args.k if args.k > 0 else spec["k"]
     normL = 2.0 * float(g.degrees.max())
-    tol = args.rel_tol * normL
+    kind, tv = spec["tol"]
+    tol = (args.rel_tol if args.rel_tol > 0 else tv) * normL if kind == "rel" else tv
+    rel_for_cfg = tol / normL
     if args.single_solve:
         prec = isira.ISIRA_FP64 if args.single_solve == "fp64" else isira.ISIRA_MIXED
         with isira.Solver(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev),
@@ -401,9 +480,9 @@ def main():
             e2e_times.append(dt)
     del vec_host
 
-    value = max_over_ranks(statistics.mean(t64))
-    value_mx = max_over_ranks(statistics.mean(tmx))
-    e2e = max_over_ranks(statistics.mean(e2e_times))
+    value = reduce_max(statistics.mean(t64))
+    value_mx = reduce_max(statistics.mean(tmx))
+    e2e = reduce_max(statistics.mean(e2e_times))
 
     # roofline of the dominant kernel (phase 1 of the FP64 inner solve), from the live events
     p1_ms = sum(s["inner_phase1_ms"] for s in sp64)
@@ -425,7 +504,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": config_with_opts(workload_config(args.workload, g, k, args.rel_tol), args),
+        "dtype": "f64", "data": "synthetic", "config": config_with_opts(workload_config(args.workload, g, k, rel_for_cfg), args),
         "mixed": {"value": value_mx, "unit": "s", "dtype": "f32 inner / f64 outer",
                   "speedup_vs_fp64": value / value_mx if value_mx else None,
                   "roofline": {"kernel": "k_phase1<float>", "bound": "hbm", "achieved": achieved_mx, "peak": peak,
@@ -449,10 +528,21 @@ def main():
                      "bytes_per_launch": bytes_launch, "avg_deflation_rank": p1_c, "traffic": traffic},
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "pinned host CSR -> isira_create -> isira_solve -> isira_eigpairs -> host"},
-        "gpu_launches": int(sum(s["kernel_launches"] for s in st64)),
+        "gpu_launches": int(sum(s["kernel_launches"] for s in (stmx if spec["prec"] == "mixed" else st64))),
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if spec["prec"] == "mixed":
+        # the configuration names the mixed form: it is the headline, FP64 is reported beside it
+        fp64_part = {"value": line["value"], "unit": "s", "dtype": "f64", "roofline": line["roofline"],
+                     **line["fp64"]}
+        mixed = line.pop("mixed")
+        mroof = mixed.pop("roofline")
+        line.update(value=mixed["value"], ms_per_step=mixed["value"] * 1e3, dtype="f32 inner / f64 outer",
+                    roofline={**mroof, "peak_source": peak_src, "hbm_frac": mroof["frac"],
+                              "traffic": ncu_traffic(f"phase1_f32_{args.workload}")})
+        line["fp64"] = fp64_part
+        line["mixed"] = mixed
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "rmat20":
         full = oracle_full_counts(args.workload)
         dt, st = oracle_sample(g, k, tol, u0_h.numpy(), SAMPLE_STEPS)
         if full is not None:

@@ -81,7 +81,7 @@ typedef struct {
     int reorder;          /* 1: relabel the vertices internally by descending degree (stable), which
                              packs the vectors' entries of high-degree vertices together for cache
                              reuse in the SpMV; vectors at the API stay in the caller's numbering;
-                             0: use the caller's numbering */
+                             0: use the caller's numbering (default 1) */
 } isira_opts;
 
 typedef struct {

@@ -32,6 +32,12 @@ __device__ __forceinline__ T precond_diag(T deg, T sigma) {
     return m < h ? h : m;
 }
 
+// 1/D_r: from the FP64 array the prep kernel filled, or computed (FP32 mode)
+template <typename T>
+__device__ __forceinline__ T inv_diag(const T* dinv, int64_t r, T D) {
+    return dinv ? dinv[r] : T(1) / D;
+}
+
 template <typename T>
 __device__ __forceinline__ T* wbuf(const InnerArgs<T>& a, int j) {
     int r = j % 3;
@@ -46,6 +52,7 @@ struct Phase1Epi {
     T sigma;
     int c;
     const T* Vt;
+    const T* dinv;
     T* Y; T* x;
     const T* zc; const T* zp; const T* wo2; const T* wo1; T* wn;
     T inv_beta, cprev, inv_oldb, s_term, oldeps, dlt, inv_gamma, phi;
@@ -78,7 +85,8 @@ struct Phase1Epi {
         }
         Y[r] = y1;
         acc[0] += zr * inv_beta * y1;
-        const T yd = y1 / D;
+        if (NC == 0) return;
+        const T yd = y1 * inv_diag(dinv, r, D);
 #pragma unroll
         for (int t = 0; t < NC; ++t)   // second read of the row of Vh: an L1 hit
             if (t < c) acc[1 + t] += Vt[(int64_t)t * ldv + r] * yd;
@@ -99,6 +107,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_phase1(InnerArgs<T> a) {
     epi.sigma = st->p_sigma;
     epi.c = c;
     epi.Vt = a.Vt;
+    epi.dinv = a.dinv;
     epi.Y = a.Y;
     epi.x = a.x;
     epi.zc = ((k - 1) & 1) ? a.z1 : a.z0;
@@ -194,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, c
         }
         T y = a.Y[r];
         if (!init) y -= coef * D * zc[r] + q1;
-        const T z = (y - q2) / D;
+        const T z = (y - q2) * inv_diag(a.dinv, r, D);
         zn[r] = z;
         acc[0] += y * z;
         acc[1] += z;
@@ -299,12 +308,16 @@ __global__ void __launch_bounds__(kThreads) k_prep(InnerArgs<T> a, const double*
         a.wb0[r] = T(0);
         a.wb1[r] = T(0);
         a.wb2[r] = T(0);
-        if (NC > 0 && r != a.trim) {
+        if (a.dinv || NC > 0) {
             const T degT = (T)(a.rs.rp[r + 1] - a.rs.rp[r]);
-            const T bd = b / precond_diag(degT, a.sigma);
+            const T di = T(1) / precond_diag(degT, a.sigma);
+            if (a.dinv) a.dinv[r] = di;
+            if (NC > 0 && r != a.trim) {
+                const T bd = b * di;
 #pragma unroll
-            for (int t = 0; t < NC; ++t)
-                if (t < a.c) acc[t] += a.Vt[(int64_t)t * a.ldv + r] * bd;
+                for (int t = 0; t < NC; ++t)
+                    if (t < a.c) acc[t] += a.Vt[(int64_t)t * a.ldv + r] * bd;
+            }
         }
     }
     const int nv = NC > 0 ? a.c : 0;

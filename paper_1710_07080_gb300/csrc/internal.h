@@ -39,6 +39,7 @@ struct InnerArgs {
     int64_t ldv;
     int c;
     T* z0; T* z1; T* Y; T* wb0; T* wb1; T* wb2; T* x;
+    T* dinv;                    // FP64 mode: 1/D per row, written by the prep kernel (nullptr: divide)
     T* partial; int pstride;
     unsigned* counter;
     InnerState<T>* st;

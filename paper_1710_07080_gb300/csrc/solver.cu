@@ -109,9 +109,11 @@ namespace {
 template <typename T>
 void alloc_inner(isira_handle h, InnerBuffers<T>& b) {
     if (b.base) return;
-    ck(cudaMalloc(&b.base, sizeof(T) * (size_t)h->ld * 7));
+    // 7 MINRES vectors, plus the reciprocal preconditioner diagonal in FP64 mode
+    const int nvec = sizeof(T) == sizeof(double) ? 8 : 7;
+    ck(cudaMalloc(&b.base, sizeof(T) * (size_t)h->ld * nvec));
     ck(cudaMalloc(&b.st, sizeof(InnerState<T>)));
-    ck(cudaMemsetAsync(b.base, 0, sizeof(T) * (size_t)h->ld * 7, h->stream));
+    ck(cudaMemsetAsync(b.base, 0, sizeof(T) * (size_t)h->ld * nvec, h->stream));
     ck(cudaMemsetAsync(b.st, 0, sizeof(InnerState<T>), h->stream));
 }
 
@@ -131,6 +133,7 @@ InnerArgs<T> make_args(isira_handle h, InnerBuffers<T>& b, double sigma, int c, 
     const int64_t ld = h->ld;
     a.z0 = v; a.z1 = v + ld; a.Y = v + 2 * ld; a.wb0 = v + 3 * ld; a.wb1 = v + 4 * ld; a.wb2 = v + 5 * ld;
     a.x = v + 6 * ld;
+    a.dinv = sizeof(T) == sizeof(double) ? v + 7 * ld : nullptr;
     a.partial = reinterpret_cast<T*>(h->partial);
     a.pstride = (int)(h->partial_elems / 512);
     a.counter = h->counter;
@@ -441,7 +444,7 @@ void isira_default_opts(isira_opts* o) {
     o->spmv_lanes = 0;
     o->inner_chunk = 16;
     o->inner_graph = 1;
-    o->reorder = 0;
+    o->reorder = 1;
 }
 
 const char* isira_error_string(isira_status s) {
