@@ -98,10 +98,10 @@ typedef struct {
     int restarts, breakdowns;
     long long inner_iters;    /* total MINRES iterations */
     long long inner_solves;
-    long long spmv_launches;  /* launches of the inner operator kernel (phase 1) */
+    long long spmv_launches;  /* launches of the inner operator's gather kernel (phase 1) */
     double solve_ms;          /* host wall time of the last isira_solve */
-    double inner_phase1_ms;   /* summed device time of phase-1 launches (only with profiling on) */
-    long long inner_phase1_timed; /* number of phase-1 launches timed */
+    double inner_phase1_ms;   /* summed device time of the phase-1 gather launches (profiling on only) */
+    long long inner_phase1_timed; /* number of phase-1 gather launches timed */
     long long inner_phase1_csum;  /* sum of the deflation rank c over the timed phase-1 launches */
     long long kernel_launches;    /* kernels launched by the last isira_solve */
 } isira_stats;

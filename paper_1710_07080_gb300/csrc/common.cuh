@@ -140,14 +140,30 @@ struct RowSched {
     int n_items;
     int n_warps;
     int light_deg;
+    int hub;                                // x[0:hub] is staged in shared memory (0: none)
     __host__ __device__ int grid() const { return n_warps / kWarps; }
 };
 
 // Calls epi(row, degree, sum_{c in N(row)} x[c]) exactly once for every row 0..n-1 (with a
 // zero sum for row `skip`).  G = lanes per light row (1, 2, 4, 8, 16 or 32).
+// Shared-memory capacity for the hub block of x: 16 KB per CTA.
+template <typename T>
+struct HubCap { static constexpr int value = 16384 / sizeof(T); };
+
+template <typename T>
+__device__ __forceinline__ T gather_x(const T* __restrict__ x, const T* sx, int hub, int32_t c) {
+    return c < hub ? sx[c] : __ldg(x + c);
+}
+
 template <typename T, int G, class Epi>
 __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* __restrict__ x, Epi& epi,
                                                     int64_t skip) {
+    // With the solver's degree-descending numbering the first `hub` vertices are the hubs most
+    // entries point at; their x values are staged once per CTA and read from shared memory.
+    __shared__ T sx[HubCap<T>::value];
+    const int hub = S.hub < HubCap<T>::value ? S.hub : HubCap<T>::value;
+    for (int i = threadIdx.x; i < hub; i += blockDim.x) sx[i] = x[i];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int u_beg = S.warp_start[gw], u_end = S.warp_start[gw + 1];
@@ -170,10 +186,10 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
             // a predicated batch of 8 independent index loads, then 8 independent gathers
             int32_t c[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) c[q] = (e + 32 * q < end) ? __ldg(S.ci + e + 32 * q) : -1;
+            for (int q = 0; q < 8; ++q) c[q] = (e + 32 * q < end) ? __ldcs(S.ci + e + 32 * q) : -1;
             T v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = c[q] >= 0 ? __ldg(x + c[q]) : T(0);
+            for (int q = 0; q < 8; ++q) v[q] = c[q] >= 0 ? gather_x(x, sx, hub, c[q]) : T(0);
             s0 += (v[0] + v[1]) + (v[2] + v[3]);
             s1 += (v[4] + v[5]) + (v[6] + v[7]);
         }
@@ -234,10 +250,10 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
                 for (int64_t e = sb + (lane % G); e < se; e += 8 * G) {
                     int32_t c[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) c[q] = (e + q * G < se) ? __ldg(S.ci + e + q * G) : -1;
+                    for (int q = 0; q < 8; ++q) c[q] = (e + q * G < se) ? __ldcs(S.ci + e + q * G) : -1;
                     T v[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) v[q] = c[q] >= 0 ? __ldg(x + c[q]) : T(0);
+                    for (int q = 0; q < 8; ++q) v[q] = c[q] >= 0 ? gather_x(x, sx, hub, c[q]) : T(0);
                     s += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
                 }
             }
@@ -249,6 +265,13 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
         if (light) epi(row, deg, mine);
     }
 }
+
+// Epilogue of the plain gather: g[row] = sum over the row (0 for the skipped row).
+template <typename T>
+struct GatherStore {
+    T* g;
+    __device__ __forceinline__ void operator()(int64_t r, int64_t, T s) { g[r] = s; }
+};
 
 // ------------------------------------------------------------------ SplitMix64
 __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t counter) {

@@ -93,8 +93,22 @@ struct Phase1Epi {
     }
 };
 
-template <typename T, int G, int NC>
-__global__ void __launch_bounds__(kThreads, 4) k_phase1(InnerArgs<T> a) {
+// Gather of phase 1: g_r = sum_{c in N(r)} z_k[c] (the trimmed row gathers nothing).  Only this
+// kernel walks the CSR; it keeps few registers so many warps keep loads in flight.
+template <typename T, int G>
+__global__ void __launch_bounds__(kThreads, 6) k_phase1_gather(InnerArgs<T> a) {
+    const InnerState<T>* st = a.st;
+    if (st->done) return;
+    const int itn = st->itn;                 // iteration k = itn + 1 gathers z_k = z[itn & 1]
+    const T* zc = (itn & 1) ? a.z1 : a.z0;
+    GatherStore<T> epi{a.gsum};
+    for_each_row_gather<T, G>(a.rs, zc, epi, a.trim);
+}
+
+// Row epilogue of phase 1, one thread per row (coalesced): the operator value from the gathered
+// sum, the Lanczos update, the deferred w/x update, and the reductions alpha_k, Vh^T D^{-1} y1.
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
     InnerState<T>* st = a.st;
     if (st->done) return;
     const int k = st->itn + 1;
@@ -132,7 +146,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_phase1(InnerArgs<T> a) {
     for (int t = 0; t < 1 + NC; ++t) epi.acc[t] = T(0);
     __syncthreads();
 
-    for_each_row_gather<T, G>(a.rs, epi.zc, epi, a.trim);
+    const int64_t n = a.rs.n;
+    const int64_t* __restrict__ rp = a.rs.rp;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        epi(r, rp[r + 1] - rp[r], a.gsum[r]);
 
     if (block_partials_arrive<T, 1 + NC>(epi.acc, 1 + c, a.partial, a.pstride, a.counter)) {
         last_block_sum(a.partial, a.pstride, gridDim.x, 1 + c, red, a.counter);
@@ -533,24 +550,30 @@ __global__ void k_copy_vcol(const double* src, T* dst, int64_t n) {
         else { F(32); }         \
     } while (0)
 
-template <typename T, int G>
-static void phase1_launch_g(const InnerArgs<T>& a, cudaStream_t s) {
+template <typename T>
+void inner_gather(const InnerArgs<T>& a, int lanes, cudaStream_t s) {
     const int grid = a.rs.grid();
-#define L1(NC) k_phase1<T, G, NC><<<grid, kThreads, 0, s>>>(a)
+    switch (lanes) {
+        case 1: k_phase1_gather<T, 1><<<grid, kThreads, 0, s>>>(a); break;
+        case 2: k_phase1_gather<T, 2><<<grid, kThreads, 0, s>>>(a); break;
+        case 4: k_phase1_gather<T, 4><<<grid, kThreads, 0, s>>>(a); break;
+        case 8: k_phase1_gather<T, 8><<<grid, kThreads, 0, s>>>(a); break;
+        case 16: k_phase1_gather<T, 16><<<grid, kThreads, 0, s>>>(a); break;
+        default: k_phase1_gather<T, 32><<<grid, kThreads, 0, s>>>(a); break;
+    }
+}
+
+template <typename T>
+void inner_rows(const InnerArgs<T>& a, cudaStream_t s) {
+#define L1(NC) k_phase1<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a)
     ISIRA_NC_DISPATCH(a.c, L1);
 #undef L1
 }
 
 template <typename T>
 void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s) {
-    switch (lanes) {
-        case 1: phase1_launch_g<T, 1>(a, s); break;
-        case 2: phase1_launch_g<T, 2>(a, s); break;
-        case 4: phase1_launch_g<T, 4>(a, s); break;
-        case 8: phase1_launch_g<T, 8>(a, s); break;
-        case 16: phase1_launch_g<T, 16>(a, s); break;
-        default: phase1_launch_g<T, 32>(a, s); break;
-    }
+    inner_gather<T>(a, lanes, s);
+    inner_rows<T>(a, s);
 }
 
 template <typename T>
@@ -605,6 +628,8 @@ void copy_vcol(const double* src, T* dst, int64_t n, cudaStream_t s) {
 
 #define ISIRA_INSTANTIATE_INNER(T)                                                                        \
     template void inner_phase1<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
+    template void inner_gather<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
+    template void inner_rows<T>(const InnerArgs<T>&, cudaStream_t);                                      \
     template void inner_phase2<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
     template void inner_phase2_cond<T>(const InnerArgs<T>&, cudaGraphConditionalHandle, cudaStream_t);   \
     template void inner_prep_launch<T>(const InnerArgs<T>&, const double*, const double*, cudaStream_t); \

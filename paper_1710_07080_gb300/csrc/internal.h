@@ -40,6 +40,7 @@ struct InnerArgs {
     int c;
     T* z0; T* z1; T* Y; T* wb0; T* wb1; T* wb2; T* x;
     T* dinv;                    // FP64 mode: 1/D per row, written by the prep kernel (nullptr: divide)
+    T* gsum;                    // per-row neighbour sums written by the gather kernel
     T* partial; int pstride;
     unsigned* counter;
     InnerState<T>* st;
@@ -53,7 +54,9 @@ struct InnerArgs {
 // Launchers (instantiated for float and double in inner_f32.cu / inner_f64.cu).
 template <typename T> void inner_prep_launch(const InnerArgs<T>& a, const double* R, const double* rnorm_dev,
                                              cudaStream_t s);
-template <typename T> void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s);
+template <typename T> void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s);   // gather + rows
+template <typename T> void inner_gather(const InnerArgs<T>& a, int lanes, cudaStream_t s);
+template <typename T> void inner_rows(const InnerArgs<T>& a, cudaStream_t s);
 template <typename T> void inner_phase2(const InnerArgs<T>& a, int init, cudaStream_t s);
 // phase 2 inside a CUDA graph whose WHILE node is driven by `cond` (set to 0 once the solve stops)
 template <typename T> void inner_phase2_cond(const InnerArgs<T>& a, cudaGraphConditionalHandle cond,
@@ -67,6 +70,7 @@ template <typename T> void copy_vcol(const double* src, T* dst, int64_t n, cudaS
 // ------------------------------------------------------------------ outer loop (FP64)
 struct OuterArgs {
     RowSched rs;
+    double* gsum;               // per-row neighbour sums of the gather kernel
     int64_t n, ld;              // leading dimension of U, W, V
     double* U; double* W; double* V;
     double* H;                  // kMMax x kMMax, column-major, ld kMMax

@@ -429,37 +429,29 @@ void outer_cgs2(const OuterArgs& a, int k, int c, cudaStream_t s) {
 
 // ------------------------------------------------------------------ expand (lines 4 and 19)
 
-struct ExpandEpi {
-    const double* Z; double* u; double* w; double inv;
-    __device__ __forceinline__ void operator()(int64_t r, int64_t deg, double gsum) {
-        const double ur = Z[r] * inv;
-        u[r] = ur;
-        w[r] = (double)deg * ur - gsum * inv;
-    }
-};
-
+// Plain gather g[r] = sum_{c in N(r)} x[c] over the full Laplacian (no trimmed row).
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_expand(OuterArgs a, int k) {
-    ExpandEpi e;
-    e.Z = a.Z;
-    e.u = a.U + (int64_t)k * a.ld;
-    e.w = a.W + (int64_t)k * a.ld;
-    const double nz = a.dscratch[2];
-    e.inv = nz > 0.0 ? 1.0 / nz : 0.0;
-    for_each_row_gather<double, G>(a.rs, a.Z, e, -1);
+__global__ void __launch_bounds__(kThreads, 6) k_gather_plain(RowSched rs, const double* x, double* g) {
+    GatherStore<double> epi{g};
+    for_each_row_gather<double, G>(rs, x, epi, -1);
 }
 
-struct LapEpi {
-    const double* x; double* y;
-    __device__ __forceinline__ void operator()(int64_t r, int64_t deg, double gsum) {
-        y[r] = (double)deg * x[r] - gsum;
+// U(:,k) = Z / ||Z||, W(:,k) = L U(:,k) from the gathered sums of Z
+__global__ void __launch_bounds__(kThreads) k_expand_rows(OuterArgs a, int k) {
+    const double nz = a.dscratch[2];
+    const double inv = nz > 0.0 ? 1.0 / nz : 0.0;
+    double* u = a.U + (int64_t)k * a.ld;
+    double* w = a.W + (int64_t)k * a.ld;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += (int64_t)gridDim.x * blockDim.x) {
+        const double ur = a.Z[r] * inv;
+        u[r] = ur;
+        w[r] = (double)(a.rs.rp[r + 1] - a.rs.rp[r]) * ur - a.gsum[r] * inv;
     }
-};
+}
 
-template <int G>
-__global__ void __launch_bounds__(kThreads) k_laplacian(RowSched rs, const double* x, double* y) {
-    LapEpi e{x, y};
-    for_each_row_gather<double, G>(rs, x, e, -1);
+__global__ void __launch_bounds__(kThreads) k_laplacian_rows(OuterArgs a, const double* x, double* y) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += (int64_t)gridDim.x * blockDim.x)
+        y[r] = (double)(a.rs.rp[r + 1] - a.rs.rp[r]) * x[r] - a.gsum[r];
 }
 
 #define ISIRA_LANES_DISPATCH(lanes, F) \
@@ -474,20 +466,24 @@ __global__ void __launch_bounds__(kThreads) k_laplacian(RowSched rs, const doubl
         }                              \
     } while (0)
 
+static void outer_gather(const OuterArgs& a, const double* x, int lanes, cudaStream_t s) {
+#define LG(G) k_gather_plain<G><<<a.rs.grid(), kThreads, 0, s>>>(a.rs, x, a.gsum)
+    ISIRA_LANES_DISPATCH(lanes, LG);
+#undef LG
+}
+
 void outer_expand(const OuterArgs& a, int k, int lanes, cudaStream_t s) {
     ts_smem_attr();
-#define LE(G) k_expand<G><<<a.rs.grid(), kThreads, 0, s>>>(a, k)
-    ISIRA_LANES_DISPATCH(lanes, LE);
-#undef LE
+    outer_gather(a, a.Z, lanes, s);
+    k_expand_rows<<<a.ew_blocks, kThreads, 0, s>>>(a, k);
     // H(0:k+1, k) = U(:, 0:k+1)^T W(:, k)
     k_tall_skinny<0><<<a.ts_blocks, kThreads, ts_smem(k + 1), s>>>(a, k + 1, 0, a.W + (int64_t)k * a.ld, nullptr,
                                                                    nullptr, nullptr, a.H, k);
 }
 
 void outer_laplacian(const OuterArgs& a, const double* x, double* y, int lanes, cudaStream_t s) {
-#define LL(G) k_laplacian<G><<<a.rs.grid(), kThreads, 0, s>>>(a.rs, x, y)
-    ISIRA_LANES_DISPATCH(lanes, LL);
-#undef LL
+    outer_gather(a, x, lanes, s);
+    k_laplacian_rows<<<a.ew_blocks, kThreads, 0, s>>>(a, x, y);
 }
 
 // ------------------------------------------------------------------ rotate (restart, purge)
@@ -559,24 +555,17 @@ void outer_random(const OuterArgs& a, uint64_t seed, uint64_t blk, cudaStream_t 
 
 // ------------------------------------------------------------------ true residual
 
-struct TrueResEpi {
-    const double* v; double lam; double acc[1];
-    __device__ __forceinline__ void operator()(int64_t r, int64_t deg, double gsum) {
-        const double d = (double)deg * v[r] - gsum - lam * v[r];
+// ||L v - lambda v||^2 from the gathered sums of v
+__global__ void __launch_bounds__(kThreads) k_trueres_rows(OuterArgs a, const double* v, const double* lam_dev, int j,
+                                                           double* out) {
+    __shared__ double red[1];
+    const double lam = lam_dev[j];
+    double acc[1] = {0.0};
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += (int64_t)gridDim.x * blockDim.x) {
+        const double d = (double)(a.rs.rp[r + 1] - a.rs.rp[r]) * v[r] - a.gsum[r] - lam * v[r];
         acc[0] += d * d;
     }
-};
-
-template <int G>
-__global__ void __launch_bounds__(kThreads) k_true_residual(OuterArgs a, const double* v, const double* lam_dev,
-                                                            int j, double* out) {
-    __shared__ double red[1];
-    TrueResEpi e;
-    e.v = v;
-    e.lam = lam_dev[j];
-    e.acc[0] = 0.0;
-    for_each_row_gather<double, G>(a.rs, v, e, -1);
-    if (block_partials_arrive<double, 1>(e.acc, 1, a.partial, a.pstride, a.counter)) {
+    if (block_partials_arrive<double, 1>(acc, 1, a.partial, a.pstride, a.counter)) {
         last_block_sum(a.partial, a.pstride, gridDim.x, 1, red, a.counter);
         if (threadIdx.x == 0) out[j] = red[0];
     }
@@ -585,9 +574,8 @@ __global__ void __launch_bounds__(kThreads) k_true_residual(OuterArgs a, const d
 void outer_true_residual(const OuterArgs& a, int d, const double* lam_dev, double* out, int lanes, cudaStream_t s) {
     for (int j = 0; j < d; ++j) {
         const double* v = a.V + (int64_t)j * a.ld;
-#define LT(G) k_true_residual<G><<<a.rs.grid(), kThreads, 0, s>>>(a, v, lam_dev, j, out)
-        ISIRA_LANES_DISPATCH(lanes, LT);
-#undef LT
+        outer_gather(a, v, lanes, s);
+        k_trueres_rows<<<a.ew_blocks, kThreads, 0, s>>>(a, v, lam_dev, j, out);
     }
 }
 

@@ -78,6 +78,7 @@ struct isira_handle_s {
     double* R = nullptr;
     double* Z = nullptr;
     double* dscratch = nullptr;
+    double* gsum = nullptr;       // gather output, n doubles (shared by both precisions)
     double* partial = nullptr;
     size_t partial_elems = 0;
     unsigned* counter = nullptr;
@@ -134,6 +135,7 @@ InnerArgs<T> make_args(isira_handle h, InnerBuffers<T>& b, double sigma, int c, 
     a.z0 = v; a.z1 = v + ld; a.Y = v + 2 * ld; a.wb0 = v + 3 * ld; a.wb1 = v + 4 * ld; a.wb2 = v + 5 * ld;
     a.x = v + 6 * ld;
     a.dinv = sizeof(T) == sizeof(double) ? v + 7 * ld : nullptr;
+    a.gsum = reinterpret_cast<T*>(h->gsum);
     a.partial = reinterpret_cast<T*>(h->partial);
     a.pstride = (int)(h->partial_elems / 512);
     a.counter = h->counter;
@@ -155,6 +157,7 @@ OuterArgs make_outer(isira_handle h) {
     a.U = h->U; a.W = h->W; a.V = h->V;
     a.H = h->H; a.theta = h->theta; a.S = h->S;
     a.R = h->R; a.Z = h->Z;
+    a.gsum = h->gsum;
     a.partial = h->partial;
     a.pstride = (int)(h->partial_elems / 512);
     a.counter = h->counter;
@@ -231,12 +234,13 @@ int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* 
         const bool prof = h->profiling != 0;
         for (int i = 0; i < chunk; ++i) {
             if (prof) ck(cudaEventRecord(h->ev[2 * i], s));
-            inner_phase1<T>(a, h->lanes, s);
+            inner_gather<T>(a, h->lanes, s);
             if (prof) ck(cudaEventRecord(h->ev[2 * i + 1], s));
+            inner_rows<T>(a, s);
             inner_phase2<T>(a, 0, s);
         }
         h->stats.spmv_launches += chunk;
-        h->stats.kernel_launches += 2 * chunk;
+        h->stats.kernel_launches += 3 * chunk;
         sync(h);
         const int itn = hst(h)->inner_iters;
         if (prof) {
@@ -295,13 +299,13 @@ bool expand_basis(isira_handle h, int k, int c) {
             const int its = hst(h)->inner_iters;
             h->stats.inner_iters += its;
             h->stats.spmv_launches += its;
-            h->stats.kernel_launches += 2 * its;
+            h->stats.kernel_launches += 3 * its;
             h->pending_inner_stats = 0;
         }
         const double zin = hst(h)->cgs_in, zout = hst(h)->cgs_out;
         if (zout > 1e-10 * zin && zout > 0.0 && std::isfinite(zout)) {
             outer_expand(oa, k, h->lanes, s);
-            h->stats.kernel_launches += 2;
+            h->stats.kernel_launches += 3;
             return true;
         }
         h->stats.breakdowns += 1;
@@ -361,7 +365,7 @@ void choose_lanes(isira_handle h) {
 
 void free_handle(isira_handle h) {
     if (!h) return;
-    void* ptrs[] = {h->own_rp, h->own_ci, h->perm, h->inv, h->item_row, h->item_k, h->item_partial,
+    void* ptrs[] = {h->gsum, h->own_rp, h->own_ci, h->perm, h->inv, h->item_row, h->item_k, h->item_partial,
                     h->item_count, h->warp_start, h->U, h->W, h->V, h->H, h->theta, h->S, h->R, h->Z, h->dscratch,
                     h->partial, h->counter, h->Gm, h->Cinv, h->lam_dev, h->tres_dev, h->fb.base, h->fb.st,
                     h->db.base, h->db.st, h->Vt_f};
@@ -550,10 +554,10 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         rs.item_count = h->item_count;
         rs.n_items = (int)di.n_items;
         rs.light_deg = light_deg;
-        // one launch wave of warps (4 CTAs per SM), each with an equal share of the estimated cost
+        // one launch wave of gather warps (6 CTAs per SM), each with an equal share of the estimated cost
         const int64_t n_units = di.n_items + (n + 31) / 32;
         if (n_units > INT32_MAX) throw StatusError{ISIRA_ERR_INVALID_ARG};
-        rs.n_warps = (int)std::max<int64_t>(kWarps, std::min<int64_t>((int64_t)h->nsm * 4 * kWarps,
+        rs.n_warps = (int)std::max<int64_t>(kWarps, std::min<int64_t>((int64_t)h->nsm * 6 * kWarps,
                                                                       (n_units + kWarps - 1) / kWarps * kWarps));
         ck(cudaMalloc(&h->warp_start, sizeof(int32_t) * (size_t)(rs.n_warps + 1)));
         {
@@ -568,6 +572,8 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
             cudaFree(prefix);
         }
         rs.warp_start = h->warp_start;
+        // stage the hub block of x only when the numbering puts the hubs first
+        rs.hub = h->perm ? (int)std::min<int64_t>(n, 1 << 20) : 0;
         h->ew_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)h->nsm * 4));
         h->ts_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64, (int64_t)h->nsm * 2));
         // shared scratch for block partial sums: 512 slots x the largest grid
@@ -581,6 +587,7 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         ck(cudaMalloc(&h->S, sizeof(double) * kMMax * kMMax));
         ck(cudaMalloc(&h->R, sizeof(double) * (size_t)h->ld));
         ck(cudaMalloc(&h->Z, sizeof(double) * (size_t)h->ld));
+        ck(cudaMalloc(&h->gsum, sizeof(double) * (size_t)h->ld));
         ck(cudaMalloc(&h->dscratch, sizeof(double) * 512));
         ck(cudaMalloc(&h->Gm, sizeof(double) * kCMax * kCMax));
         ck(cudaMalloc(&h->Cinv, sizeof(double) * kCMax * kCMax));
