@@ -82,6 +82,17 @@ typedef struct {
                              packs the vectors' entries of high-degree vertices together for cache
                              reuse in the SpMV; vectors at the API stay in the caller's numbering;
                              0: use the caller's numbering (default 1) */
+    int gather_block;     /* threads per CTA of the SpMV gather kernels: 256 (up to 6 CTAs per SM)
+                             or 1024 (one CTA per SM); 0: 1024 with relabelling, else 256 */
+    int hub_kb;           /* with relabelling, each gather CTA copies the vector entries of the first
+                             (highest-degree) vertices into this many KB of shared memory with one
+                             bulk asynchronous copy; 0: 192 (capped by the device), < 0: none */
+    int gather_sched;     /* 0: gather warps take work units from a device counter as they finish
+                             (balanced whatever the row costs); 1: a static partition by estimated
+                             cost.  Results are identical either way. */
+    int index_vec;        /* 1: with relabelling, read column indices in 128-bit chunks of the
+                             solver's padded copy; 0: 32-bit loads (default) */
+    int gather_chunk;     /* work units a gather warp takes at a time (1..32); 0: 2 */
 } isira_opts;
 
 typedef struct {
@@ -104,6 +115,10 @@ typedef struct {
     long long inner_phase1_timed; /* number of phase-1 gather launches timed */
     long long inner_phase1_csum;  /* sum of the deflation rank c over the timed phase-1 launches */
     long long kernel_launches;    /* kernels launched by the last isira_solve */
+    int gather_block;             /* threads per gather CTA in use */
+    int hub_bytes;                /* shared memory of a gather CTA holding hub vector entries */
+    long long hub_timeouts;       /* gather CTAs whose staging copy missed its wait limit (they then
+                                     read every entry from global memory; results unchanged) */
 } isira_stats;
 
 /* Fills *opts with the defaults listed above (precision = ISIRA_MIXED). */

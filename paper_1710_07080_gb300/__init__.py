@@ -40,7 +40,8 @@ class isira_opts(C.Structure):
                 ("max_inner", C.c_int), ("max_outer", C.c_int), ("trim_index", C.c_int64), ("delta", C.c_double),
                 ("sigma_omega", C.c_double), ("drop_rank1", C.c_int), ("validate", C.c_int), ("seed", C.c_uint64),
                 ("spmv_lanes", C.c_int), ("inner_chunk", C.c_int), ("inner_graph", C.c_int),
-                ("reorder", C.c_int)]
+                ("reorder", C.c_int), ("gather_block", C.c_int), ("hub_kb", C.c_int),
+                ("gather_sched", C.c_int), ("index_vec", C.c_int), ("gather_chunk", C.c_int)]
 
 
 class isira_stats(C.Structure):
@@ -50,7 +51,8 @@ class isira_stats(C.Structure):
                 ("outer_steps", C.c_int), ("restarts", C.c_int), ("breakdowns", C.c_int),
                 ("inner_iters", C.c_longlong), ("inner_solves", C.c_longlong), ("spmv_launches", C.c_longlong),
                 ("solve_ms", C.c_double), ("inner_phase1_ms", C.c_double), ("inner_phase1_timed", C.c_longlong),
-                ("inner_phase1_csum", C.c_longlong), ("kernel_launches", C.c_longlong)]
+                ("inner_phase1_csum", C.c_longlong), ("kernel_launches", C.c_longlong),
+                ("gather_block", C.c_int), ("hub_bytes", C.c_int), ("hub_timeouts", C.c_longlong)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

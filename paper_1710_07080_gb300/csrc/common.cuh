@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <initializer_list>
+
 namespace isira {
 
 constexpr int kThreads = 256;         // threads per CTA for every kernel here
@@ -125,6 +127,7 @@ constexpr int kItemNnz = 1024;
 // Work units are the items (0 .. n_items-1) followed by the light tiles; setup cuts the unit
 // list into n_warps ranges of equal estimated cost (one launch wave), warp w walking units
 // [warp_start[w], warp_start[w+1]).  The static partition keeps every reduction deterministic.
+constexpr int kUnitChunk = 2;      // default units a warp takes at a time (dynamic distribution)
 constexpr int kTileRowCost = 12;   // estimated cost of one row epilogue, in gathered entries
 constexpr int kItemCost = 32;      // fixed cost of one work item
 
@@ -140,60 +143,231 @@ struct RowSched {
     int n_items;
     int n_warps;
     int light_deg;
-    int hub;                                // x[0:hub] is staged in shared memory (0: none)
-    __host__ __device__ int grid() const { return n_warps / kWarps; }
+    int hub;                                // x[0:hub] may be staged in shared memory (0: none)
+    int hub_bytes;                          // dynamic shared memory of a gather CTA for that block
+    int tpb;                                // threads per gather CTA (kThreads or kBigBlock)
+    int ci_vec;                             // ci is 16-byte aligned and padded to a multiple of 4
+                                            // entries: 128-bit index loads
+    int dyn;                                // 1: dynamic unit distribution through sched
+    unsigned* sched;                        // [next unit, warps finished], zero between launches
+    int chunk;                              // units per take (1..32)
+    unsigned* hub_timeouts;                 // CTAs whose staging copy missed the wait limit
+    __host__ __device__ int grid() const { return n_warps / (tpb / 32); }
 };
 
-// Calls epi(row, degree, sum_{c in N(row)} x[c]) exactly once for every row 0..n-1 (with a
-// zero sum for row `skip`).  G = lanes per light row (1, 2, 4, 8, 16 or 32).
-// Shared-memory capacity for the hub block of x: 16 KB per CTA.
-template <typename T>
-struct HubCap { static constexpr int value = 16384 / sizeof(T); };
+constexpr int kBigBlock = 1024;             // one gather CTA per SM holding a large hub block
+constexpr int kDefaultHubBytes = 192 * 1024;  // hub block of a 1024-thread gather CTA
+
+// Calls F(G, TPB) with compile-time lanes per light row and threads per gather CTA.
+#define ISIRA_GATHER_DISPATCH(lanes, tpb, F) \
+    do {                                     \
+        if ((tpb) == kBigBlock) {            \
+            switch (lanes) {                 \
+                case 1: F(1, kBigBlock); break; \
+                case 2: F(2, kBigBlock); break; \
+                case 4: F(4, kBigBlock); break; \
+                case 8: F(8, kBigBlock); break; \
+                case 16: F(16, kBigBlock); break; \
+                default: F(32, kBigBlock); break; \
+            }                                \
+        } else {                             \
+            switch (lanes) {                 \
+                case 1: F(1, kThreads); break; \
+                case 2: F(2, kThreads); break; \
+                case 4: F(4, kThreads); break; \
+                case 8: F(8, kThreads); break; \
+                case 16: F(16, kThreads); break; \
+                default: F(32, kThreads); break; \
+            }                                \
+        }                                    \
+    } while (0)
 
 template <typename T>
 __device__ __forceinline__ T gather_x(const T* __restrict__ x, const T* sx, int hub, int32_t c) {
     return c < hub ? sx[c] : __ldg(x + c);
 }
 
+// ------------------------------------------------------------------ hub staging (TMA bulk copy)
+// The dynamic shared memory of a gather launch holds the hub block x[0:hub).
+extern __shared__ __align__(128) unsigned char g_dyn_smem[];
+
+constexpr int kHubWaitPolls = 1 << 20;      // x ~64 ns: a bound far above the copy's microseconds
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    for (int i = 0; i < kHubWaitPolls; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+        if (i >= 8) __nanosleep(64);
+    }
+    return false;
+}
+
+// Copies x[0:hub) into shared memory with one bulk asynchronous copy (the tensor memory
+// accelerator) that an mbarrier tracks; returns the number of staged entries (a multiple of
+// 16 bytes).  Should the copy not land within the wait limit, the CTA waits once more for the
+// copy in flight, counts the event and gathers everything from global memory (hub 0), which
+// gives the same sums.
+template <typename T>
+__device__ __forceinline__ int stage_hub(const RowSched& S, const T* __restrict__ x, T* sx) {
+    constexpr int kUnit = 16 / (int)sizeof(T);
+    int hub = S.hub < S.hub_bytes / (int)sizeof(T) ? S.hub : S.hub_bytes / (int)sizeof(T);
+    hub = hub / kUnit * kUnit;
+    if (hub <= 0) return 0;
+    if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0) {
+        for (int i = threadIdx.x; i < hub; i += blockDim.x) sx[i] = x[i];
+        __syncthreads();
+        return hub;
+    }
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned bar_a = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)hub * (unsigned)sizeof(T);
+        asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}"
+                     :: "r"(bar_a), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(smem_u32(sx)), "l"(x), "r"(bytes), "r"(bar_a) : "memory");
+    }
+    if (__syncthreads_and(mbar_wait_bounded(bar_a, 0))) return hub;
+    const bool landed = __syncthreads_and(mbar_wait_bounded(bar_a, 0));
+    if (threadIdx.x == 0) atomicAdd(S.hub_timeouts, 1u);
+    return landed ? hub : 0;
+}
+
+// Partial sum over the stored entries [beg, end) of ci taken by sub-lane j of a group of W lanes.
+// Each pass loads a batch of independent indices first and then issues all their gathers, so a
+// lane keeps a whole batch of loads in flight.  The summation order depends only on (beg, end,
+// W), never on the launch shape.
+//  * vector form (ci 16-byte aligned and padded): sub-lane j reads the 128-bit chunks starting at
+//    (beg rounded down to 4) + 4j + 4W*u, u < NB, and masks the entries outside [beg, end);
+//  * scalar form: sub-lane j reads entries beg + j + W*u, u < 8 (u < 4 in a short last pass).
+template <typename T, int W, int NB>
+__device__ __forceinline__ T seg_sum_vec(const int32_t* __restrict__ ci, const T* __restrict__ x, const T* sx,
+                                         int hub, int64_t beg, int64_t end, int j) {
+    T s0 = 0, s1 = 0;
+    for (int64_t base = (beg & ~(int64_t)3) + 4 * j; base < end; base += 4 * W * NB) {
+        int4 q[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int64_t p = base + 4 * W * u;
+            q[u] = p < end ? __ldcs(reinterpret_cast<const int4*>(ci + p)) : make_int4(0, 0, 0, 0);
+        }
+        T v[4 * NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int64_t p = base + 4 * W * u;
+            const int32_t cc[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                v[4 * u + w] = (p + w >= beg && p + w < end) ? gather_x(x, sx, hub, cc[w]) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const T t = (v[4 * u] + v[4 * u + 1]) + (v[4 * u + 2] + v[4 * u + 3]);
+            if (u & 1) s1 += t; else s0 += t;
+        }
+    }
+    return s0 + s1;
+}
+
+// One pass of the scalar form: sub-lane j takes entries e + W*q, q < Q (e = pass base + j).
+template <typename T, int W, int Q>
+__device__ __forceinline__ void scalar_pass(const int32_t* __restrict__ ci, const T* __restrict__ x, const T* sx,
+                                            int hub, int64_t e, int64_t end, T& s0, T& s1) {
+    int32_t c[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) c[q] = (e + W * q < end) ? __ldcs(ci + e + W * q) : -1;
+    T v[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) v[q] = c[q] >= 0 ? gather_x(x, sx, hub, c[q]) : T(0);
+    if constexpr (Q == 8) {
+        s0 += (v[0] + v[1]) + (v[2] + v[3]);
+        s1 += (v[4] + v[5]) + (v[6] + v[7]);
+    } else {
+        s0 += v[0] + v[1];
+        s1 += v[2] + v[3];
+    }
+}
+
+// Whole-warp segments (W = 32) end with a half-width pass when at most 4W entries remain, so
+// the tail adds fewer padding zeros.
+template <typename T, int W>
+__device__ __forceinline__ T seg_sum_scalar(const int32_t* __restrict__ ci, const T* __restrict__ x, const T* sx,
+                                            int hub, int64_t beg, int64_t end, int j) {
+    T s0 = 0, s1 = 0;
+    for (int64_t base = beg; base < end;) {
+        if (W == 32 && end - base <= 4 * W) {
+            scalar_pass<T, W, 4>(ci, x, sx, hub, base + j, end, s0, s1);
+            base += 4 * W;
+        } else {
+            scalar_pass<T, W, 8>(ci, x, sx, hub, base + j, end, s0, s1);
+            base += 8 * W;
+        }
+    }
+    return s0 + s1;
+}
+
+// 128-bit index chunks per lane and pass: 16 indices in flight per lane for FP32, 8 for FP64
+template <typename T>
+struct VecChunks { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
+
+template <typename T, int W>
+__device__ __forceinline__ T seg_sum(const RowSched& S, const T* __restrict__ x, const T* sx, int hub, int64_t beg,
+                                     int64_t end, int j) {
+    return S.ci_vec ? seg_sum_vec<T, W, VecChunks<T>::value>(S.ci, x, sx, hub, beg, end, j)
+                    : seg_sum_scalar<T, W>(S.ci, x, sx, hub, beg, end, j);
+}
+
+// Calls epi(row, degree, sum_{c in N(row)} x[c]) exactly once for every row 0..n-1 (with a
+// zero sum for row `skip`).  G = lanes per light row (1, 2, 4, 8, 16 or 32).
+// Launched with S.grid() CTAs of S.tpb threads and S.hub_bytes of dynamic shared memory.
 template <typename T, int G, class Epi>
 __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* __restrict__ x, Epi& epi,
                                                     int64_t skip) {
     // With the solver's degree-descending numbering the first `hub` vertices are the hubs most
     // entries point at; their x values are staged once per CTA and read from shared memory.
-    __shared__ T sx[HubCap<T>::value];
-    const int hub = S.hub < HubCap<T>::value ? S.hub : HubCap<T>::value;
-    for (int i = threadIdx.x; i < hub; i += blockDim.x) sx[i] = x[i];
-    __syncthreads();
+    T* sx = reinterpret_cast<T*>(g_dyn_smem);
+    const int hub = stage_hub<T>(S, x, sx);
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int u_beg = S.warp_start[gw], u_end = S.warp_start[gw + 1];
     // long rows: finished rows are collected one per lane and their epilogues run 32 at a time,
     // so the epilogue arithmetic uses every lane of the warp
     T* part = static_cast<T*>(S.item_partial);
     int64_t my_row = -1, my_deg = 0;
     T my_sum = 0;
     int nb = 0;                                            // rows collected (warp-uniform)
-    const int it_end = u_end < S.n_items ? u_end : S.n_items;
-    for (int it = u_beg; it < it_end; ++it) {
-        const int64_t r = S.item_row[it];
-        if (r == skip) continue;
-        const int kpos = S.item_k[it];
-        const int64_t rb = S.rp[r], re = S.rp[r + 1];
+    // item u's header (row, position in the row, row extent); loaded lane-parallel for a chunk
+    int h_row = -1, h_k = 0;
+    int64_t h_rb = 0, h_re = 0;
+    auto load_headers = [&](int u0, int u1) {
+        const int u = u0 + lane;
+        h_row = -1;
+        if (u < u1 && u < S.n_items) {
+            h_row = S.item_row[u];
+            h_k = S.item_k[u];
+            h_rb = S.rp[h_row];
+            h_re = S.rp[h_row + 1];
+        }
+    };
+    auto do_item = [&](int it, int j) {
+        const int64_t r = __shfl_sync(kFull, h_row, j);
+        const int kpos = __shfl_sync(kFull, h_k, j);
+        const int64_t rb = __shfl_sync(kFull, h_rb, j), re = __shfl_sync(kFull, h_re, j);
+        if (r == skip) return;
         const int64_t beg = rb + (int64_t)kpos * kItemNnz;
         const int64_t end = beg + kItemNnz < re ? beg + kItemNnz : re;
-        T s0 = 0, s1 = 0;
-        for (int64_t e = beg + lane; e < end; e += 256) {
-            // a predicated batch of 8 independent index loads, then 8 independent gathers
-            int32_t c[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) c[q] = (e + 32 * q < end) ? __ldcs(S.ci + e + 32 * q) : -1;
-            T v[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = c[q] >= 0 ? gather_x(x, sx, hub, c[q]) : T(0);
-            s0 += (v[0] + v[1]) + (v[2] + v[3]);
-            s1 += (v[4] + v[5]) + (v[6] + v[7]);
-        }
-        T s = warp_sum(s0 + s1);
+        T s = warp_sum(seg_sum<T, 32>(S, x, sx, hub, beg, end, lane));
         const int nit = (int)((re - rb + kItemNnz - 1) / kItemNnz);
         int done = 1;
         if (nit > 1) {
@@ -224,13 +398,10 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
                 nb = 0;
             }
         }
-    }
-    if (my_row >= 0) epi(my_row, my_deg, my_sum);
+    };
     // light tiles: 32 consecutive rows, G lanes per row, one lane per row for the epilogue
     constexpr int RPS = 32 / G;                            // rows per sub-pass
-    const int t_beg = (u_beg > S.n_items ? u_beg : S.n_items) - S.n_items;
-    const int t_end = u_end - S.n_items;
-    for (int tile = t_beg; tile < t_end; ++tile) {
+    auto do_tile = [&](int tile) {
         const int64_t row = (int64_t)tile * 32 + lane;
         const bool valid = row < S.n;
         int64_t beg = valid ? S.rp[row] : 0;
@@ -238,6 +409,7 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
         const int64_t deg = end - beg;
         const int light = valid && (deg <= S.light_deg || row == skip);
         if (row == skip) end = beg;                        // the skipped row gathers nothing
+        if (!__any_sync(kFull, light)) return;
         T mine = 0;
 #pragma unroll
         for (int sub = 0; sub < G; ++sub) {
@@ -245,25 +417,45 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
             const int64_t sb = __shfl_sync(kFull, beg, src);
             const int64_t se = __shfl_sync(kFull, end, src);
             const int sl = __shfl_sync(kFull, light, src);
-            T s = 0;
-            if (sl) {
-                for (int64_t e = sb + (lane % G); e < se; e += 8 * G) {
-                    int32_t c[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) c[q] = (e + q * G < se) ? __ldcs(S.ci + e + q * G) : -1;
-                    T v[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) v[q] = c[q] >= 0 ? gather_x(x, sx, hub, c[q]) : T(0);
-                    s += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
-                }
-            }
+            T s = sl ? seg_sum<T, G>(S, x, sx, hub, sb, se, lane % G) : T(0);
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
             const T t = __shfl_sync(kFull, s, (lane % RPS) * G);
             if (lane / RPS == sub) mine = t;
         }
         if (light) epi(row, deg, mine);
+    };
+    auto do_range = [&](int u0, int u1) {             // u1 - u0 <= 32
+        if (u0 < S.n_items) load_headers(u0, u1);
+        for (int u = u0; u < u1; ++u) {
+            if (u < S.n_items) do_item(u, u - u0); else do_tile(u - S.n_items);
+        }
+    };
+    const int n_units = S.n_items + (int)((S.n + 31) / 32);
+    if (S.dyn) {
+        // dynamic: warps take chunks of S.chunk units from a counter; the last warp to finish
+        // resets it for the next launch.  Which warp takes a unit never changes its sum.
+        for (;;) {
+            int u0 = 0;
+            if (lane == 0) u0 = (int)atomicAdd(S.sched, (unsigned)S.chunk);
+            u0 = __shfl_sync(kFull, u0, 0);
+            if (u0 >= n_units) break;             // the failing take precedes the fence below
+            do_range(u0, u0 + S.chunk < n_units ? u0 + S.chunk : n_units);
+        }
+        if (lane == 0) {
+            const unsigned n_warps = gridDim.x * (blockDim.x >> 5);
+            __threadfence();
+            if (atomicAdd(S.sched + 1, 1u) == n_warps - 1) {
+                S.sched[0] = 0u;
+                S.sched[1] = 0u;
+            }
+        }
+    } else {
+        const int gw = blockIdx.x * (int)(blockDim.x >> 5) + (threadIdx.x >> 5);
+        const int u_beg = S.warp_start[gw], u_end = S.warp_start[gw + 1];
+        for (int u = u_beg; u < u_end; u += 32) do_range(u, u + 32 < u_end ? u + 32 : u_end);
     }
+    if (my_row >= 0) epi(my_row, my_deg, my_sum);
 }
 
 // Epilogue of the plain gather: g[row] = sum over the row (0 for the skipped row).

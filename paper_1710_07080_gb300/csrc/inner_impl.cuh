@@ -95,8 +95,8 @@ struct Phase1Epi {
 
 // Gather of phase 1: g_r = sum_{c in N(r)} z_k[c] (the trimmed row gathers nothing).  Only this
 // kernel walks the CSR; it keeps few registers so many warps keep loads in flight.
-template <typename T, int G>
-__global__ void __launch_bounds__(kThreads, 6) k_phase1_gather(InnerArgs<T> a) {
+template <typename T, int G, int TPB>
+__global__ void __launch_bounds__(TPB, TPB == kThreads ? 4 : 1) k_phase1_gather(InnerArgs<T> a) {
     const InnerState<T>* st = a.st;
     if (st->done) return;
     const int itn = st->itn;                 // iteration k = itn + 1 gathers z_k = z[itn & 1]
@@ -552,15 +552,22 @@ __global__ void k_copy_vcol(const double* src, T* dst, int64_t n) {
 
 template <typename T>
 void inner_gather(const InnerArgs<T>& a, int lanes, cudaStream_t s) {
-    const int grid = a.rs.grid();
-    switch (lanes) {
-        case 1: k_phase1_gather<T, 1><<<grid, kThreads, 0, s>>>(a); break;
-        case 2: k_phase1_gather<T, 2><<<grid, kThreads, 0, s>>>(a); break;
-        case 4: k_phase1_gather<T, 4><<<grid, kThreads, 0, s>>>(a); break;
-        case 8: k_phase1_gather<T, 8><<<grid, kThreads, 0, s>>>(a); break;
-        case 16: k_phase1_gather<T, 16><<<grid, kThreads, 0, s>>>(a); break;
-        default: k_phase1_gather<T, 32><<<grid, kThreads, 0, s>>>(a); break;
-    }
+#define LG(G, TPB) k_phase1_gather<T, G, TPB><<<a.rs.grid(), TPB, a.rs.hub_bytes, s>>>(a)
+    ISIRA_GATHER_DISPATCH(lanes, a.rs.tpb, LG);
+#undef LG
+}
+
+// Lets every gather kernel of precision T take up to `bytes` of dynamic shared memory.
+template <typename T>
+cudaError_t inner_gather_attrs(int bytes) {
+    cudaError_t e = cudaSuccess;
+#define LA(G, TPB)                                                                                      \
+    if (e == cudaSuccess)                                                                               \
+        e = cudaFuncSetAttribute(k_phase1_gather<T, G, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+    for (int tpb : {kThreads, kBigBlock})
+        for (int g : {1, 2, 4, 8, 16, 32}) ISIRA_GATHER_DISPATCH(g, tpb, LA);
+#undef LA
+    return e;
 }
 
 template <typename T>
@@ -636,6 +643,7 @@ void copy_vcol(const double* src, T* dst, int64_t n, cudaStream_t s) {
     template void inner_finalize_to<T>(const InnerArgs<T>&, double*, cudaStream_t);                      \
     template void inner_opstats<T>(const InnerArgs<T>&, const T*, cudaStream_t);                         \
     template void gram_setup<T>(const InnerArgs<T>&, double*, double*, double*, cudaStream_t);           \
-    template void copy_vcol<T>(const double*, T*, int64_t, cudaStream_t);
+    template void copy_vcol<T>(const double*, T*, int64_t, cudaStream_t);                                 \
+    template cudaError_t inner_gather_attrs<T>(int);
 
 }  // namespace isira

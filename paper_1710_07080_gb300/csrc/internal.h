@@ -56,6 +56,8 @@ template <typename T> void inner_prep_launch(const InnerArgs<T>& a, const double
                                              cudaStream_t s);
 template <typename T> void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s);   // gather + rows
 template <typename T> void inner_gather(const InnerArgs<T>& a, int lanes, cudaStream_t s);
+// every gather kernel of precision T may take up to `bytes` of dynamic shared memory
+template <typename T> cudaError_t inner_gather_attrs(int bytes);
 template <typename T> void inner_rows(const InnerArgs<T>& a, cudaStream_t s);
 template <typename T> void inner_phase2(const InnerArgs<T>& a, int init, cudaStream_t s);
 // phase 2 inside a CUDA graph whose WHILE node is driven by `cond` (set to 0 once the solve stops)
@@ -93,6 +95,9 @@ void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, in
 void outer_cgs2(const OuterArgs& a, int k, int c, cudaStream_t s);
 // U(:,k) = Z/||Z||, W(:,k) = L U(:,k), H(0:k, k) = U(:,0:k+1)^T W(:,k) (and the symmetric row).
 void outer_expand(const OuterArgs& a, int k, int lanes, cudaStream_t s);
+cudaError_t outer_gather_attrs(int bytes);
+// resident gather CTAs per SM at tpb threads and hub_bytes of dynamic shared memory (0: error)
+int gather_ctas_per_sm(int tpb, int hub_bytes);
 // X(:, 0:ncol) <- X(:, 0:kk) S(:, c0:c0+ncol); with vout != NULL also vout = X S(:, 0).
 void outer_rotate(const OuterArgs& a, double* X, int kk, int c0, int ncol, double* vout, cudaStream_t s);
 // H <- diag(theta(c0 : c0 + cnt))

@@ -430,8 +430,8 @@ void outer_cgs2(const OuterArgs& a, int k, int c, cudaStream_t s) {
 // ------------------------------------------------------------------ expand (lines 4 and 19)
 
 // Plain gather g[r] = sum_{c in N(r)} x[c] over the full Laplacian (no trimmed row).
-template <int G>
-__global__ void __launch_bounds__(kThreads, 6) k_gather_plain(RowSched rs, const double* x, double* g) {
+template <int G, int TPB>
+__global__ void __launch_bounds__(TPB, TPB == kThreads ? 4 : 1) k_gather_plain(RowSched rs, const double* x, double* g) {
     GatherStore<double> epi{g};
     for_each_row_gather<double, G>(rs, x, epi, -1);
 }
@@ -454,22 +454,29 @@ __global__ void __launch_bounds__(kThreads) k_laplacian_rows(OuterArgs a, const 
         y[r] = (double)(a.rs.rp[r + 1] - a.rs.rp[r]) * x[r] - a.gsum[r];
 }
 
-#define ISIRA_LANES_DISPATCH(lanes, F) \
-    do {                               \
-        switch (lanes) {               \
-            case 1: F(1); break;       \
-            case 2: F(2); break;       \
-            case 4: F(4); break;       \
-            case 8: F(8); break;       \
-            case 16: F(16); break;     \
-            default: F(32); break;     \
-        }                              \
-    } while (0)
-
 static void outer_gather(const OuterArgs& a, const double* x, int lanes, cudaStream_t s) {
-#define LG(G) k_gather_plain<G><<<a.rs.grid(), kThreads, 0, s>>>(a.rs, x, a.gsum)
-    ISIRA_LANES_DISPATCH(lanes, LG);
+#define LG(G, TPB) k_gather_plain<G, TPB><<<a.rs.grid(), TPB, a.rs.hub_bytes, s>>>(a.rs, x, a.gsum)
+    ISIRA_GATHER_DISPATCH(lanes, a.rs.tpb, LG);
 #undef LG
+}
+
+cudaError_t outer_gather_attrs(int bytes) {
+    cudaError_t e = cudaSuccess;
+#define LA(G, TPB)                                                                                      \
+    if (e == cudaSuccess)                                                                               \
+        e = cudaFuncSetAttribute(k_gather_plain<G, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+    for (int tpb : {kThreads, kBigBlock})
+        for (int g : {1, 2, 4, 8, 16, 32}) ISIRA_GATHER_DISPATCH(g, tpb, LA);
+#undef LA
+    return e;
+}
+
+int gather_ctas_per_sm(int tpb, int hub_bytes) {
+    int nb = 0;
+    cudaError_t e = tpb == kBigBlock
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather_plain<1, kBigBlock>, kBigBlock, hub_bytes)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather_plain<1, kThreads>, kThreads, hub_bytes);
+    return e == cudaSuccess ? nb : 0;
 }
 
 void outer_expand(const OuterArgs& a, int k, int lanes, cudaStream_t s) {

@@ -449,6 +449,11 @@ void isira_default_opts(isira_opts* o) {
     o->inner_chunk = 16;
     o->inner_graph = 1;
     o->reorder = 1;
+    o->gather_block = 0;
+    o->hub_kb = 0;
+    o->gather_sched = 0;
+    o->index_vec = 0;
+    o->gather_chunk = 0;
 }
 
 const char* isira_error_string(isira_status s) {
@@ -503,7 +508,10 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         if (h->opts.reorder) {
             setup_degrees(d_row_ptr, n, light_deg, nullptr, nullptr, 0, scratch, &di, s);   // max degree
             ck(cudaMalloc(&h->own_rp, sizeof(int64_t) * (size_t)(n + 1)));
-            ck(cudaMalloc(&h->own_ci, sizeof(int32_t) * (size_t)nnz));
+            // padded to a multiple of 4 entries: the gathers read the relabelled copy in 128-bit chunks
+            const size_t nnz_pad = ((size_t)nnz + 3) / 4 * 4;
+            ck(cudaMalloc(&h->own_ci, sizeof(int32_t) * nnz_pad));
+            ck(cudaMemsetAsync(h->own_ci + nnz, 0, sizeof(int32_t) * (nnz_pad - (size_t)nnz), s));
             ck(cudaMalloc(&h->perm, sizeof(int32_t) * (size_t)n));
             ck(cudaMalloc(&h->inv, sizeof(int32_t) * (size_t)n));
             ck(build_reordered_graph(d_row_ptr, d_col_idx, n, nnz, di.max_degree, h->own_rp, h->own_ci, h->perm,
@@ -554,11 +562,35 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         rs.item_count = h->item_count;
         rs.n_items = (int)di.n_items;
         rs.light_deg = light_deg;
-        // one launch wave of gather warps (6 CTAs per SM), each with an equal share of the estimated cost
+        rs.ci_vec = h->own_ci != nullptr && h->opts.index_vec == 1;
+        rs.dyn = h->opts.gather_sched == 0;
+        rs.chunk = (h->opts.gather_chunk >= 1 && h->opts.gather_chunk <= 32) ? h->opts.gather_chunk : kUnitChunk;
+        // Gather launch shape.  With the hubs numbered first (relabelling on) one 1024-thread CTA
+        // per SM stages the largest block x[0:hub) that fits in shared memory, so most gathered
+        // entries are shared-memory reads; otherwise 256-thread CTAs, up to 6 per SM.
+        {
+            int optin = 0;
+            ck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            const int smem_max = std::max(0, optin - 1024);          // room for static shared memory
+            ck(inner_gather_attrs<float>(smem_max));
+            ck(inner_gather_attrs<double>(smem_max));
+            ck(outer_gather_attrs(smem_max));
+            const int gb = h->opts.gather_block;
+            rs.tpb = (gb == kThreads || gb == kBigBlock) ? gb : (h->perm ? kBigBlock : kThreads);
+            int64_t cap = h->opts.hub_kb > 0 ? (int64_t)h->opts.hub_kb * 1024 : (int64_t)kDefaultHubBytes;
+            cap = std::min<int64_t>(cap, smem_max) / 128 * 128;
+            rs.hub = (h->perm && h->opts.hub_kb >= 0) ? (int)n : 0;
+            rs.hub_bytes = rs.hub ? (int)std::min<int64_t>(cap, (n * (int64_t)sizeof(double) + 127) / 128 * 128) : 0;
+        }
+        const int wpb = rs.tpb / 32;
+        int ctas = gather_ctas_per_sm(rs.tpb, rs.hub_bytes);
+        if (rs.tpb == kThreads) ctas = std::min(ctas, 6);
+        if (ctas < 1) throw StatusError{ISIRA_ERR_INVALID_ARG};
+        // one launch wave of gather warps, each with an equal share of the estimated cost
         const int64_t n_units = di.n_items + (n + 31) / 32;
         if (n_units > INT32_MAX) throw StatusError{ISIRA_ERR_INVALID_ARG};
-        rs.n_warps = (int)std::max<int64_t>(kWarps, std::min<int64_t>((int64_t)h->nsm * 6 * kWarps,
-                                                                      (n_units + kWarps - 1) / kWarps * kWarps));
+        rs.n_warps = (int)std::max<int64_t>(wpb, std::min<int64_t>((int64_t)h->nsm * ctas * wpb,
+                                                                   (n_units + wpb - 1) / wpb * wpb));
         ck(cudaMalloc(&h->warp_start, sizeof(int32_t) * (size_t)(rs.n_warps + 1)));
         {
             int64_t* cost = nullptr;
@@ -572,16 +604,16 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
             cudaFree(prefix);
         }
         rs.warp_start = h->warp_start;
-        // stage the hub block of x only when the numbering puts the hubs first
-        rs.hub = h->perm ? (int)std::min<int64_t>(n, 1 << 20) : 0;
         h->ew_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)h->nsm * 4));
         h->ts_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64, (int64_t)h->nsm * 2));
         // shared scratch for block partial sums: 512 slots x the largest grid
         const int64_t maxgrid = std::max<int64_t>({(int64_t)rs.grid(), (int64_t)h->ew_blocks, (int64_t)h->ts_blocks});
         h->partial_elems = (size_t)512 * (size_t)maxgrid;
         ck(cudaMalloc(&h->partial, sizeof(double) * h->partial_elems));
-        ck(cudaMalloc(&h->counter, sizeof(unsigned) * 4));
-        ck(cudaMemsetAsync(h->counter, 0, sizeof(unsigned) * 4, s));
+        ck(cudaMalloc(&h->counter, sizeof(unsigned) * 8));
+        ck(cudaMemsetAsync(h->counter, 0, sizeof(unsigned) * 8, s));
+        rs.hub_timeouts = h->counter + 4;
+        rs.sched = h->counter + 5;
         ck(cudaMalloc(&h->H, sizeof(double) * kMMax * kMMax));
         ck(cudaMalloc(&h->theta, sizeof(double) * kMMax));
         ck(cudaMalloc(&h->S, sizeof(double) * kMMax * kMMax));
@@ -611,6 +643,8 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         h->stats.spmv_lanes = h->lanes;
         h->stats.n_long_rows = h->n_long;
         h->stats.n_work_items = h->n_items;
+        h->stats.gather_block = h->rs.tpb;
+        h->stats.hub_bytes = h->rs.hub_bytes;
     } catch (CudaError& e) {
         isira_status st = map_cuda(e.e);
         free_handle(h);
@@ -633,6 +667,13 @@ isira_status isira_set_profiling(isira_handle h, int on) {
 
 isira_status isira_get_stats(isira_handle h, isira_stats* out) {
     if (!h || !out) return ISIRA_ERR_INVALID_ARG;
+    unsigned to = 0;
+    if (h->counter) {
+        cudaError_t e = cudaMemcpyAsync(&to, h->counter + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    h->stats.hub_timeouts = to;
     *out = h->stats;
     return ISIRA_OK;
 }

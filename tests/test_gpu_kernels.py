@@ -99,6 +99,39 @@ def test_operator_fp32_within_rounding_bound(isira, name, lanes):
         assert np.all(err <= 2 * mag + 1e-30), float(np.max(err / (mag + 1e-300)))
 
 
+@pytest.mark.parametrize("name", ["rmat12", "star5000", "grid31x33"])
+@pytest.mark.parametrize("dtype", ["fp32", "fp64"])
+@pytest.mark.parametrize("index_vec", [0, 1])
+def test_operator_independent_of_gather_launch_shape(isira, name, dtype, index_vec):
+    """The gather's summation order is fixed by the row and its work items, not by the launch
+    shape: 256- and 1024-thread CTAs, dynamic or static work distribution, with the hub block of
+    x staged in shared memory by a bulk copy (whole vector, a part of it) or not at all, give
+    bit-identical operator values."""
+    g = graphs()[name]
+    rp, ci = dev_graph(g)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(g.n)
+    V = orthonormal_columns(g.n, 2, 9)
+    tx = torch.from_numpy(x).cuda()
+    tV = torch.from_numpy(V).cuda()
+    if dtype == "fp32":
+        tx, tV = tx.float(), tV.float()
+    prec = isira.ISIRA_MIXED if dtype == "fp32" else isira.ISIRA_FP64
+    outs = []
+    for block, hub, sched in [(256, -1, 1), (256, 16, 0), (1024, -1, 0), (1024, 1, 1), (1024, 0, 0), (256, 0, 1)]:
+        with isira.Solver(rp, ci, precision=prec, spmv_lanes=2, gather_block=block, hub_kb=hub, gather_sched=sched,
+                          index_vec=index_vec) as s:
+            st = s.stats()
+            assert st["gather_block"] == block
+            assert (st["hub_bytes"] > 0) == (hub >= 0)
+            outs.append(s.apply_operator(tx, sigma=0.3, V=tV).cpu().numpy())
+            # a second launch on the same handle: the work counter was reset by the first
+            np.testing.assert_array_equal(s.apply_operator(tx, sigma=0.3, V=tV).cpu().numpy(), outs[-1])
+            assert s.stats()["hub_timeouts"] == 0
+    for y in outs[1:]:
+        np.testing.assert_array_equal(y, outs[0])
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 7, 17, 30, 50, 64])
 def test_sym_eig_matches_oracle_and_lapack(isira, k):
     rng = np.random.default_rng(100 + k)
