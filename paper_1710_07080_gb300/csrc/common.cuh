@@ -46,6 +46,44 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Warp sums of NV per-lane values by recursive halving: at each butterfly level a lane keeps
+// half of its values and adds the partner's copy of that half, so a lane spends about 2P adds
+// (P = NV rounded up to a power of two) instead of 5 NV.  Afterwards value i's total is in
+// slot i % S of lane i / S when P >= 32 (S = P / 32 slots per lane), and in slot 0 of lanes
+// i * (32 / P) ... i * (32 / P) + 32 / P - 1 when P < 32.  The summation order is fixed.
+template <int NV>
+struct MultiShape {
+    static constexpr int P = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : NV <= 32 ? 32 : 64;
+    static constexpr int S = P >= 32 ? P / 32 : 1;
+};
+
+template <typename T, int O, int M, int P>
+__device__ __forceinline__ void multi_level(T (&a)[P], int lane) {
+    if constexpr (M > 1) {
+        const bool up = (lane & O) != 0;
+#pragma unroll
+        for (int j = 0; j < M / 2; ++j) {
+            const T send = up ? a[j] : a[j + M / 2];
+            const T keep = up ? a[j + M / 2] : a[j];
+            a[j] = keep + __shfl_xor_sync(kFull, send, O);
+        }
+    } else {
+        a[0] += __shfl_xor_sync(kFull, a[0], O);
+    }
+    if constexpr (O > 1) multi_level<T, O / 2, (M > 1 ? M / 2 : 1), P>(a, lane);
+}
+
+template <typename T, int NV>
+__device__ __forceinline__ void warp_reduce_multi(const T (&v)[NV], T (&out)[MultiShape<NV>::S]) {
+    constexpr int P = MultiShape<NV>::P;
+    T a[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) a[i] = i < NV ? v[i] : T(0);
+    multi_level<T, 16, P, P>(a, threadIdx.x & 31);
+#pragma unroll
+    for (int q = 0; q < MultiShape<NV>::S; ++q) out[q] = a[q];
+}
+
 // Reduces NV per-thread values over the block; the block's sums go to
 // partial[i * pstride + blockIdx.x] (i < nv).  Returns true in the last block to
 // arrive, after which all partials of all blocks are visible to it.
@@ -55,12 +93,18 @@ __device__ __forceinline__ bool block_partials_arrive(T (&v)[NV], int nv, T* par
     __shared__ T red[kWarps][NV];
     __shared__ int last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int P = MultiShape<NV>::P, S = MultiShape<NV>::S;
+    T out[S];
+    warp_reduce_multi<T, NV>(v, out);
+    if constexpr (P >= 32) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        if (i < nv) {
-            T s = warp_sum(v[i]);
-            if (lane == 0) red[w][i] = s;
+        for (int q = 0; q < S; ++q) {
+            const int i = lane * S + q;
+            if (i < nv && i < NV) red[w][i] = out[q];
         }
+    } else {
+        const int i = lane / (32 / P);
+        if (lane % (32 / P) == 0 && i < nv && i < NV) red[w][i] = out[0];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nv; i += blockDim.x) {
@@ -360,14 +404,22 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
             h_re = S.rp[h_row + 1];
         }
     };
-    auto do_item = [&](int it, int j) {
+    // per-lane partial sum of the item whose header sits in lane j (zero for the skipped row)
+    auto item_partial = [&](int j) -> T {
         const int64_t r = __shfl_sync(kFull, h_row, j);
         const int kpos = __shfl_sync(kFull, h_k, j);
         const int64_t rb = __shfl_sync(kFull, h_rb, j), re = __shfl_sync(kFull, h_re, j);
-        if (r == skip) return;
+        if (r == skip) return T(0);
         const int64_t beg = rb + (int64_t)kpos * kItemNnz;
         const int64_t end = beg + kItemNnz < re ? beg + kItemNnz : re;
-        T s = warp_sum(seg_sum<T, 32>(S, x, sx, hub, beg, end, lane));
+        return seg_sum<T, 32>(S, x, sx, hub, beg, end, lane);
+    };
+    // item it (header in lane j) with its warp total s: combine a split row, collect the row
+    auto item_finish = [&](int it, int j, T s) {
+        const int64_t r = __shfl_sync(kFull, h_row, j);
+        if (r == skip) return;
+        const int kpos = __shfl_sync(kFull, h_k, j);
+        const int64_t rb = __shfl_sync(kFull, h_rb, j), re = __shfl_sync(kFull, h_re, j);
         const int nit = (int)((re - rb + kItemNnz - 1) / kItemNnz);
         int done = 1;
         if (nit > 1) {
@@ -399,6 +451,17 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
             }
         }
     };
+    auto do_item = [&](int it, int j) { item_finish(it, j, warp_sum(item_partial(j))); };
+    // two items share one butterfly reduction; it applies the same lane pairs in the same order
+    // as two warp_sum calls, so the totals are bit-identical to reducing them one by one
+    auto do_item_pair = [&](int it, int j) {
+        const T v[2] = {item_partial(j), item_partial(j + 1)};
+        T out[1];
+        warp_reduce_multi<T, 2>(v, out);
+        const T s0 = __shfl_sync(kFull, out[0], 0), s1 = __shfl_sync(kFull, out[0], 16);
+        item_finish(it, j, s0);
+        item_finish(it + 1, j + 1, s1);
+    };
     // light tiles: 32 consecutive rows, G lanes per row, one lane per row for the epilogue
     constexpr int RPS = 32 / G;                            // rows per sub-pass
     auto do_tile = [&](int tile) {
@@ -427,8 +490,14 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
     };
     auto do_range = [&](int u0, int u1) {             // u1 - u0 <= 32
         if (u0 < S.n_items) load_headers(u0, u1);
-        for (int u = u0; u < u1; ++u) {
-            if (u < S.n_items) do_item(u, u - u0); else do_tile(u - S.n_items);
+        for (int u = u0; u < u1;) {
+            if (u + 1 < u1 && u + 1 < S.n_items) {
+                do_item_pair(u, u - u0);
+                u += 2;
+            } else {
+                if (u < S.n_items) do_item(u, u - u0); else do_tile(u - S.n_items);
+                u += 1;
+            }
         }
     };
     const int n_units = S.n_items + (int)((S.n + 31) / 32);

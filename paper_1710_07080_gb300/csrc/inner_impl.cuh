@@ -193,9 +193,11 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, c
     const T coef = init ? T(0) : st->alpha / st->beta;
     __shared__ T qvs[NC > 0 ? NC : 1], tvs[NC > 0 ? NC : 1];
     __shared__ T red[2 + NC];
+    // y = Y - coef D z_k - Vh qv and z = D^{-1}(y - Vh tv) need only Vh (qv + tv) per row;
+    // y^T z = z^T D z + tv^T (Vh^T z) (since y = D z + Vh tv) is finished by the last block
     for (int t = threadIdx.x; t < c; t += blockDim.x) {
-        qvs[t] = init ? T(0) : st->qv[t];
         tvs[t] = st->tv[t];
+        qvs[t] = (init ? T(0) : st->qv[t]) + tvs[t];
     }
     __syncthreads();
     T acc[2 + NC];
@@ -209,20 +211,15 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, c
         }
         const T degT = (T)(a.rs.rp[r + 1] - a.rs.rp[r]);
         const T D = precond_diag(degT, sigma);
-        T q1 = 0, q2 = 0;
+        T q = 0;
 #pragma unroll
-        for (int t = 0; t < NC; ++t) {
-            if (t < c) {
-                const T v = a.Vt[(int64_t)t * a.ldv + r];
-                q1 += v * qvs[t];
-                q2 += v * tvs[t];
-            }
-        }
+        for (int t = 0; t < NC; ++t)
+            if (t < c) q += a.Vt[(int64_t)t * a.ldv + r] * qvs[t];
         T y = a.Y[r];
-        if (!init) y -= coef * D * zc[r] + q1;
-        const T z = (y - q2) * inv_diag(a.dinv, r, D);
+        if (!init) y -= coef * D * zc[r];
+        const T z = (y - q) * inv_diag(a.dinv, r, D);
         zn[r] = z;
-        acc[0] += y * z;
+        acc[0] += D * z * z;
         acc[1] += z;
 #pragma unroll
         for (int t = 0; t < NC; ++t)   // second read of the row of Vh: an L1 hit
@@ -232,7 +229,8 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, c
         last_block_sum(a.partial, a.pstride, gridDim.x, 2 + c, red, a.counter);
         __shared__ T bnew_s, bold_s;
         if (threadIdx.x == 0) {
-            const T bb = red[0];
+            T bb = red[0];
+            for (int t = 0; t < c; ++t) bb += tvs[t] * red[2 + t];
             const T bnew = bb > T(0) ? sqrt(bb) : T(0);
             bold_s = st->beta;
             bnew_s = bnew;
