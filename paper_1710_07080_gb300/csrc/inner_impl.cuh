@@ -20,6 +20,7 @@
 // buffers, x, and c columns of Vh.
 #pragma once
 #include <mutex>
+#include <unordered_map>
 
 #include "internal.h"
 
@@ -555,7 +556,48 @@ void inner_gather(const InnerArgs<T>& a, int lanes, cudaStream_t s) {
 #undef LG
 }
 
-// Lets every gather kernel of precision T take up to `bytes` of dynamic shared memory.
+// ---- one-wave grids for the row kernels.  Their register use grows with the deflation bucket
+// NC (FP64, NC = 32: over 200 registers), so the resident CTAs per SM differ per instance; a grid
+// of ew_blocks CTAs could then run as one full wave plus a partial one.  Each instance is
+// launched with min(ew_blocks, SMs x resident CTAs); the row loops are grid-stride.
+struct WaveCache {
+    std::mutex mu;
+    std::unordered_map<const void*, int> per_sm;
+    int nsm = 0;
+};
+inline WaveCache& wave_cache() {
+    static WaveCache c;
+    return c;
+}
+
+inline cudaError_t wave_register(const void* fn) {
+    WaveCache& c = wave_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    cudaError_t e = cudaSuccess;
+    if (c.nsm == 0) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    if (c.per_sm.count(fn)) return cudaSuccess;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, 0);
+    if (e == cudaSuccess) c.per_sm[fn] = nb > 0 ? nb : 1;
+    return e;
+}
+
+inline int wave_grid(const void* fn, int want) {
+    WaveCache& c = wave_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.per_sm.find(fn);
+    if (it == c.per_sm.end() || c.nsm == 0) return want;
+    const int cap = c.nsm * it->second;
+    return want < cap ? want : cap;
+}
+
+// Lets every gather kernel of precision T take up to `bytes` of dynamic shared memory, and
+// records the resident CTAs per SM of every row-kernel instance (before any graph capture).
 template <typename T>
 cudaError_t inner_gather_attrs(int bytes) {
     cudaError_t e = cudaSuccess;
@@ -565,12 +607,21 @@ cudaError_t inner_gather_attrs(int bytes) {
     for (int tpb : {kThreads, kBigBlock})
         for (int g : {1, 2, 4, 8, 16, 32}) ISIRA_GATHER_DISPATCH(g, tpb, LA);
 #undef LA
+#define LW(NC)                                                                                          \
+    do {                                                                                                \
+        if (e == cudaSuccess) e = wave_register((const void*)k_phase1<T, NC>);                          \
+        if (e == cudaSuccess) e = wave_register((const void*)k_phase2<T, NC>);                          \
+        if (e == cudaSuccess) e = wave_register((const void*)k_prep<T, NC>);                            \
+        if (e == cudaSuccess) e = wave_register((const void*)k_opstats<T, NC>);                         \
+    } while (0)
+    for (int nc : {0, 8, 12, 16, 24, 32}) ISIRA_NC_DISPATCH(nc, LW);
+#undef LW
     return e;
 }
 
 template <typename T>
 void inner_rows(const InnerArgs<T>& a, cudaStream_t s) {
-#define L1(NC) k_phase1<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a)
+#define L1(NC) k_phase1<T, NC><<<wave_grid((const void*)k_phase1<T, NC>, a.ew_blocks), kThreads, 0, s>>>(a)
     ISIRA_NC_DISPATCH(a.c, L1);
 #undef L1
 }
@@ -583,21 +634,21 @@ void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s) {
 
 template <typename T>
 void inner_phase2(const InnerArgs<T>& a, int init, cudaStream_t s) {
-#define L2(NC) k_phase2<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a, init, 0, 0)
+#define L2(NC) k_phase2<T, NC><<<wave_grid((const void*)k_phase2<T, NC>, a.ew_blocks), kThreads, 0, s>>>(a, init, 0, 0)
     ISIRA_NC_DISPATCH(a.c, L2);
 #undef L2
 }
 
 template <typename T>
 void inner_phase2_cond(const InnerArgs<T>& a, cudaGraphConditionalHandle cond, cudaStream_t s) {
-#define L2C(NC) k_phase2<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a, 0, cond, 1)
+#define L2C(NC) k_phase2<T, NC><<<wave_grid((const void*)k_phase2<T, NC>, a.ew_blocks), kThreads, 0, s>>>(a, 0, cond, 1)
     ISIRA_NC_DISPATCH(a.c, L2C);
 #undef L2C
 }
 
 template <typename T>
 void inner_prep_launch(const InnerArgs<T>& a, const double* R, const double* rnorm_dev, cudaStream_t s) {
-#define LP(NC) k_prep<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a, R, rnorm_dev)
+#define LP(NC) k_prep<T, NC><<<wave_grid((const void*)k_prep<T, NC>, a.ew_blocks), kThreads, 0, s>>>(a, R, rnorm_dev)
     ISIRA_NC_DISPATCH(a.c, LP);
 #undef LP
 }
@@ -609,7 +660,7 @@ void inner_finalize_to(const InnerArgs<T>& a, double* Z, cudaStream_t s) {
 
 template <typename T>
 void inner_opstats(const InnerArgs<T>& a, const T* x, cudaStream_t s) {
-#define LS(NC) k_opstats<T, NC><<<a.ew_blocks, kThreads, 0, s>>>(a, x)
+#define LS(NC) k_opstats<T, NC><<<wave_grid((const void*)k_opstats<T, NC>, a.ew_blocks), kThreads, 0, s>>>(a, x)
     ISIRA_NC_DISPATCH(a.c, LS);
 #undef LS
 }

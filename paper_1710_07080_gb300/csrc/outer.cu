@@ -63,12 +63,13 @@ void outer_residual(const OuterArgs& a, int k, cudaStream_t s) {
 // magnitude (first index on ties) is positive.
 
 constexpr int kEigLd = kMMax + 1;
+constexpr int kEigThreads = 1024;        // one CTA; a round's K*K updates take one pass for K <= 32
 
 template <typename T>
 struct JacobiSmem {
     T* A; T* A2; T* Q; T* Q2;       // [kMMax][kEigLd] each, column-major
     int* partner; T* alpha; T* beta; int* zero_pq;   // per index
-    double* red;                    // [kWarps]
+    double* red;                    // [blockDim.x / 32]
 };
 
 template <typename T>
@@ -82,7 +83,7 @@ __device__ double jacobi_off(const T* A, int K, double* red) {
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off;
     __syncthreads();
     double tot = 0.0;
-    for (int w = 0; w < kWarps; ++w) tot += red[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
     __syncthreads();
     return tot;
 }
@@ -98,7 +99,7 @@ __device__ double jacobi_frob(const T* A, int K, double* red) {
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
     __syncthreads();
     double tot = 0.0;
-    for (int w = 0; w < kWarps; ++w) tot += red[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
     __syncthreads();
     return tot;
 }
@@ -180,11 +181,11 @@ __device__ void small_gemm(const double* X, const double* Y, double* C, int K, b
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) k_sym_eig(const double* H, int ldh, int k, double* theta, double* S,
+__global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* H, int ldh, int k, double* theta, double* S,
                                                       int lds, HostStatus* hs) {
     extern __shared__ double eig_sm[];
     __shared__ int partner_[kMMax], zero_[kMMax], perm[kMMax];
-    __shared__ double alpha_[kMMax], beta_[kMMax], red_[kWarps];
+    __shared__ double alpha_[kMMax], beta_[kMMax], red_[kEigThreads / 32];
     __shared__ float alphaf_[kMMax], betaf_[kMMax];
     const int K = k + (k & 1);
     const int tid = threadIdx.x;
@@ -272,7 +273,7 @@ void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, in
     const int bytes = (int)(sizeof(double) * 4 * kMMax * kEigLd);
     static std::once_flag once;
     std::call_once(once, [bytes] { cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
-    k_sym_eig<<<1, kThreads, bytes, s>>>(H, ldh, k, theta, S, lds, hs);
+    k_sym_eig<<<1, kEigThreads, bytes, s>>>(H, ldh, k, theta, S, lds, hs);
 }
 
 // ------------------------------------------------------------------ tall-skinny passes (line 18, line 4)
