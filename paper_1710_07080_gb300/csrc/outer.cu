@@ -63,7 +63,7 @@ void outer_residual(const OuterArgs& a, int k, cudaStream_t s) {
 // magnitude (first index on ties) is positive.
 
 constexpr int kEigLd = kMMax + 1;
-constexpr int kEigThreads = 1024;        // one CTA; a round's K*K updates take one pass for K <= 32
+constexpr int kEigThreads = 256;         // one CTA (more threads only add barrier cost)
 
 template <typename T>
 struct JacobiSmem {
