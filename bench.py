@@ -458,7 +458,8 @@ def main():
     def relerr(a):
         return float(np.max(np.abs(a.numpy() - lam_ref) / np.abs(lam_ref)))
 
-    # end to end through the public API: pinned host CSR -> device, create, solve, eigenpairs -> host
+    # end to end through the public API, in the precision the configuration names:
+    # pinned host CSR -> device, create, solve, eigenpairs -> host
     e2e_times = []
     h2d = rp_h.numel() * 8 + ci_h.numel() * 4 + u0_h.numel() * 8
     d2h = n * k * 8 + k * 8 * 2
@@ -469,7 +470,8 @@ def main():
         rp_d = rp_h.to(dev, non_blocking=True)
         ci_d = ci_h.to(dev, non_blocking=True)
         u0_d = u0_h.to(dev, non_blocking=True)
-        with isira.Solver(rp_d, ci_d, precision=isira.ISIRA_FP64, **solver_opts(args)) as s:
+        e2e_prec = isira.ISIRA_MIXED if spec["prec"] == "mixed" else isira.ISIRA_FP64
+        with isira.Solver(rp_d, ci_d, precision=e2e_prec, **solver_opts(args)) as s:
             s.solve(k, tol=tol, u0=u0_d)
             lam_e, vec_e, res_e = s.eigpairs()
             vec_host = vec_e.cpu()

@@ -102,6 +102,9 @@ int gather_ctas_per_sm(int tpb, int hub_bytes);
 void outer_rotate(const OuterArgs& a, double* X, int kk, int c0, int ncol, double* vout, cudaStream_t s);
 // H <- diag(theta(c0 : c0 + cnt))
 void outer_set_diag(const OuterArgs& a, int c0, int cnt, cudaStream_t s);
+// purge after a lock with a Householder reflection (U and W in place, H to P H P trimmed);
+// vout receives the locked vector U s1 (S(:, 0) of the last Rayleigh-Ritz step)
+void outer_purge(const OuterArgs& a, int k, double* vout, cudaStream_t s);
 // Z <- centred SplitMix64 vector, block `blk` of stream `seed`.
 void outer_random(const OuterArgs& a, uint64_t seed, uint64_t blk, cudaStream_t s);
 // out[j] = ||L V(:,j) - lam[j] V(:,j)||_2^2 for j < d (out is device, d doubles).

@@ -416,6 +416,23 @@ static void ts_smem_attr() {
     });
 }
 
+// One launch wave: at most SMs x resident CTAs (registers and dynamic shared memory decide the
+// latter), so a tile loop never runs as a full wave plus a partial one.
+static int wave_of(const void* fn, size_t smem, int want) {
+    static int nsm_of[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return want;
+    if (nsm_of[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return want;
+        nsm_of[dev] = v;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess || nb < 1) return want;
+    const int cap = nb * nsm_of[dev];
+    return want < cap ? want : cap;
+}
+
 static size_t ts_smem(int nq) { return sizeof(double) * ((size_t)nq * kTsRows + kTsRows + nq + 1); }
 
 void outer_cgs2(const OuterArgs& a, int k, int c, cudaStream_t s) {
@@ -423,9 +440,13 @@ void outer_cgs2(const OuterArgs& a, int k, int c, cudaStream_t s) {
     const int nq = k + c;
     double* cA = a.dscratch + 8;                 // coefficients of pass B
     double* cB = a.dscratch + 8 + kTsMaxCols + 1; // coefficients of pass C
-    k_tall_skinny<0><<<a.ts_blocks, kThreads, ts_smem(nq), s>>>(a, k, c, a.Z, nullptr, nullptr, cA, nullptr, 0);
-    k_tall_skinny<1><<<a.ts_blocks, kThreads, ts_smem(nq), s>>>(a, k, c, a.Z, a.Z, cA, cB, nullptr, 0);
-    k_tall_skinny<2><<<a.ts_blocks, kThreads, ts_smem(nq), s>>>(a, k, c, a.Z, a.Z, cB, nullptr, nullptr, 0);
+    const size_t sm = ts_smem(nq);
+    k_tall_skinny<0><<<wave_of((const void*)k_tall_skinny<0>, sm, a.ts_blocks), kThreads, sm, s>>>(
+        a, k, c, a.Z, nullptr, nullptr, cA, nullptr, 0);
+    k_tall_skinny<1><<<wave_of((const void*)k_tall_skinny<1>, sm, a.ts_blocks), kThreads, sm, s>>>(
+        a, k, c, a.Z, a.Z, cA, cB, nullptr, 0);
+    k_tall_skinny<2><<<wave_of((const void*)k_tall_skinny<2>, sm, a.ts_blocks), kThreads, sm, s>>>(
+        a, k, c, a.Z, a.Z, cB, nullptr, nullptr, 0);
 }
 
 // ------------------------------------------------------------------ expand (lines 4 and 19)
@@ -485,7 +506,8 @@ void outer_expand(const OuterArgs& a, int k, int lanes, cudaStream_t s) {
     outer_gather(a, a.Z, lanes, s);
     k_expand_rows<<<a.ew_blocks, kThreads, 0, s>>>(a, k);
     // H(0:k+1, k) = U(:, 0:k+1)^T W(:, k)
-    k_tall_skinny<0><<<a.ts_blocks, kThreads, ts_smem(k + 1), s>>>(a, k + 1, 0, a.W + (int64_t)k * a.ld, nullptr,
+    k_tall_skinny<0><<<wave_of((const void*)k_tall_skinny<0>, ts_smem(k + 1), a.ts_blocks), kThreads,
+                       ts_smem(k + 1), s>>>(a, k + 1, 0, a.W + (int64_t)k * a.ld, nullptr,
                                                                    nullptr, nullptr, a.H, k);
 }
 
@@ -538,7 +560,81 @@ void outer_rotate(const OuterArgs& a, double* X, int kk, int c0, int ncol, doubl
                              (int)(sizeof(double) * ((size_t)kMMax * kRotRows + (size_t)kMMax * (kMMax + 1))));
     });
     const size_t smem = sizeof(double) * ((size_t)kk * kRotRows + (size_t)kk * (ncol + 1));
-    k_rotate<<<a.ts_blocks, kThreads, smem, s>>>(a, X, kk, c0, ncol, vout);
+    k_rotate<<<wave_of((const void*)k_rotate, smem, a.ts_blocks), kThreads, smem, s>>>(a, X, kk, c0, ncol, vout);
+}
+
+// ------------------------------------------------------------------ purge after a lock (line 22)
+// The purge keeps span U minus the locked Ritz direction U s1.  Any orthonormal basis of that
+// space gives the same later Ritz pairs, so instead of the k x (k-1) product U S(:, 2:k) the
+// solver applies the Householder reflection P = I - beta v v^T, v = s1 + sign(s1[0]) e1, which
+// maps s1 to -sign(s1[0]) e1: the first column of U P is -sign(s1[0]) U s1 (the locked vector)
+// and columns 2..k of U P span the rest.  Per row that is 2k FMAs instead of k(k-1).  The
+// projected matrix becomes the trailing (k-1) x (k-1) block of P H P (its first row and column
+// vanish because s1 is an eigenvector of H).  Scratch: beta, sign and v in dscratch[400 ..].
+constexpr int kPurgeSlot = 400;
+
+__global__ void __launch_bounds__(kThreads) k_purge_prep(OuterArgs a, int k) {
+    __shared__ double Hs[kMMax][kMMax + 1];
+    __shared__ double v[kMMax], w[kMMax];
+    __shared__ double beta_s, gamma_s;
+    const int tid = threadIdx.x;
+    const double s0 = a.S[0];
+    const double sgn = s0 >= 0.0 ? 1.0 : -1.0;
+    for (int i = tid; i < k; i += blockDim.x) v[i] = a.S[i] + (i == 0 ? sgn : 0.0);
+    for (int idx = tid; idx < k * k; idx += blockDim.x) {
+        const int i = idx % k, j = idx / k;
+        Hs[i][j] = 0.5 * (a.H[i + j * kMMax] + a.H[j + i * kMMax]);
+    }
+    if (tid == 0) beta_s = 1.0 / (1.0 + fabs(s0));       // 2 / (v^T v) for a unit s1
+    __syncthreads();
+    for (int i = tid; i < k; i += blockDim.x) {
+        double t = 0.0;
+        for (int j = 0; j < k; ++j) t += Hs[i][j] * v[j];
+        w[i] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double g = 0.0;
+        for (int j = 0; j < k; ++j) g += v[j] * w[j];
+        gamma_s = g;
+        a.dscratch[kPurgeSlot] = beta_s;
+        a.dscratch[kPurgeSlot + 1] = -sgn;
+    }
+    for (int i = tid; i < k; i += blockDim.x) a.dscratch[kPurgeSlot + 2 + i] = v[i];
+    __syncthreads();
+    // P H P = H - beta v w^T - beta w v^T + beta^2 gamma v v^T; keep rows/columns 1..k-1
+    const double b = beta_s, bg = beta_s * beta_s * gamma_s;
+    for (int idx = tid; idx < (k - 1) * (k - 1); idx += blockDim.x) {
+        const int i = idx % (k - 1) + 1, j = idx / (k - 1) + 1;
+        const double h = Hs[i][j] - b * (v[i] * w[j] + w[i] * v[j]) + bg * v[i] * v[j];
+        a.H[(i - 1) + (j - 1) * kMMax] = h;
+    }
+}
+
+// X(r, 0:k) <- (X P)(r, 1:k) in place, one thread per row; vout[r] = -sign(s1[0]) (X P)(r, 0)
+__global__ void __launch_bounds__(kThreads) k_purge_rows(OuterArgs a, double* X, double* Y, int k, double* vout) {
+    __shared__ double v[kMMax];
+    const double* ps = a.dscratch + kPurgeSlot;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) v[i] = ps[2 + i];
+    __syncthreads();
+    const double beta = ps[0], sg = ps[1];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll 1
+        for (int m = 0; m < 2; ++m) {
+            double* Z = m == 0 ? X : Y;
+            if (!Z) continue;
+            double y = 0.0;
+            for (int j = 0; j < k; ++j) y += Z[(int64_t)j * a.ld + r] * v[j];
+            const double by = beta * y;
+            if (m == 0 && vout) vout[r] = sg * (Z[r] - by * v[0]);
+            for (int j = 1; j < k; ++j) Z[(int64_t)(j - 1) * a.ld + r] = Z[(int64_t)j * a.ld + r] - by * v[j];
+        }
+    }
+}
+
+void outer_purge(const OuterArgs& a, int k, double* vout, cudaStream_t s) {
+    k_purge_prep<<<1, kThreads, 0, s>>>(a, k);
+    k_purge_rows<<<a.ew_blocks, kThreads, 0, s>>>(a, a.U, a.W, k, vout);
 }
 
 __global__ void k_set_diag(double* H, const double* theta, int c0, int cnt) {

@@ -735,10 +735,11 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
             if (rn < tol || exhausted) {                                           // lines 8-10: lock
                 double* vcol = h->V + (size_t)c * h->ld;
                 const bool more = (c + 1 < d);
-                outer_rotate(oa, h->U, k, 1, more ? k - 1 : 0, vcol, s);           // v_j = U s1; purge (line 22)
-                h->stats.kernel_launches += 1;
-                if (more && k > 1) {
-                    outer_rotate(oa, h->W, k, 1, k - 1, nullptr, s);
+                if (more && k >= 2) {
+                    outer_purge(oa, k, vcol, s);                                   // v_j = U s1; purge (line 22)
+                    h->stats.kernel_launches += 2;
+                } else {
+                    outer_rotate(oa, h->U, k, 1, 0, vcol, s);                      // v_j = U s1
                     h->stats.kernel_launches += 1;
                 }
                 if (h->opts.precision == ISIRA_MIXED) {
@@ -751,8 +752,6 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 if (c == d) break;
                 gram_dirty = true;
                 if (k >= 2) {                                                      // line 23: move sigma
-                    outer_set_diag(oa, 1, k - 1, s);
-                    h->stats.kernel_launches += 1;
                     const double move = std::max(omega * (th2 - th1), 0.01 * th2);
                     sig = th2 - move;
                     k -= 1;
