@@ -157,20 +157,20 @@ __device__ __forceinline__ T block_sum0(T v) {
 }
 
 // ------------------------------------------------------------------ row scheduler
-// Grid layout of an SpMV-style launch: [long-row CTAs][light-row CTAs].
+// Work of an SpMV-style gather launch, in units:
+//  * every row longer than light_deg is cut into work items of at most kItemNnz stored
+//    entries, summed by one warp; a row with several items gets its sum from the warp that
+//    finishes its last item, which adds the items' partial sums in item order (deterministic);
 //  * light rows (degree <= light_deg) are processed in tiles of 32 consecutive rows by one
-//    warp, G lanes per row, so the per-row epilogue runs with one lane per row and coalesced
-//    vector accesses;
-//  * every longer row is cut into work items of at most kItemNnz stored entries, one warp per
-//    item; a row with several items gets its sum from the warp that finishes its last item,
-//    which adds the items' partial sums in item order (deterministic) and runs the epilogue.
+//    warp, G lanes per row, so the per-row epilogue runs with one lane per row.
 // The row `skip` (the trimmed vertex, or -1) is never gathered: its epilogue runs from the
 // light tiles with a zero sum.
 constexpr int kItemNnz = 1024;
 
-// Work units are the items (0 .. n_items-1) followed by the light tiles; setup cuts the unit
-// list into n_warps ranges of equal estimated cost (one launch wave), warp w walking units
-// [warp_start[w], warp_start[w+1]).  The static partition keeps every reduction deterministic.
+// Work units are the items (0 .. n_items-1) followed by the light tiles.  By default warps take
+// units from a device counter (dynamic distribution); alternatively setup cuts the unit list
+// into n_warps ranges of equal estimated cost, warp w walking [warp_start[w], warp_start[w+1]).
+// Either way every row's sum is computed in the same order.
 constexpr int kUnitChunk = 2;      // default units a warp takes at a time (dynamic distribution)
 constexpr int kTileRowCost = 12;   // estimated cost of one row epilogue, in gathered entries
 constexpr int kItemCost = 32;      // fixed cost of one work item
@@ -225,6 +225,12 @@ constexpr int kDefaultHubBytes = 192 * 1024;  // hub block of a 1024-thread gath
             }                                \
         }                                    \
     } while (0)
+
+__device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 
 template <typename T>
 __device__ __forceinline__ T gather_x(const T* __restrict__ x, const T* sx, int hub, int32_t c) {
@@ -428,10 +434,10 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
             if (lane == 0) {
                 const int64_t first = it - kpos;
                 part[it] = s;
-                __threadfence();
-                const unsigned prev = atomicAdd(S.item_count + first, 1u);
+                // one acquire-release add: publishes this partial and, in the last arriver,
+                // makes every other item's partial visible (no full fences)
+                const unsigned prev = atomic_add_acq_rel(S.item_count + first, 1u);
                 if (prev == (unsigned)(nit - 1)) {
-                    __threadfence();
                     T tot = 0;
                     for (int q = 0; q < nit; ++q) tot += __ldcg(part + first + q);
                     S.item_count[first] = 0u;
