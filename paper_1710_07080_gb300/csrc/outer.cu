@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(kThreads) k_purge_rows(OuterArgs a, double* X,
 
 void outer_purge(const OuterArgs& a, int k, double* vout, cudaStream_t s) {
     k_purge_prep<<<1, kThreads, 0, s>>>(a, k);
-    k_purge_rows<<<a.ew_blocks, kThreads, 0, s>>>(a, a.U, a.W, k, vout);
+    k_purge_rows<<<wave_of((const void*)k_purge_rows, 0, a.ew_blocks), kThreads, 0, s>>>(a, a.U, a.W, k, vout);
 }
 
 __global__ void k_set_diag(double* H, const double* theta, int c0, int cnt) {

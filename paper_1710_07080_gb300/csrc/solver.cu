@@ -604,7 +604,9 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
             cudaFree(prefix);
         }
         rs.warp_start = h->warp_start;
-        h->ew_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)h->nsm * 4));
+        // up to 8 CTAs per SM (a full SM of 256-thread CTAs); register-heavy row kernels are cut to
+        // one wave of their resident CTAs at launch
+        h->ew_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)h->nsm * 8));
         h->ts_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64, (int64_t)h->nsm * 6));
         // shared scratch for block partial sums: 512 slots x the largest grid
         const int64_t maxgrid = std::max<int64_t>({(int64_t)rs.grid(), (int64_t)h->ew_blocks, (int64_t)h->ts_blocks});
