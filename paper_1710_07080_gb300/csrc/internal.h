@@ -88,7 +88,8 @@ struct OuterArgs {
 };
 
 void outer_residual(const OuterArgs& a, int k, cudaStream_t s);
-void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, int lds, HostStatus* hs,
+// warm_w > 0: S's leading warm_w x warm_w block holds eigenvectors of H's leading block (warm start)
+void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, int lds, HostStatus* hs, int warm_w,
                    cudaStream_t s);
 // Z <- Z - Q(Q^T Z) - mean(Z) twice, then ||Z||, for Q = [U(:,0:k) V(:,0:c)]; Z already holds the
 // FP64 input.  Writes cgs_in / cgs_out to the host status.
@@ -100,10 +101,11 @@ cudaError_t outer_gather_attrs(int bytes);
 int gather_ctas_per_sm(int tpb, int hub_bytes);
 // X(:, 0:ncol) <- X(:, 0:kk) S(:, c0:c0+ncol); with vout != NULL also vout = X S(:, 0).
 void outer_rotate(const OuterArgs& a, double* X, int kk, int c0, int ncol, double* vout, cudaStream_t s);
-// H <- diag(theta(c0 : c0 + cnt))
+// H <- diag(theta[c0 .. c0+cnt)) and S's leading cnt x cnt block <- I (after a restart)
 void outer_set_diag(const OuterArgs& a, int c0, int cnt, cudaStream_t s);
 // purge after a lock with a Householder reflection (U and W in place, H to P H P trimmed);
-// vout receives the locked vector U s1 (S(:, 0) of the last Rayleigh-Ritz step)
+// vout receives the locked vector U s1 (S(:, 0) of the last Rayleigh-Ritz step); S's leading
+// (k-1) x (k-1) block becomes the eigenvectors of the new H, (P S)(1:k, 1:k)
 void outer_purge(const OuterArgs& a, int k, double* vout, cudaStream_t s);
 // Z <- centred SplitMix64 vector, block `blk` of stream `seed`.
 void outer_random(const OuterArgs& a, uint64_t seed, uint64_t blk, cudaStream_t s);

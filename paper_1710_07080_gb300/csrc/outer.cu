@@ -181,8 +181,12 @@ __device__ void small_gemm(const double* X, const double* Y, double* C, int K, b
     __syncthreads();
 }
 
+// warm_w > 0: S holds, in its leading warm_w x warm_w block, eigenvectors of H's leading block
+// (from the previous outer step, or set by the purge / restart).  The kernel then works on
+// A = Q0^T H Q0, Q0 = S(0:w, 0:w) (+) I, which is diagonal up to the rows and columns added since
+// (an arrowhead after one expansion), and returns S = Q0 times A's eigenvectors.
 __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* H, int ldh, int k, double* theta, double* S,
-                                                      int lds, HostStatus* hs) {
+                                                      int lds, HostStatus* hs, int warm_w) {
     extern __shared__ double eig_sm[];
     __shared__ int partner_[kMMax], zero_[kMMax], perm[kMMax];
     __shared__ double alpha_[kMMax], beta_[kMMax], red_[kEigThreads / 32];
@@ -195,13 +199,28 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* H, int ld
     double* D2 = eig_sm + 2 * blk;
     double* D3 = eig_sm + 3 * blk;
     // FP32 phase buffers alias D2, D3 (unused until the FP64 phase)
+    double* W5 = eig_sm + 4 * blk;  // warm-start basis Q0 (kept to the end)
     float* F = reinterpret_cast<float*>(D2);
     JacobiSmem<float> fs{F, F + blk, F + 2 * blk, F + 3 * blk, partner_, alphaf_, betaf_, zero_, red_};
+    const int w0 = (warm_w > 0 && warm_w <= k && k >= 2) ? warm_w : 0;
     for (int idx = tid; idx < K * K; idx += blockDim.x) {
         const int i = idx % K, j = idx / K;
-        const double h = (i < k && j < k) ? 0.5 * (H[i + j * ldh] + H[j + i * ldh]) : 0.0;
-        D0[i + j * kEigLd] = h;
-        fs.A[i + j * kEigLd] = (float)h;
+        D0[i + j * kEigLd] = (i < k && j < k) ? 0.5 * (H[i + j * ldh] + H[j + i * ldh]) : 0.0;
+        if (w0) W5[i + j * kEigLd] = (i < w0 && j < w0) ? S[i + j * lds] : (i == j ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    if (w0) {
+        small_gemm(D0, W5, D1, K, false);                          // T = H Q0
+        small_gemm(W5, D1, D3, K, true);                           // A = Q0^T T
+        for (int idx = tid; idx < K * K; idx += blockDim.x) {
+            const int i = idx % K, j = idx / K;
+            D0[i + j * kEigLd] = 0.5 * (D3[i + j * kEigLd] + D3[j + i * kEigLd]);
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < K * K; idx += blockDim.x) {
+        const int i = idx % K, j = idx / K;
+        fs.A[i + j * kEigLd] = (float)D0[i + j * kEigLd];
         fs.Q[i + j * kEigLd] = (i == j) ? 1.0f : 0.0f;
     }
     __syncthreads();
@@ -233,9 +252,15 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* H, int ld
         small_gemm(D1, D2, D3, K, true);                           // B = Q^T T
         JacobiSmem<double> ds{D3, D2, D1, D0, partner_, alpha_, beta_, zero_, red_};
         sweeps64 = jacobi_sweeps<double>(ds, K, 12, 0.0, true);
-        // eigenvalues on the diagonal of ds.A, eigenvectors in the columns of ds.Q
+        // eigenvalues on the diagonal of ds.A, eigenvectors in the columns of ds.Q (of A)
         double* Af = ds.A;
         double* Qf = ds.Q;
+        if (w0) {
+            // eigenvectors of H: Q0 times those of A, into a buffer the sweeps left free
+            double* Fr = ds.A2 != Af && ds.A2 != Qf ? ds.A2 : ds.Q2;
+            small_gemm(W5, Qf, Fr, K, false);
+            Qf = Fr;
+        }
         if (tid == 0) {
             for (int i = 0; i < k; ++i) perm[i] = i;
             for (int i = 0; i < k; ++i) {
@@ -269,11 +294,11 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* H, int ld
 }
 
 void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, int lds, HostStatus* hs,
-                   cudaStream_t s) {
-    const int bytes = (int)(sizeof(double) * 4 * kMMax * kEigLd);
+                   int warm_w, cudaStream_t s) {
+    const int bytes = (int)(sizeof(double) * 5 * kMMax * kEigLd);
     static std::once_flag once;
     std::call_once(once, [bytes] { cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
-    k_sym_eig<<<1, kEigThreads, bytes, s>>>(H, ldh, k, theta, S, lds, hs);
+    k_sym_eig<<<1, kEigThreads, bytes, s>>>(H, ldh, k, theta, S, lds, hs, warm_w);
 }
 
 // ------------------------------------------------------------------ tall-skinny passes (line 18, line 4)
@@ -609,6 +634,24 @@ __global__ void __launch_bounds__(kThreads) k_purge_prep(OuterArgs a, int k) {
         const double h = Hs[i][j] - b * (v[i] * w[j] + w[i] * v[j]) + bg * v[i] * v[j];
         a.H[(i - 1) + (j - 1) * kMMax] = h;
     }
+    // eigenvectors of the new H: (P S)(1:k, 1:k), P S = S - beta v (v^T S) (warm start of the
+    // next Rayleigh-Ritz step); S is read whole into shared memory before it is overwritten
+    __syncthreads();
+    for (int idx = tid; idx < k * k; idx += blockDim.x) {
+        const int i = idx % k, j = idx / k;
+        Hs[i][j] = a.S[i + j * kMMax];
+    }
+    __syncthreads();
+    for (int j = tid; j < k; j += blockDim.x) {
+        double t = 0.0;
+        for (int i = 0; i < k; ++i) t += v[i] * Hs[i][j];
+        w[j] = t;                                          // (v^T S)_j
+    }
+    __syncthreads();
+    for (int idx = tid; idx < (k - 1) * (k - 1); idx += blockDim.x) {
+        const int i = idx % (k - 1) + 1, j = idx / (k - 1) + 1;
+        a.S[(i - 1) + (j - 1) * kMMax] = Hs[i][j] - b * v[i] * w[j];
+    }
 }
 
 // X(r, 0:k) <- (X P)(r, 1:k) in place, one thread per row; vout[r] = -sign(s1[0]) (X P)(r, 0)
@@ -637,15 +680,18 @@ void outer_purge(const OuterArgs& a, int k, double* vout, cudaStream_t s) {
     k_purge_rows<<<wave_of((const void*)k_purge_rows, 0, a.ew_blocks), kThreads, 0, s>>>(a, a.U, a.W, k, vout);
 }
 
-__global__ void k_set_diag(double* H, const double* theta, int c0, int cnt) {
+// after a restart U S(:, c0 : c0+cnt) is the Ritz basis: H is diagonal and its eigenvectors
+// (the warm start of the next Rayleigh-Ritz step) are the identity
+__global__ void k_set_diag(double* H, const double* theta, double* S, int c0, int cnt) {
     for (int idx = threadIdx.x; idx < kMMax * kMMax; idx += blockDim.x) {
         const int i = idx % kMMax, j = idx / kMMax;
         H[idx] = (i == j && i < cnt) ? theta[c0 + i] : 0.0;
+        if (i < cnt && j < cnt) S[idx] = i == j ? 1.0 : 0.0;
     }
 }
 
 void outer_set_diag(const OuterArgs& a, int c0, int cnt, cudaStream_t s) {
-    k_set_diag<<<1, kThreads, 0, s>>>(a.H, a.theta, c0, cnt);
+    k_set_diag<<<1, kThreads, 0, s>>>(a.H, a.theta, a.S, c0, cnt);
 }
 
 __global__ void k_random(double* Z, int64_t n, uint64_t seed, uint64_t blk) {

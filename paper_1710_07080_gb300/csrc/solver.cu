@@ -725,10 +725,12 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         int k = 1, c = 0;
         double sig = sigma;
         bool gram_dirty = true;
+        int warm_w = 0;   // S's leading warm_w block diagonalises H's leading block (warm start)
         while (true) {
             if (h->stats.outer_steps >= max_outer) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
             h->stats.outer_steps += 1;
-            outer_sym_eig(h->H, kMMax, k, h->theta, h->S, kMMax, h->hs_dev, s);   // line 6
+            outer_sym_eig(h->H, kMMax, k, h->theta, h->S, kMMax, h->hs_dev, warm_w, s);   // line 6
+            warm_w = k;
             outer_residual(oa, k, s);                                              // line 7
             h->stats.kernel_launches += 2;
             sync(h);
@@ -757,11 +759,13 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                     const double move = std::max(omega * (th2 - th1), 0.01 * th2);
                     sig = th2 - move;
                     k -= 1;
+                    warm_w = k;                        // the purge left S = eigenvectors of H
                 } else {
                     outer_random(oa, o.seed, (uint64_t)(1000003 + c), s);
                     h->stats.kernel_launches += 1;
                     if (!expand_basis(h, 0, c)) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
                     k = 1;
+                    warm_w = 0;
                 }
                 continue;
             }
@@ -771,6 +775,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 outer_set_diag(oa, 0, q, s);
                 h->stats.kernel_launches += 3;
                 k = q;
+                warm_w = q;
                 h->stats.restarts += 1;
             }
             // line 17: inner solve of Eq. 2.14 and back-map Eq. 2.5 -> Z
@@ -896,7 +901,7 @@ isira_status isira_inner_solve(isira_handle h, int precision, double sigma, int 
 isira_status isira_sym_eig(int k, const double* d_H, double* d_theta, double* d_S, void* stream) {
     if (k < 1 || k > kMMax || !d_H || !d_theta || !d_S) return ISIRA_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    outer_sym_eig(d_H, k, k, d_theta, d_S, k, nullptr, s);
+    outer_sym_eig(d_H, k, k, d_theta, d_S, k, nullptr, 0, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? ISIRA_OK : ISIRA_ERR_CUDA;
