@@ -11,6 +11,7 @@ ctypes with numpy arrays.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -50,26 +51,50 @@ class Stats(C.Structure):
                 ("sec_w", C.c_double), ("sec_inner", C.c_double), ("sec_total", C.c_double)]
 
 
+def build_variant(out_path: str, plant: int) -> str:
+    """Mutation testing only: compile a separate copy of the oracle with one planted mistake
+    (-DOR_PLANT=plant, see isira_oracle.c) to check that the pins catch it."""
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", f"-DOR_PLANT={int(plant)}",
+                           "-Wl,-Bsymbolic", "-o", out_path, _SRC, "-lm"])
+    return out_path
+
+
+@contextlib.contextmanager
+def using_library(path: str):
+    """Mutation testing only: route every oracle call through the library at `path`."""
+    global _lib
+    saved = _lib
+    _lib = _bind(C.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = C.CDLL(build())
-        P = C.c_void_p
-        lib.or_laplacian_apply.argtypes = [C.c_int64, P, P, P, P]
-        lib.or_sym_eig.argtypes = [C.c_int, P, P, P, C.c_int]
-        lib.or_sym_eig.restype = C.c_int
-        lib.or_dense_laplacian_eig.argtypes = [C.c_int64, P, P, P, P]
-        lib.or_trimmed_apply.argtypes = [C.c_int64, P, P, C.c_int64, C.c_double, C.c_double, P, C.c_int,
-                                         C.c_int, P, P]
-        lib.or_backmap.argtypes = [C.c_int64, C.c_int64, P, P]
-        lib.or_precond_apply.argtypes = [C.c_int64, P, C.c_int64, C.c_double, C.c_double, P, C.c_int, P, P]
-        lib.or_inner_solve.argtypes = [C.c_int64, P, P, C.c_int64, C.c_double, C.c_double, P, C.c_int,
-                                       C.c_int, P, C.c_double, C.c_int, P, P]
-        lib.or_inner_solve.restype = C.c_int
-        lib.or_isira.argtypes = [C.c_int64, P, P, P, C.POINTER(Params), P, P, C.POINTER(Stats)]
-        lib.or_isira.restype = C.c_int
-        _lib = lib
+        _lib = _bind(C.CDLL(build()))
     return _lib
+
+
+def _bind(lib):
+    """Declares the C signatures on a loaded oracle library."""
+    P = C.c_void_p
+    lib.or_laplacian_apply.argtypes = [C.c_int64, P, P, P, P]
+    lib.or_sym_eig.argtypes = [C.c_int, P, P, P, C.c_int]
+    lib.or_sym_eig.restype = C.c_int
+    lib.or_dense_laplacian_eig.argtypes = [C.c_int64, P, P, P, P]
+    lib.or_trimmed_apply.argtypes = [C.c_int64, P, P, C.c_int64, C.c_double, C.c_double, P, C.c_int,
+                                     C.c_int, P, P]
+    lib.or_backmap.argtypes = [C.c_int64, C.c_int64, P, P]
+    lib.or_precond_apply.argtypes = [C.c_int64, P, C.c_int64, C.c_double, C.c_double, P, C.c_int, P, P]
+    lib.or_inner_solve.argtypes = [C.c_int64, P, P, C.c_int64, C.c_double, C.c_double, P, C.c_int,
+                                   C.c_int, P, C.c_double, C.c_int, P, P]
+    lib.or_inner_solve.restype = C.c_int
+    lib.or_isira.argtypes = [C.c_int64, P, P, P, C.POINTER(Params), P, P, C.POINTER(Stats)]
+    lib.or_isira.restype = C.c_int
+    return lib
 
 
 def _p(a: np.ndarray):

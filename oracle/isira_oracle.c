@@ -54,13 +54,20 @@ static double uniform_at(uint64_t seed, uint64_t counter) {
     return (double)(splitmix64_at(seed, counter) >> 11) * (1.0 / 9007199254740992.0);
 }
 
+/* Mutation testing only: tests/test_oracle_mutants.py builds separate copies of this file with
+ * -DOR_PLANT=k, each planting one known, plausible mistake, and checks that the pins in
+ * tests/test_oracle_pins.py catch it.  The oracle itself is built with OR_PLANT = 0. */
+#ifndef OR_PLANT
+#define OR_PLANT 0
+#endif
+
 /* ---------------------------------------------------------------- Eq. 1.1 */
 
 void or_laplacian_apply(int64_t n, const int64_t* rp, const int32_t* ci, const double* x, double* y) {
     for (int64_t r = 0; r < n; ++r) {
         double deg = (double)(rp[r + 1] - rp[r]);
         double s = deg * x[r];
-        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) s -= x[ci[e]];
+        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) s -= (OR_PLANT == 1 ? -1.0 : 1.0) * x[ci[e]];
         y[r] = s;
     }
 }
@@ -113,7 +120,7 @@ int or_sym_eig(int k, const double* Ain, double* theta, double* S, int max_sweep
                 A[p + (size_t)q * k] = A[q + (size_t)p * k] = 0.0;   /* what the rotation annihilates */
                 for (int r = 0; r < k; ++r) {          /* S <- S J */
                     double srp = S[r + (size_t)p * k], srq = S[r + (size_t)q * k];
-                    S[r + (size_t)p * k] = c * srp - s * srq;
+                    S[r + (size_t)p * k] = c * srp - (OR_PLANT == 2 ? -s : s) * srq;
                     S[r + (size_t)q * k] = s * srp + c * srq;
                 }
             }
@@ -180,8 +187,8 @@ void or_trimmed_apply(int64_t n, const int64_t* rp, const int32_t* ci, int64_t t
             if (col == trim) continue;                 /* column i is deleted */
             s -= xh[hat_of(col, trim)];
         }
-        if (!drop_rank1) s += (sigma / (double)n) * s1;
-        for (int j = 0; j < c; ++j) s += delta * V[r + (int64_t)j * n] * g[j];
+        if (!drop_rank1 && OR_PLANT != 3) s += (sigma / (double)n) * s1;
+        for (int j = 0; j < c; ++j) s += (OR_PLANT == 4 ? -delta : delta) * V[r + (int64_t)j * n] * g[j];
         yh[rh] = s;
     }
     free(g);
@@ -190,7 +197,7 @@ void or_trimmed_apply(int64_t n, const int64_t* rp, const int32_t* ci, int64_t t
 void or_backmap(int64_t n, int64_t trim, const double* zh, double* zstar) {
     double s = 0.0;
     for (int64_t t = 0; t < n - 1; ++t) s += zh[t];
-    double shift = s / (double)n;
+    double shift = s / (double)(OR_PLANT == 5 ? n - 1 : n);
     for (int64_t r = 0; r < n; ++r) zstar[r] = (r == trim ? 0.0 : zh[hat_of(r, trim)]) - shift;
 }
 
@@ -334,7 +341,7 @@ static int minres(const op_ctx* cx, const double* b, double* x, double tau, int 
         double bb = dot(nh, r2, y);
         beta = bb > 0.0 ? sqrt(bb) : 0.0;
         double oldeps = epsln;
-        double dlt = cs * dbar + sn * alfa;
+        double dlt = cs * dbar + (OR_PLANT == 6 ? -sn : sn) * alfa;
         double gbar = sn * dbar - cs * alfa;
         epsln = sn * beta;
         dbar = -cs * beta;
