@@ -294,7 +294,7 @@ static void ctx_precond(const op_ctx* x, const double* xh, double* ph) {
         int64_t rh = hat_of(r, x->trim);
         double s = 0.0;
         for (int a = 0; a < c; ++a) s += x->V[r + (int64_t)a * n] * b[a];
-        ph[rh] -= x->delta * s / x->mdiag[rh];
+        ph[rh] -= (OR_PLANT == 7 ? -x->delta : x->delta) * s / x->mdiag[rh];
     }
     free(b);
 }
@@ -515,7 +515,7 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
             /* the search space cannot grow past the orthogonal complement of [V 1] */
             int exhausted = (k + c >= n - 1);
             if (rn < p->eps || exhausted) {                       /* lines 8-10 */
-                lam[j - 1] = theta[0];
+                lam[j - 1] = theta[OR_PLANT == 8 && k >= 2 ? 1 : 0];
                 memcpy(V + (int64_t)c * n, y, sizeof(double) * (size_t)n);
                 ++c;
                 st->n_locked = c;

@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import synthgraphs as sg
+from tests import closed_forms as cf
 from tests import test_oracle_pins as pins
 
 pytestmark = pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc is needed to build the variants")
@@ -26,6 +27,10 @@ MUTANTS = {
         lambda: pins.test_backmap_is_orthogonal_to_ones_and_places_zero()),
     6: ("wrong sign in the MINRES Givens recurrence",
         lambda: pins.test_minres_matches_direct_solve("spd")),
+    7: ("SMW correction of the preconditioner with the wrong sign (Eq. 3.6)",
+        lambda: pins.test_preconditioner_smw_inverts_its_matrix()),
+    8: ("the lock records the second Ritz value instead of the first (Algorithm 2, line 9)",
+        lambda: pins.test_isira_closed_forms(sg.path(40), cf.path(40), 6)),
 }
 
 
