@@ -279,7 +279,7 @@ def oracle_full_counts(name):
 
 def project_oracle(st_sample, full):
     """Seconds of the oracle's full run, projected from a sample's per-unit costs: seconds per
-    recomputed W column (line 4), per inner MINRES iteration (line 17) and per outer step (the
+    recomputed W column (the W_k, H_k step of Algorithm 2), per inner MINRES iteration (its inner solve) and per outer step (the
     rest), times the full run's counts of those units."""
     per_col = st_sample["sec_w"] / max(1, st_sample["w_columns"])
     per_it = st_sample["sec_inner"] / max(1, st_sample["inner_iters"])

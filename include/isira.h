@@ -137,7 +137,7 @@ ISIRA_API isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, c
 
 /* Algorithm 2: computes the k (the paper's d, 1 <= k <= min(32, n-2)) smallest positive
  * eigenpairs.  sigma: initial shift (the paper uses 0).  tol: the paper's epsilon, an
- * absolute bound on ||W s1 - theta1 U s1||_2 for unit Ritz vectors (Algorithm 2 line 8).
+ * absolute bound on ||W s1 - theta1 U s1||_2 for unit Ritz vectors (the lock test of Algorithm 2).
  * d_u0: optional device n-vector, the k0 = 1 start basis (must be orthogonal to the
  * all-ones vector and of unit norm; NULL = a SplitMix64 vector from opts.seed).
  * Blocks until done.  Returns ISIRA_ERR_NO_CONVERGENCE if max_outer is reached (pairs
@@ -176,7 +176,7 @@ ISIRA_API void isira_destroy(isira_handle h);
 ISIRA_API isira_status isira_apply_operator(isira_handle h, int precision, double sigma, int c, const double* d_V,
                                   const void* d_x, void* d_y);
 
-/* One inner solve (Algorithm 2 line 17): preconditioned MINRES on the operator
+/* One inner solve (the inner solve of Algorithm 2): preconditioned MINRES on the operator
  * above for the right-hand side d_r (double n-vector, its trim entry ignored) to
  * relative preconditioned residual tau, then the back-map of Eq. 2.5:
  * d_z (double n-vector) is orthogonal to the all-ones vector.  *iters and *relres
@@ -185,7 +185,7 @@ ISIRA_API isira_status isira_inner_solve(isira_handle h, int precision, double s
                                const double* d_r, double tau, int max_it, double* d_z, int* iters,
                                double* relres);
 
-/* All eigenpairs of a symmetric k-by-k matrix (k <= 64), Algorithm 2 line 6: one CTA of
+/* All eigenpairs of a symmetric k-by-k matrix (k <= 64), the Rayleigh-Ritz step of Algorithm 2: one CTA of
  * parallel cyclic Jacobi in FP64.  d_H: k-by-k column-major input (not modified);
  * d_theta: k ascending eigenvalues; d_S: k-by-k unit eigenvectors, each signed so that
  * its largest-magnitude entry (first on ties) is positive.  stream as above. */

@@ -396,7 +396,7 @@ static void cgs_pass(int64_t n, const double* U, int k, const double* V, int c, 
     free(h);
 }
 
-/* Orthonormalise z against U and V (Algorithm 2, line 18). Returns 1 on breakdown replacement. */
+/* Orthonormalise z against U and V (Algorithm 2, orthonormalisation). Returns 1 on breakdown replacement. */
 static int orthonormalize(int64_t n, const double* U, int k, const double* V, int c, double* z,
                           uint64_t seed, int* n_breakdowns) {
     int replaced = 0;
@@ -469,18 +469,18 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
     double* col = (double*)malloc(sizeof(double) * (size_t)n);
     double* vtu = (double*)calloc((size_t)(d + 1), sizeof(double));
 
-    /* line 1: D = [], V = [], k = k0 = 1, flag = 0 */
+    /* start: D = [], V = [], k = k0 = 1, flag = 0 */
     memcpy(U, u0, sizeof(double) * (size_t)n);
     int k = 1, c = 0;
     double sigma = p->sigma0;
     int status = 0;
 
-    for (int j = 1; j <= d; ++j) {                               /* line 2 */
+    for (int j = 1; j <= d; ++j) {                               /* for j = 1 .. d */
         int flag = 0;
-        while (!flag) {                                          /* line 3 */
+        while (!flag) {                                          /* until pair j locks */
             if (st->outer_steps >= p->max_outer) { status = 1; goto finish; }
             st->outer_steps++;
-            /* line 4: W_k = (L + delta V V^T) U_k,  H_k = U_k^T W_k */
+            /* W_k = (L + delta V V^T) U_k,  H_k = U_k^T W_k */
             const double t_w = wall_seconds();
             st->w_columns += k;
             for (int a = 0; a < k; ++a) {
@@ -499,9 +499,9 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
                     H[a + (size_t)b * k] = H[b + (size_t)a * k] = h;
                 }
             st->sec_w += wall_seconds() - t_w;
-            /* line 6: all eigenpairs of H_k, ascending, unit vectors */
+            /* Rayleigh-Ritz: all eigenpairs of H_k, ascending, unit vectors */
             or_sym_eig(k, H, theta, S, 100);
-            /* line 7: r = W_k s1 - theta1 U_k s1 */
+            /* residual: r = W_k s1 - theta1 U_k s1 */
             for (int64_t t = 0; t < n; ++t) { y[t] = 0.0; r[t] = 0.0; }
             for (int a = 0; a < k; ++a) {
                 double s = S[a];
@@ -514,34 +514,34 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
             double rn = nrm2(n, r);
             /* the search space cannot grow past the orthogonal complement of [V 1] */
             int exhausted = (k + c >= n - 1);
-            if (rn < p->eps || exhausted) {                       /* lines 8-10 */
+            if (rn < p->eps || exhausted) {                       /* lock */
                 lam[j - 1] = theta[OR_PLANT == 8 && k >= 2 ? 1 : 0];
                 memcpy(V + (int64_t)c * n, y, sizeof(double) * (size_t)n);
                 ++c;
                 st->n_locked = c;
                 flag = 1;
             } else {
-                if (k == m) {                                      /* lines 12-15: restart */
+                if (k == m) {                                      /* restart */
                     rotate_basis(n, U, k, S, 0, q);
                     rotate_basis(n, W, k, S, 0, q);
                     k = q;
                     st->restarts++;
                 }
-                /* line 17: trimmed solve (Eq. 2.4 / 2.14) and the back-map (Eq. 2.5) */
+                /* inexact inner solve: trimmed solve (Eq. 2.4 / 2.14) and the back-map (Eq. 2.5) */
                 double rr;
                 const double t_in = wall_seconds();
                 int its = or_inner_solve(n, rp, ci, trim, sigma, delta, V, c, p->drop_rank1, r,
                                          p->tau_inner, p->max_inner, z, &rr);
                 st->inner_iters += its;
                 st->sec_inner += wall_seconds() - t_in;
-                /* line 18: orthonormalise against U_k and V */
+                /* orthonormalise against U_k and V */
                 if (orthonormalize(n, U, k, V, c, z, p->seed, &st->breakdowns) < 0) { status = 1; goto finish; }
-                memcpy(U + (int64_t)k * n, z, sizeof(double) * (size_t)n);   /* line 19 */
+                memcpy(U + (int64_t)k * n, z, sizeof(double) * (size_t)n);   /* expand */
                 ++k;
             }
         }
         if (j == d) break;
-        /* line 22: purge v_j; line 23: move sigma */
+        /* purge v_j, then move sigma */
         double th2 = (k >= 2) ? theta[1] : sigma;
         if (k >= 2) {
             rotate_basis(n, U, k, S, 1, k - 1);

@@ -85,9 +85,9 @@ typedef struct {
     int breakdowns;
     int64_t trim;
     double delta;
-    long long w_columns;   /* columns of W_k recomputed (line 4), summed over outer steps */
-    double sec_w;          /* wall seconds in line 4 (W_k, H_k) */
-    double sec_inner;      /* wall seconds in line 17 (inner solves) */
+    long long w_columns;   /* columns of W_k recomputed (W_k, H_k step), summed over outer steps */
+    double sec_w;          /* wall seconds in the W_k, H_k step */
+    double sec_inner;      /* wall seconds in the inner solves */
     double sec_total;      /* wall seconds of the whole call */
 } or_stats;
 

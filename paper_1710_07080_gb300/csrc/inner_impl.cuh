@@ -1,4 +1,4 @@
-// inner_impl.cuh -- the inexact inner solve of Algorithm 2 (line 17) on the GPU.
+// inner_impl.cuh -- the inexact inner solve of Algorithm 2 on the GPU.
 //
 // Operator (Theorem 2.6, Eq. 2.14), applied in n-space with the trimmed entry i
 // pinned to zero (x_i = 0 in every Krylov vector, y_i = 0):

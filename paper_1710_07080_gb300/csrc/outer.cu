@@ -1,10 +1,10 @@
 // outer.cu -- FP64 kernels of the outer loop of Algorithm 2 and of the setup.
 //
-//   residual      r = W s1 - theta1 U s1, ||r||                     (Algorithm 2 line 7)
-//   sym_eig       all eigenpairs of H_k, one CTA, parallel Jacobi    (line 6)
-//   cgs2          classical Gram-Schmidt, two passes, against [U V 1] (line 18)
-//   expand        U(:,k) = u, W(:,k) = L u, H(:,k) = U^T W(:,k)      (lines 4, 19)
-//   rotate        X <- X S(:, a:b) in place, row tiles in shared memory (lines 13, 22)
+//   residual      r = W s1 - theta1 U s1, ||r||                     (Algorithm 2, residual)
+//   sym_eig       all eigenpairs of H_k, one CTA, parallel Jacobi    (Rayleigh-Ritz)
+//   cgs2          classical Gram-Schmidt, two passes, against [U V 1] (orthonormalisation)
+//   expand        U(:,k) = u, W(:,k) = L u, H(:,k) = U^T W(:,k)      (expansion)
+//   rotate        X <- X S(:, a:b) in place, row tiles in shared memory (restart)
 //   true_residual ||L v_j - lambda_j v_j||                           (final check)
 //   setup         degrees, maximum degree and its vertex, row classes (Remark 4.1)
 // The tall-skinny kernels stage a tile of basis rows in shared memory once and use
@@ -16,7 +16,7 @@
 
 namespace isira {
 
-// ------------------------------------------------------------------ residual (line 7)
+// ------------------------------------------------------------------ residual
 
 __global__ void __launch_bounds__(kThreads) k_residual(OuterArgs a, int k) {
     __shared__ double s1[kMMax];
@@ -47,7 +47,7 @@ void outer_residual(const OuterArgs& a, int k, cudaStream_t s) {
     k_residual<<<a.ew_blocks, kThreads, 0, s>>>(a, k);
 }
 
-// ------------------------------------------------------------------ symmetric eigensolver (line 6)
+// ------------------------------------------------------------------ symmetric eigensolver (Rayleigh-Ritz)
 // All eigenpairs of the small symmetric H_k in one CTA.  One SM's FP64 pipe is slow on this
 // part, so the bulk of the work runs in FP32 and FP64 only finishes it:
 //   1. parallel cyclic Jacobi in FP32 (round-robin ordering: in each of K-1 rounds the K
@@ -301,7 +301,7 @@ void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, in
     k_sym_eig<<<1, kEigThreads, bytes, s>>>(H, ldh, k, theta, S, lds, hs, warm_w);
 }
 
-// ------------------------------------------------------------------ tall-skinny passes (line 18, line 4)
+// ------------------------------------------------------------------ tall-skinny passes (orthonormalisation, H column)
 
 constexpr int kTsRows = 64;              // rows per shared-memory tile
 constexpr int kTsMaxCols = kMMax + kCMax;
@@ -474,7 +474,7 @@ void outer_cgs2(const OuterArgs& a, int k, int c, cudaStream_t s) {
         a, k, c, a.Z, a.Z, cB, nullptr, nullptr, 0);
 }
 
-// ------------------------------------------------------------------ expand (lines 4 and 19)
+// ------------------------------------------------------------------ expand
 
 // Plain gather g[r] = sum_{c in N(r)} x[c] over the full Laplacian (no trimmed row).
 template <int G, int TPB>
@@ -588,7 +588,7 @@ void outer_rotate(const OuterArgs& a, double* X, int kk, int c0, int ncol, doubl
     k_rotate<<<wave_of((const void*)k_rotate, smem, a.ts_blocks), kThreads, smem, s>>>(a, X, kk, c0, ncol, vout);
 }
 
-// ------------------------------------------------------------------ purge after a lock (line 22)
+// ------------------------------------------------------------------ purge after a lock
 // The purge keeps span U minus the locked Ritz direction U s1.  Any orthonormal basis of that
 // space gives the same later Ritz pairs, so instead of the k x (k-1) product U S(:, 2:k) the
 // solver applies the Householder reflection P = I - beta v v^T, v = s1 + sign(s1[0]) e1, which

@@ -729,18 +729,18 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         while (true) {
             if (h->stats.outer_steps >= max_outer) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
             h->stats.outer_steps += 1;
-            outer_sym_eig(h->H, kMMax, k, h->theta, h->S, kMMax, h->hs_dev, warm_w, s);   // line 6
+            outer_sym_eig(h->H, kMMax, k, h->theta, h->S, kMMax, h->hs_dev, warm_w, s);   // Rayleigh-Ritz
             warm_w = k;
-            outer_residual(oa, k, s);                                              // line 7
+            outer_residual(oa, k, s);                                              // residual
             h->stats.kernel_launches += 2;
             sync(h);
             const double rn = hst(h)->rnorm, th1 = hst(h)->theta[0], th2 = hst(h)->theta[1];
             const bool exhausted = (int64_t)(k + c) >= h->n - 1;
-            if (rn < tol || exhausted) {                                           // lines 8-10: lock
+            if (rn < tol || exhausted) {                                           // lock
                 double* vcol = h->V + (size_t)c * h->ld;
                 const bool more = (c + 1 < d);
                 if (more && k >= 2) {
-                    outer_purge(oa, k, vcol, s);                                   // v_j = U s1; purge (line 22)
+                    outer_purge(oa, k, vcol, s);                                   // v_j = U s1; purge
                     h->stats.kernel_launches += 2;
                 } else {
                     outer_rotate(oa, h->U, k, 1, 0, vcol, s);                      // v_j = U s1
@@ -755,7 +755,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 h->stats.n_locked = c;
                 if (c == d) break;
                 gram_dirty = true;
-                if (k >= 2) {                                                      // line 23: move sigma
+                if (k >= 2) {                                                      // move sigma
                     const double move = std::max(omega * (th2 - th1), 0.01 * th2);
                     sig = th2 - move;
                     k -= 1;
@@ -769,7 +769,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 }
                 continue;
             }
-            if (k == m) {                                                          // lines 12-15: restart
+            if (k == m) {                                                          // restart
                 outer_rotate(oa, h->U, k, 0, q, nullptr, s);
                 outer_rotate(oa, h->W, k, 0, q, nullptr, s);
                 outer_set_diag(oa, 0, q, s);
@@ -778,7 +778,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 warm_w = q;
                 h->stats.restarts += 1;
             }
-            // line 17: inner solve of Eq. 2.14 and back-map Eq. 2.5 -> Z
+            // inner solve of Eq. 2.14 and back-map Eq. 2.5 -> Z
             if (h->opts.precision == ISIRA_MIXED)
                 run_inner<float>(h, h->fb, sig, c, h->Vt_f, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch,
                                  true);
@@ -786,7 +786,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 run_inner<double>(h, h->db, sig, c, h->V, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch,
                                   true);
             gram_dirty = false;
-            // lines 18-19: orthonormalise against [U V 1] and expand U, W, H
+            // orthonormalise against [U V 1] and expand U, W, H
             if (!expand_basis(h, k, c)) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
             k += 1;
         }

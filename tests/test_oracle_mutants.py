@@ -29,7 +29,7 @@ MUTANTS = {
         lambda: pins.test_minres_matches_direct_solve("spd")),
     7: ("SMW correction of the preconditioner with the wrong sign (Eq. 3.6)",
         lambda: pins.test_preconditioner_smw_inverts_its_matrix()),
-    8: ("the lock records the second Ritz value instead of the first (Algorithm 2, line 9)",
+    8: ("the lock records the second Ritz value instead of the first (Algorithm 2, lock step)",
         lambda: pins.test_isira_closed_forms(sg.path(40), cf.path(40), 6)),
 }
 
