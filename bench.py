@@ -529,7 +529,7 @@ def main():
     p1mx_c = sum(s["inner_phase1_csum"] for s in spmx) / max(1, p1mx_n)
     avgmx_s = p1mx_ms / 1e3 / max(1, p1mx_n)
     achieved_mx = phase1_bytes(n, Z, p1mx_c, 4) / avgmx_s / 1e9 if avgmx_s > 0 else None
-    traffic = ncu_traffic("phase1_fp64_rmat20")
+    traffic = ncu_traffic(f"phase1_fp64_{args.workload}")
     ops_peak = fp64_peak_ops(clocks.get("sm_max_mhz"))
     ops_achieved = phase1_fp64_ops(n, Z, p1_c) / avg_s if avg_s > 0 else None
 
