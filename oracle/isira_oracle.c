@@ -522,8 +522,8 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
                 flag = 1;
             } else {
                 if (k == m) {                                      /* restart */
-                    rotate_basis(n, U, k, S, 0, q);
-                    rotate_basis(n, W, k, S, 0, q);
+                    rotate_basis(n, U, k, S, OR_PLANT == 9 ? k - q : 0, q);
+                    rotate_basis(n, W, k, S, OR_PLANT == 9 ? k - q : 0, q);
                     k = q;
                     st->restarts++;
                 }

@@ -31,6 +31,8 @@ MUTANTS = {
         lambda: pins.test_preconditioner_smw_inverts_its_matrix()),
     8: ("the lock records the second Ritz value instead of the first (Algorithm 2, lock step)",
         lambda: pins.test_isira_closed_forms(sg.path(40), cf.path(40), 6)),
+    9: ("the restart keeps the q largest Ritz vectors instead of the q smallest (Algorithm 2)",
+        lambda: pins.test_isira_restart_branch_keeps_the_closed_form_pairs()),
 }
 
 

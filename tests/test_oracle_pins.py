@@ -303,3 +303,15 @@ def test_isira_rejects_bad_arguments():
     u0 = sg.start_vector(g.n, 1)
     _, _, st = oracle.isira(g.row_ptr, g.col_idx, 4, u0)
     assert st["status"] == 2
+
+
+def test_isira_restart_branch_keeps_the_closed_form_pairs():
+    """A small search space (m = 6, q = 4 for d = 4) forces restarts (U <- U S(:, 1:q)); the locked
+    pairs are still the path graph's closed-form eigenpairs."""
+    g = sg.path(40)
+    eps = 1e-10
+    lam, V, st = oracle.isira(g.row_ptr, g.col_idx, 4, sg.start_vector(g.n, 1), eps=eps, tau_inner=1e-3,
+                              m=6, q=4)
+    assert st["status"] == 0 and st["n_locked"] == 4
+    assert st["restarts"] > 0
+    _check_pairs(g, lam, V, eps, cf.path(40)[1:5])
