@@ -82,8 +82,9 @@ typedef struct {
                              packs the vectors' entries of high-degree vertices together for cache
                              reuse in the SpMV; vectors at the API stay in the caller's numbering;
                              0: use the caller's numbering (default 1) */
-    int gather_block;     /* threads per CTA of the SpMV gather kernels: 256 (up to 6 CTAs per SM)
-                             or 1024 (one CTA per SM); 0: 1024 with relabelling, else 256 */
+    int gather_block;     /* threads per CTA of the SpMV gather kernels: 256 (as many CTAs per SM as
+                             registers and shared memory allow, at most 6) or 1024 (one CTA per
+                             SM); 0: 1024 with relabelling, else 256 */
     int hub_kb;           /* with relabelling, each gather CTA copies the vector entries of the first
                              (highest-degree) vertices into this many KB of shared memory with one
                              bulk asynchronous copy; 0: 192 (capped by the device), < 0: none */
