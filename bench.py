@@ -1,22 +1,29 @@
 #!/usr/bin/env python3
 """Benchmark: time to the k smallest positive Laplacian eigenpairs with iSIRA on one GB300.
 
-Workload (default): R-MAT scale 20 (edge factor 16, a,b,c,d = .57/.19/.19/.05, seed 1),
-symmetrised, deduplicated, loop-free, largest connected component; k = 10; convergence at
-relative residual ||L x - lambda x|| / ||L|| <= 1e-8 with ||L|| := 2 * max degree.  The
-headline value is the plain-FP64 solve; the mixed solve (FP32 inner, FP64 outer) is timed on
-the same graph and reported beside it.
+Workload (default): 3-D 7-point grid 128^3 (n = 2,097,152), k = 20, mixed precision (FP32
+inner solve with FP32 accumulation, FP64 outer loop); the plain-FP64 solve of the same graph
+at the same tolerance is timed beside it.
+
+Tolerance.  The paper's epsilon is an absolute bound on the Ritz residual (the lock test of
+Algorithm 2).  The metric asks for relative residual ||L x - lambda x|| / ||L|| <= 1e-8
+(||L|| := 2 * max degree) and eigenvalue relative error <= 1e-9.  Because the eigenvalue error
+of a Ritz value behaves like ||r||^2 / gap, the second bar is the binding one for small,
+clustered eigenvalues, so the timed solves use
+    eps = min(1e-8 ||L||, sqrt(1e-10 * lambda_j * gap_j) over the wanted pairs),
+with lambda_j and gap_j estimated from the Ritz values of one untimed solve at 1e-8 ||L||
+(gaps below 1e-6 lambda_j are treated as one eigenvalue of higher multiplicity).
 
 A step is one full isira_solve (all of Algorithm 2: inner solves, orthogonalisation,
 Rayleigh-Ritz, restarts, locking).  Inputs are resident in HBM; the L2 is flushed (a 512 MB
 write) between timed steps; each step is timed with CUDA events on the library's stream.
 
-  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference] [--workload NAME]
 
 With N > 1 (torchrun) every rank solves its own copy of the workload (replicas: the method
-has no data-parallel split of one graph) and rank 0 prints the max over ranks.
-``--impl reference`` times the FP64 CPU oracle (Algorithm 2 as written, 1 thread) on a
-bounded sample of the same workload.
+has no data-parallel split of one graph) and rank 0 prints the max over ranks; the batched
+workload shards its graphs over the ranks instead.  ``--impl reference`` times the FP64 CPU
+oracle (Algorithm 2 as written, 1 thread) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -25,6 +32,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -37,17 +45,24 @@ sys.path.insert(0, ROOT)
 METRIC = "time to k eigenpairs at resid 1e-8 (mixed vs FP64); SpMV GB/s vs HBM peak"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
+EIG_RTOL_TARGET = 1e-10      # eigenvalue relative error aimed at (10x below the 1e-9 bar)
+RESID_REL = 1e-8             # relative residual bar of the metric
+CLUSTER_REL = 1e-6           # Ritz values closer than this (relative) count as one eigenvalue
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="rmat20")
+    p.add_argument("--workload", default="grid128^3")
     p.add_argument("--k", type=int, default=0, help="eigenpairs (0: the workload's k)")
-    p.add_argument("--rel-tol", type=float, default=0.0, help="relative residual (0: the workload's)")
+    p.add_argument("--eps", type=float, default=0.0,
+                   help="absolute tolerance of the lock test (0: the workload's rule)")
+    p.add_argument("--cmp-steps", type=int, default=2,
+                   help="timed solves of the other precision (plus one untimed)")
+    p.add_argument("--e2e-steps", type=int, default=3, help="timed end-to-end runs (plus one untimed)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--single-solve", choices=["fp64", "mixed"], default=None,
                    help="create one solver and run one solve, nothing else (for profiler captures)")
@@ -55,7 +70,7 @@ def parse():
                    help="solver option key=value applied to every solver (e.g. reorder=1)")
     p.add_argument("--graph-cache", default=None,
                    help="directory to keep the generated graph in (.npz), reused by later runs")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def solver_opts(args):
@@ -66,12 +81,31 @@ def solver_opts(args):
     return out
 
 
+# the configurations: k, the precision of the headline value, the tolerance rule, the reference
+WORKLOADS = {
+    "grid128^3": dict(k=20, prec="mixed", tol="c4", ref="grid3d:128,128,128", desc="3-D 7-point grid 128^3"),
+    "rmat20": dict(k=10, prec="fp64", tol="c4", ref="golden:rmat20_tight.json",
+                   desc="R-MAT scale 20, edge factor 16, a,b,c,d=.57/.19/.19/.05, seed 1, symmetrised LCC"),
+    "grid100x100": dict(k=5, prec="fp64", tol="abs:1e-10", ref="grid2d:100,100", desc="2-D 5-point grid 100 x 100"),
+    "rgg4M": dict(k=20, prec="mixed", tol="c4", ref=None,
+                  desc="random geometric graph, unit square, n = 4e6, r = sqrt(12/(pi n)), seed 1, LCC "
+                       "(GPU cell-list generator)"),
+    "rmat24": dict(k=10, prec="mixed", tol="c4", ref=None,
+                   desc="R-MAT scale 24, edge factor 16, same a,b,c,d, seed 1, symmetrised LCC (GPU generator)"),
+    "batch256": dict(k=8, prec="mixed", tol="rel:1e-8", ref=None,
+                     desc="256 graphs, n log-uniform in [1e3, 2e5]: ER mean degree 8 / 2-D grid / WS k=10 p=0.1"),
+}
+
+
 def load_workload(args):
     import numpy as np
     import synthgraphs as sg
     if args.workload == "rmat24":
         rp, ci = sg.rmat_gpu(24)
         return sg.Graph(rp.cpu().numpy(), ci.cpu().numpy(), "rmat24")
+    if args.workload == "rgg4M":
+        rp, ci = sg.rgg_gpu(4_000_000, 12.0, seed=1)
+        return sg.Graph(rp.cpu().numpy(), ci.cpu().numpy(), "rgg4M")
     if args.graph_cache:
         path = os.path.join(args.graph_cache, f"{args.workload}.npz")
         if os.path.exists(path):
@@ -112,27 +146,71 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-# the five configurations: k, the precision of the headline value, tolerance
-WORKLOADS = {
-    "rmat20": dict(k=10, prec="fp64", tol=("rel", 1e-8),
-                   desc="R-MAT scale 20, edge factor 16, a,b,c,d=.57/.19/.19/.05, seed 1, symmetrised LCC"),
-    "grid100x100": dict(k=5, prec="fp64", tol=("abs", 1e-10), desc="2-D 5-point grid 100 x 100"),
-    "grid128^3": dict(k=20, prec="mixed", tol=("rel", 1e-8), desc="3-D 7-point grid 128^3"),
-    "rgg4M": dict(k=20, prec="mixed", tol=("rel", 1e-8),
-                  desc="random geometric graph, unit square, n = 4e6, r = sqrt(12/(pi n)), seed 1, LCC"),
-    "rmat24": dict(k=10, prec="mixed", tol=("rel", 1e-8),
-                   desc="R-MAT scale 24, edge factor 16, same a,b,c,d, seed 1, symmetrised LCC (GPU generator)"),
-    "batch256": dict(k=8, prec="mixed", tol=("rel", 1e-8),
-                     desc="256 graphs, n log-uniform in [1e3, 2e5]: ER mean degree 8 / 2-D grid / WS k=10 p=0.1"),
-}
+# --------------------------------------------------------------------------------------------- tolerance
+
+def accuracy_eps(eig_est, norm_L, eig_rtol=EIG_RTOL_TARGET, resid_rel=RESID_REL, cluster_rel=CLUSTER_REL):
+    """Absolute lock tolerance meeting both accuracy bars: min(resid_rel * ||L||,
+    sqrt(eig_rtol * lambda_j * gap_j)) over the estimated eigenvalues, where gap_j is the distance
+    to the nearest other estimate that differs by more than cluster_rel * lambda_j (closer ones
+    are taken as copies of one multiple eigenvalue, whose eigenvectors may mix freely)."""
+    lam = sorted(float(x) for x in eig_est)
+    eps = resid_rel * norm_L
+    for j, l in enumerate(lam):
+        gaps = [abs(m - l) for i, m in enumerate(lam) if i != j and abs(m - l) > cluster_rel * abs(l)]
+        if gaps and l > 0:
+            eps = min(eps, math.sqrt(eig_rtol * l * min(gaps)))
+    return eps
 
 
-def workload_config(name, g, k, rel_tol):
+def fixed_eps(rule, norm_L):
+    """Tolerance of a rule that needs no estimates ("abs:x", "rel:x"), else None."""
+    if rule.startswith("abs:"):
+        return float(rule[4:])
+    if rule.startswith("rel:"):
+        return float(rule[4:]) * norm_L
+    return None
+
+
+# --------------------------------------------------------------------------------------------- references
+
+def reference_eigs(ref, k):
+    """Exact or oracle eigenvalues the results are compared with: closed forms for grids (the
+    Laplacian of a Cartesian product is the Kronecker sum of path Laplacians, whose spectrum is
+    2 - 2 cos(pi i / N)), or the FP64 oracle's stored values (tests/golden).  None if unknown."""
+    import numpy as np
+    if ref is None:
+        return None, None
+    kind, arg = ref.split(":", 1)
+    if kind in ("grid2d", "grid3d"):
+        dims = [int(x) for x in arg.split(",")]
+        out = np.zeros(1)
+        for N in dims:
+            out = (out[:, None] + (2.0 - 2.0 * np.cos(np.pi * np.arange(N) / N))[None, :]).ravel()
+        return np.sort(out)[1:k + 1], "closed form (Kronecker sum of path spectra)"
+    if kind == "golden":
+        path = os.path.join(ROOT, "tests", "golden", arg)
+        if not os.path.exists(path):
+            return None, None
+        g = json.load(open(path))
+        lam = np.sort(np.array(g["eigvals"]))
+        if lam.shape[0] < k:
+            return None, None
+        return lam[:k], f"FP64 oracle, eps_rel {g['eps_rel']:g} (tests/golden/{arg})"
+    return None, None
+
+
+def rel_eig_err(lam, ref):
+    import numpy as np
+    lam = np.sort(np.asarray(lam, dtype=np.float64))
+    return float(np.max(np.abs(lam - ref) / np.abs(ref)))
+
+
+def workload_config(name, g, k, eps, norm_L):
     spec = WORKLOADS[name]
-    kind, t = spec["tol"]
-    return {"workload": f"{name} k={k} {spec['prec']}", "graph": spec["desc"], "n": g.n, "nnz": g.nnz,
-            "k": k, ("resid_rel" if kind == "rel" else "tol_abs"): t, "norm_L": "2*max_degree",
-            "l2": "flushed (512 MB write) between steps", "start_vector": "splitmix64 seed 1, centred, unit norm"}
+    return {"workload": f"{name} k={k} {spec['prec']}", "graph": spec["desc"], "n": g.n, "nnz": g.nnz, "k": k,
+            "eps_abs": eps, "resid_rel_bound": eps / norm_L, "norm_L": "2*max_degree", "norm_L_value": norm_L,
+            "tol_rule": spec["tol"], "l2": "flushed (512 MB write) between steps",
+            "start_vector": "splitmix64 seed 1, centred, unit norm"}
 
 
 def config_with_opts(cfg, args):
@@ -202,30 +280,38 @@ def _isnum(s):
 
 # --------------------------------------------------------------------------------------------- roofline
 
-def phase1_bytes(n, Z, c_avg, word):
-    """Algorithmic DRAM bytes of one launch of the phase-1 gather kernel (the dominant kernel):
-    row_ptr 8(n+1), col_idx 4Z, the gathered vector once (word*n) and the per-row sums written
-    (word*n).  c_avg is unused: the deflation terms live in the row-epilogue kernel."""
-    return 8 * (n + 1) + 4 * Z + 2 * word * n
+def kernel_bytes(kind, n, Z, c, word, n_long=None, n_slices=None):
+    """Algorithmic DRAM bytes of one launch of an inner-iteration kernel (word = 4 FP32, 8 FP64):
+      gather  : column indices 4Z, the gathered vector once (w n), the row sums (w n), and the row
+                structure: row_ptr 8(n+1) for CSR rows, or with the sliced light rows 8(n_long+1)
+                for the long rows plus 8(n_slices+1) slice offsets;
+      rows    : degrees 4n; reads of the row sums, z_k, z_{k-1}, two w buffers and x (6 w n), the
+                c columns of Vh (c w n); writes of Y, the new w and x (3 w n); FP64 adds the
+                reciprocal preconditioner diagonal (8 n);
+      phase2  : degrees 4n; reads of Y, z_k (2 w n) and Vh (c w n); write of z_{k+1} (w n); FP64
+                adds 8 n.
+    c is the launch's deflation rank (averaged over the timed launches)."""
+    extra = 8 * n if word == 8 else 0
+    if kind == "gather":
+        struct = 8 * (n + 1) if not n_slices else 8 * (n_long + 1) + 8 * (n_slices + 1)
+        return struct + 4 * Z + 2 * word * n
+    if kind == "rows":
+        return 4 * n + (9 + c) * word * n + extra
+    if kind == "phase2":
+        return 4 * n + (3 + c) * word * n + extra
+    raise KeyError(kind)
 
 
-def phase1_fp64_ops(n, Z, c_avg):
-    """FP64 lane operations of one FP64 gather launch: one add per stored entry."""
-    return Z
-
-
-def fp64_peak_ops(sm_max_mhz):
-    """FP64 lane operations per second: 152 SMs x 2 lanes per clock (the FP64 pipe issues one warp
-    instruction per 16 cycles per SM on this part; 1.25 TFLOP/s nominal counts an FMA as 2) x clock."""
-    mhz = sm_max_mhz or 2070.0
-    return 152 * 2 * mhz * 1e6
-
+KERNEL_NAMES = {"gather": "k_phase1_gather (trimmed-operator SpMV gather)",
+                "rows": "k_phase1 (operator row epilogue + MINRES update)",
+                "phase2": "k_phase2 (SMW preconditioner + MINRES reductions)"}
+STAT_OF = {"gather": "inner_phase1_ms", "rows": "inner_rows_ms", "phase2": "inner_phase2_ms"}
 
 GATHER_SOURCES = ["paper_1710_07080_gb300/csrc/common.cuh", "paper_1710_07080_gb300/csrc/inner_impl.cuh"]
 
 
 def source_hash(files=GATHER_SOURCES):
-    """Hash of the sources that define the gather kernel: a stored ncu traffic figure applies only
+    """Hash of the sources that define the inner kernels: a stored ncu traffic figure applies only
     while they are unchanged."""
     h = hashlib.sha256()
     for f in files:
@@ -234,8 +320,8 @@ def source_hash(files=GATHER_SOURCES):
 
 
 def ncu_traffic(kernel_key):
-    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -260,43 +346,90 @@ def hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def kernel_rooflines(st, n, Z, word, workload, prec_tag):
+    """Per-kernel achieved GB/s from one profiled solve's CUDA-event totals, and the dominant one."""
+    peak, peak_src = hbm_peak()
+    nl = st["inner_phase1_timed"]
+    c_avg = st["inner_phase1_csum"] / max(1, nl)
+    n_slices = (n - st["n_long_rows"] + 31) // 32 if st.get("sell_entries") else None
+    out = {}
+    for kind in ("gather", "rows", "phase2"):
+        ms = st[STAT_OF[kind]]
+        avg_s = ms / 1e3 / max(1, nl)
+        b = kernel_bytes(kind, n, Z, c_avg, word, st["n_long_rows"], n_slices)
+        ach = b / avg_s / 1e9 if avg_s > 0 else None
+        out[kind] = {"kernel": KERNEL_NAMES[kind], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak if ach else None, "bytes_per_launch": b, "avg_us": avg_s * 1e6,
+                     "launches_timed": nl, "total_ms": ms, "avg_deflation_rank": c_avg,
+                     "traffic": ncu_traffic(f"{kind}_{prec_tag}_{workload}")}
+    dom = max(out, key=lambda q: out[q]["total_ms"])
+    tot = sum(v["total_ms"] for v in out.values())
+    for v in out.values():
+        v["share_of_inner_kernels"] = v["total_ms"] / tot if tot > 0 else None
+    return out, dom, peak_src
+
+
 # --------------------------------------------------------------------------------------------- oracle leg
 
-def oracle_sample(g, k, tol_abs, u0, max_outer):
+def oracle_counts(workload):
+    """Unit counts of the FP64 oracle's own full run at the accuracy tolerance (tests/golden,
+    written by tests/golden/make_golden.py, which calls only oracle/)."""
+    name = {"grid128^3": "grid128_c4.json", "rmat20": "rmat20_c4.json"}.get(workload)
+    if name is None:
+        return None, None
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        return None, None
+    g = json.load(open(path))
+    return g["oracle_stats"], {"file": f"tests/golden/{name}", "eps_abs": g.get("eps_abs"),
+                               "oracle_seconds_on_build_host": g.get("oracle_seconds")}
+
+
+SAMPLE_CAPS = {"grid128^3": (2, 150), "rmat20": (3, 5000), "grid100x100": (100000, 20000),
+               "rgg4M": (1, 60), "rmat24": (1, 20)}
+
+
+def oracle_sample(g, k, eps, u0, workload):
+    """Runs the oracle on the workload with outer steps and inner iterations capped (a bounded
+    sample); returns its wall seconds and its stats (per-phase seconds and unit counts)."""
     import oracle
+    max_outer, max_inner = SAMPLE_CAPS.get(workload, (2, 100))
     t0 = time.perf_counter()
-    lam, V, st = oracle.isira(g.row_ptr, g.col_idx, k, u0, eps=tol_abs, tau_inner=1e-3, max_outer=max_outer)
+    _, _, st = oracle.isira(g.row_ptr, g.col_idx, k, u0, eps=eps, tau_inner=1e-3, max_outer=max_outer,
+                            max_inner=max_inner)
     return time.perf_counter() - t0, st
 
 
-def oracle_full_counts(name):
-    """Work counts of the oracle's full run on this workload (written by tests/golden/make_golden.py)."""
-    path = os.path.join(ROOT, "tests", "golden", f"{name}_bench.json")
-    if os.path.exists(path):
-        return json.load(open(path))["oracle_stats"]
-    return None
-
-
-def project_oracle(st_sample, full):
-    """Seconds of the oracle's full run, projected from a sample's per-unit costs: seconds per
-    recomputed W column (the W_k, H_k step of Algorithm 2), per inner MINRES iteration (its inner solve) and per outer step (the
-    rest), times the full run's counts of those units."""
+def project(st_sample, counts):
+    """Seconds of a full run from the sample's per-unit costs: seconds per recomputed W column (the
+    W_k, H_k step of Algorithm 2), per inner MINRES iteration (its inner solve) and per outer step
+    (the rest), times the full run's counts of those units."""
     per_col = st_sample["sec_w"] / max(1, st_sample["w_columns"])
     per_it = st_sample["sec_inner"] / max(1, st_sample["inner_iters"])
     rest = st_sample["sec_total"] - st_sample["sec_w"] - st_sample["sec_inner"]
     per_step = rest / max(1, st_sample["outer_steps"])
-    return per_col * full["w_columns"] + per_it * full["inner_iters"] + per_step * full["outer_steps"]
+    return per_col * counts["w_columns"] + per_it * counts["inner_iters"] + per_step * counts["outer_steps"]
 
 
-SAMPLE_STEPS = 6
+def host_cpu():
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
 
 
-def sample_text(st, full):
-    return (f"first {st['outer_steps']} outer steps of Algorithm 2 (FP64 oracle, tau_inner 1e-3, 1 thread) on the "
-            f"same graph: {st['sec_w'] / max(1, st['w_columns']) * 1e3:.1f} ms per recomputed W column, "
-            f"{st['sec_inner'] / max(1, st['inner_iters']) * 1e3:.1f} ms per inner iteration; projected with the "
-            f"unit counts of the oracle's full run ({full['w_columns']} W columns, {full['inner_iters']} inner "
-            f"iterations, {full['outer_steps']} outer steps; tests/golden)")
+def sample_text(st, counts, src):
+    return (f"Algorithm 2 by the FP64 oracle (tau_inner 1e-3, 1 thread) on the same graph at the same eps, "
+            f"capped at {st['outer_steps']} outer steps and {st['inner_iters']} inner iterations (measured "
+            f"{st['sec_total']:.1f} s: {st['sec_inner'] / max(1, st['inner_iters']) * 1e3:.2f} ms per inner "
+            f"iteration, {st['sec_w'] / max(1, st['w_columns']) * 1e3:.2f} ms per recomputed W column); scaled to "
+            f"one full solve with the unit counts {counts['inner_iters']} inner iterations, {counts['w_columns']} W "
+            f"columns, {counts['outer_steps']} outer steps ({src})")
 
 
 def run_reference(args):
@@ -304,32 +437,39 @@ def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    if args.workload not in ("rmat20",):
-        print(json.dumps({"impl": "reference", "unavailable": "oracle work counts exist only for rmat20"}))
+    spec = WORKLOADS.get(args.workload)
+    if spec is None or args.workload == "batch256":
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle leg for workload {args.workload}"}))
         return
-    spec = WORKLOADS[args.workload]
+    counts, src = oracle_counts(args.workload)
+    if counts is None:
+        print(json.dumps({"impl": "reference",
+                          "unavailable": f"no stored oracle unit counts for {args.workload} (tests/golden)"}))
+        return
     k = args.k if args.k > 0 else spec["k"]
     g = load_workload(args)
-    normL = 2.0 * float(g.degrees.max())
-    tol = (args.rel_tol if args.rel_tol > 0 else spec["tol"][1]) * normL
+    norm_L = 2.0 * float(g.degrees.max())
+    eps = args.eps if args.eps > 0 else (src["eps_abs"] or fixed_eps(spec["tol"], norm_L))
     u0 = sg.start_vector(g.n, 1)
-    full = oracle_full_counts(args.workload)
-    if full is None:
-        print(json.dumps({"impl": "reference", "unavailable": "no oracle work counts for this workload"}))
-        return
-    values, st = [], None
+    values, walls, st = [], [], None
+    t_all = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        _, st = oracle_sample(g, k, tol, u0, SAMPLE_STEPS)
+        dt, st = oracle_sample(g, k, eps, u0, args.workload)
         if i >= args.warmup:
-            values.append(project_oracle(st, full))
+            values.append(project(st, counts))
+            walls.append(dt)
     value = statistics.mean(values)
+    cpu = host_cpu()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.workload, g, k, tol / normL),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(walls) * 1e3,
+            "ms_per_step_is": "measured wall time of one bounded oracle sample (the timed region is steps x this); "
+                              "value is that sample scaled to one full solve",
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, g, k, eps, norm_L),
             "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": sample_text(st, full)},
-            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                             "sample": sample_text(st, counts, src["file"]), "host": cpu},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s_total": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
 
 
@@ -337,7 +477,6 @@ def run_reference(args):
 
 def run_batch(args):
     """256 graphs of uneven size solved together through isira_batch_* (one step = the whole batch)."""
-    import numpy as np
     import torch
 
     import paper_1710_07080_gb300 as isira
@@ -347,7 +486,7 @@ def run_batch(args):
     dev = torch.device("cuda", local)
     spec = WORKLOADS["batch256"]
     k = args.k if args.k > 0 else spec["k"]
-    rel = args.rel_tol if args.rel_tol > 0 else spec["tol"][1]
+    rel = float(spec["tol"][4:])
     import torch.distributed as tdist
     dist = tdist if (world > 1 and tdist.is_initialized()) else None
     all_graphs = sg.batch_family(256, 1000, 200000, seed=1)
@@ -420,46 +559,66 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
+    stages = {}
+    t_stage = time.perf_counter()
     spec = WORKLOADS[args.workload]
     g = load_workload(args)
+    stages["graph_build_s"] = time.perf_counter() - t_stage
     n, Z = g.n, g.nnz
     k = args.k if args.k > 0 else spec["k"]
-    normL = 2.0 * float(g.degrees.max())
-    kind, tv = spec["tol"]
-    tol = (args.rel_tol if args.rel_tol > 0 else tv) * normL if kind == "rel" else tv
-    rel_for_cfg = tol / normL
-    if args.single_solve:
-        prec = isira.ISIRA_FP64 if args.single_solve == "fp64" else isira.ISIRA_MIXED
-        with isira.Solver(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev),
-                          precision=prec, **solver_opts(args)) as s:
-            s.solve(k, tol=tol, u0=torch.from_numpy(sg.start_vector(n, 1)).to(dev))
-            torch.cuda.synchronize()
-            print(json.dumps({"single_solve": args.single_solve, **s.stats()}), flush=True)
-        return
+    norm_L = 2.0 * float(g.degrees.max())
+    head = spec["prec"]
+    other = "fp64" if head == "mixed" else "mixed"
+    P = {"fp64": isira.ISIRA_FP64, "mixed": isira.ISIRA_MIXED}
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()
     ci_h = torch.from_numpy(g.col_idx).pin_memory()
     u0_h = torch.from_numpy(sg.start_vector(n, 1)).pin_memory()
     rp = rp_h.to(dev)
     ci = ci_h.to(dev)
     u0 = u0_h.to(dev)
+    if args.single_solve:
+        eps = args.eps if args.eps > 0 else (fixed_eps(spec["tol"], norm_L) or RESID_REL * norm_L)
+        with isira.Solver(rp, ci, precision=P[args.single_solve], **solver_opts(args)) as s:
+            s.solve(k, tol=eps, u0=u0)
+            torch.cuda.synchronize()
+            print(json.dumps({"single_solve": args.single_solve, "eps": eps, **s.stats()}), flush=True)
+        return
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    uuid = str(torch.cuda.get_device_properties(dev).uuid) if hasattr(torch.cuda.get_device_properties(dev), "uuid") else ""
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(props.uuid) if hasattr(props, "uuid") else ""
 
-    def timed_solves(solver, profile):
-        for _ in range(args.warmup):
-            solver.solve(k, tol=tol, u0=u0)
+    t_stage = time.perf_counter()
+    solvers = {p: isira.Solver(rp, ci, precision=P[p], **solver_opts(args)) for p in (head, other)}
+    torch.cuda.synchronize()
+    stages["create_both_s"] = time.perf_counter() - t_stage
+
+    # tolerance (untimed): the workload's fixed rule, or the accuracy rule from one loose solve's Ritz values
+    t_stage = time.perf_counter()
+    eps = args.eps if args.eps > 0 else fixed_eps(spec["tol"], norm_L)
+    calib = None
+    if eps is None:
+        solvers[head].solve(k, tol=RESID_REL * norm_L, u0=u0)
+        lam_loose = solvers[head].eigpairs(want_vectors=False, want_resid=False)[0].numpy()
+        eps = accuracy_eps(lam_loose, norm_L)
+        calib = {"loose_eps_abs": RESID_REL * norm_L, "loose_eigvals": [float(x) for x in lam_loose],
+                 "rule": "min(1e-8 ||L||, sqrt(1e-10 lambda_j gap_j)), clusters merged at 1e-6 relative"}
+    stages["calibration_s"] = time.perf_counter() - t_stage
+
+    def timed(solver, warm, steps, profile=False):
+        for _ in range(warm):
+            solver.solve(k, tol=eps, u0=u0)
         torch.cuda.synchronize()
         solver.set_profiling(profile)
         times, stats = [], []
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.zero_()
             barrier()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            solver.solve(k, tol=tol, u0=u0)
+            solver.solve(k, tol=eps, u0=u0)
             e1.record(stream)
             torch.cuda.synchronize()
             barrier()
@@ -469,121 +628,117 @@ def main():
         return times, stats
 
     clk = ClockSampler(uuid.replace("GPU-", "") if uuid else "")
-    s64 = isira.Solver(rp, ci, precision=isira.ISIRA_FP64, **solver_opts(args))
-    smx = isira.Solver(rp, ci, precision=isira.ISIRA_MIXED, **solver_opts(args))
     clk.start()
-    # headline: the default device-driven inner loop (one CUDA-graph launch per inner solve)
-    t64, st64 = timed_solves(s64, False)
-    tmx, stmx = timed_solves(smx, False)
-    # kernel timing: the same solves with CUDA events around every phase-1 launch (chunked launches)
-    tp64, sp64 = timed_solves(s64, True)
-    tpmx, spmx = timed_solves(smx, True)
+    t_stage = time.perf_counter()
+    t_head, st_head = timed(solvers[head], args.warmup, args.steps)
+    stages["timed_headline_s"] = time.perf_counter() - t_stage
     clocks = clk.stop()
-    lam64, vec64, res64 = s64.eigpairs()
-    lammx, vecmx, resmx = smx.eigpairs()
+    t_stage = time.perf_counter()
+    t_oth, st_oth = timed(solvers[other], 1, max(1, min(args.steps, args.cmp_steps)))
+    stages["timed_other_precision_s"] = time.perf_counter() - t_stage
+    # kernel timing: one solve per precision with CUDA events around every inner launch (chunked launches)
+    t_stage = time.perf_counter()
+    prof = {p: timed(solvers[p], 0, 1, profile=True) for p in (head, other)}
+    stages["profiled_solves_s"] = time.perf_counter() - t_stage
 
-    # accuracy of the benchmarked solves against a tight FP64 solve (untimed)
-    ref = isira.solve(rp, ci, k, tol=1e-12 * normL, u0=u0, precision=isira.ISIRA_FP64, **solver_opts(args))
-    lam_ref = ref.eigvals.numpy()
+    # accuracy of the benchmarked solves against the closed form or the FP64 oracle (untimed)
+    ref, ref_src = reference_eigs(spec["ref"], k)
+    acc = {"reference": ref_src}
+    for p in (head, other):
+        lam, vec, res = solvers[p].eigpairs()
+        acc[f"max_true_resid_rel_{p}"] = float(res.max())
+        acc[f"n_locked_{p}"] = int(lam.numel())
+        if ref is not None and lam.numel() == k:
+            acc[f"max_rel_eig_err_{p}"] = rel_eig_err(lam.numpy(), ref)
+        acc[f"eigvals_{p}"] = [float(x) for x in lam]
+    acc["bars"] = {"max_rel_eig_err": 1e-9, "max_true_resid_rel": RESID_REL}
 
-    def relerr(a):
-        return float(np.max(np.abs(a.numpy() - lam_ref) / np.abs(lam_ref)))
-
-    # end to end through the public API, in the precision the configuration names:
-    # pinned host CSR -> device, create, solve, eigenpairs -> host
+    # end to end through the public API, in the headline precision:
+    # pinned host CSR -> device, create (with autotuning), solve, eigenpairs -> host
+    t_stage = time.perf_counter()
     e2e_times = []
     h2d = rp_h.numel() * 8 + ci_h.numel() * 4 + u0_h.numel() * 8
     d2h = n * k * 8 + k * 8 * 2
-    for i in range(args.warmup + args.steps):
+    e2e_n = max(1, min(args.steps, args.e2e_steps))
+    for i in range(1 + e2e_n):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rp_d = rp_h.to(dev, non_blocking=True)
         ci_d = ci_h.to(dev, non_blocking=True)
         u0_d = u0_h.to(dev, non_blocking=True)
-        e2e_prec = isira.ISIRA_MIXED if spec["prec"] == "mixed" else isira.ISIRA_FP64
-        with isira.Solver(rp_d, ci_d, precision=e2e_prec, **solver_opts(args)) as s:
-            s.solve(k, tol=tol, u0=u0_d)
+        with isira.Solver(rp_d, ci_d, precision=P[head], **solver_opts(args)) as s:
+            s.solve(k, tol=eps, u0=u0_d)
             lam_e, vec_e, res_e = s.eigpairs()
             vec_host = vec_e.cpu()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if i >= args.warmup:
+        if i >= 1:
             e2e_times.append(dt)
     del vec_host
+    stages["e2e_s"] = time.perf_counter() - t_stage
 
-    value = reduce_max(statistics.mean(t64))
-    value_mx = reduce_max(statistics.mean(tmx))
+    value = reduce_max(statistics.mean(t_head))
+    value_oth = reduce_max(statistics.mean(t_oth))
     e2e = reduce_max(statistics.mean(e2e_times))
+    word = {"fp64": 8, "mixed": 4}
+    kern = {}
+    for p in (head, other):
+        kern[p] = kernel_rooflines(prof[p][1][0], n, Z, word[p], args.workload, "f32" if p == "mixed" else "f64")
+    rk, dom, peak_src = kern[head]
+    roof = dict(rk[dom])
+    roof.update(peak_source=peak_src, dominant_of="inner-iteration kernels (gather, rows, phase2), by total time",
+                other_kernels={q: {kk: v[kk] for kk in ("kernel", "achieved", "frac", "avg_us", "share_of_inner_kernels")}
+                               for q, v in rk.items() if q != dom})
+    ro, dom_o, _ = kern[other]
 
-    # roofline of the dominant kernel (phase 1 of the FP64 inner solve), from the live events
-    p1_ms = sum(s["inner_phase1_ms"] for s in sp64)
-    p1_n = sum(s["inner_phase1_timed"] for s in sp64)
-    p1_c = sum(s["inner_phase1_csum"] for s in sp64) / max(1, p1_n)
-    avg_s = p1_ms / 1e3 / max(1, p1_n)
-    bytes_launch = phase1_bytes(n, Z, p1_c, 8)
-    peak, peak_src = hbm_peak()
-    achieved = bytes_launch / avg_s / 1e9 if avg_s > 0 else None
-    p1mx_ms = sum(s["inner_phase1_ms"] for s in spmx)
-    p1mx_n = sum(s["inner_phase1_timed"] for s in spmx)
-    p1mx_c = sum(s["inner_phase1_csum"] for s in spmx) / max(1, p1mx_n)
-    avgmx_s = p1mx_ms / 1e3 / max(1, p1mx_n)
-    achieved_mx = phase1_bytes(n, Z, p1mx_c, 4) / avgmx_s / 1e9 if avgmx_s > 0 else None
-    traffic = ncu_traffic(f"phase1_fp64_{args.workload}")
-    ops_peak = fp64_peak_ops(clocks.get("sm_max_mhz"))
-    ops_achieved = phase1_fp64_ops(n, Z, p1_c) / avg_s if avg_s > 0 else None
+    def summary(p, times, stats):
+        s = stats[-1]
+        return {"value": statistics.mean(times), "unit": "s", "steps": len(times),
+                "dtype": "f64" if p == "fp64" else "f32 inner / f64 outer", "outer_steps": s["outer_steps"],
+                "inner_iters": s["inner_iters"], "inner_solves": s["inner_solves"], "restarts": s["restarts"],
+                "w_columns": s["w_columns"], "spmv_lanes": s["spmv_lanes"], "gather_block": s["gather_block"],
+                "hub_bytes": s["hub_bytes"], "sell_entries": s["sell_entries"], "n_long_rows": s["n_long_rows"],
+                "profiled_solve_s": prof[p][0][0]}
 
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": config_with_opts(workload_config(args.workload, g, k, rel_for_cfg), args),
-        "mixed": {"value": value_mx, "unit": "s", "dtype": "f32 inner / f64 outer",
-                  "speedup_vs_fp64": value / value_mx if value_mx else None,
-                  "roofline": {"kernel": "k_phase1_gather<float>", "bound": "hbm", "achieved": achieved_mx, "peak": peak,
-                               "unit": "GB/s", "frac": (achieved_mx / peak) if achieved_mx else None,
-                               "bytes_per_launch": phase1_bytes(n, Z, p1mx_c, 4), "avg_deflation_rank": p1mx_c},
-                  "outer_steps": stmx[-1]["outer_steps"], "inner_iters": stmx[-1]["inner_iters"],
-                  "phase1_avg_us": avgmx_s * 1e6, "phase1_GBps": achieved_mx},
-        "fp64": {"outer_steps": st64[-1]["outer_steps"], "inner_iters": st64[-1]["inner_iters"],
-                 "restarts": st64[-1]["restarts"], "spmv_lanes": st64[-1]["spmv_lanes"],
-                 "phase1_avg_us": avg_s * 1e6, "phase1_launches_timed": p1_n,
-                 "timed_with_events_s": statistics.mean(tp64)},
-        "accuracy": {"max_rel_eig_err_fp64_vs_tight": relerr(lam64), "max_rel_eig_err_mixed_vs_tight": relerr(lammx),
-                     "max_true_resid_rel_fp64": float(res64.max()), "max_true_resid_rel_mixed": float(resmx.max()),
-                     "tight_tol_rel": 1e-12, "eigvals": [float(x) for x in lam_ref]},
-        "roofline": {"kernel": "k_phase1_gather<double> (trimmed operator SpMV gather)", "bound": "alu",
-                     "achieved": ops_achieved / 1e9 if ops_achieved else None, "peak": ops_peak / 1e9,
-                     "unit": "G FP64 lane-ops/s", "frac": (ops_achieved / ops_peak) if ops_achieved else None,
-                     "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x max SM clock (1.25 TFLOP/s nominal)",
-                     "ops_per_launch": phase1_fp64_ops(n, Z, p1_c), "hbm_achieved_GBps": achieved,
-                     "hbm_frac": (achieved / peak) if achieved else None, "hbm_peak": peak, "hbm_peak_source": peak_src,
-                     "bytes_per_launch": bytes_launch, "avg_deflation_rank": p1_c, "traffic": traffic},
-        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "path": "pinned host CSR -> isira_create -> isira_solve -> isira_eigpairs -> host"},
-        "gpu_launches": int(sum(s["kernel_launches"] for s in (stmx if spec["prec"] == "mixed" else st64))),
+        "dtype": "f64" if head == "fp64" else "f32 inner / f64 outer", "data": "synthetic",
+        "config": config_with_opts(workload_config(args.workload, g, k, eps, norm_L), args),
+        head: summary(head, t_head, st_head),
+        other: {**summary(other, t_oth, st_oth), "roofline": {**ro[dom_o], "dominant": dom_o}},
+        "mixed_speedup_vs_fp64": (value_oth / value) if head == "mixed" else (value / value_oth),
+        "accuracy": acc,
+        "roofline": roof,
+        "kernels": {p: {q: {kk: v[kk] for kk in ("achieved", "frac", "avg_us", "bytes_per_launch", "total_ms",
+                                                  "share_of_inner_kernels")} for q, v in kern[p][0].items()}
+                    for p in (head, other)},
+        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_n,
+                "path": "pinned host CSR -> isira_create (autotune) -> isira_solve -> isira_eigpairs -> host"},
+        "gpu_launches": int(sum(s["kernel_launches"] for s in st_head)),
         "clocks": clocks,
+        "stages": stages,
     }
-    if spec["prec"] == "mixed":
-        # the configuration names the mixed form: it is the headline, FP64 is reported beside it
-        fp64_part = {"value": line["value"], "unit": "s", "dtype": "f64", "roofline": line["roofline"],
-                     **line["fp64"]}
-        mixed = line.pop("mixed")
-        mroof = mixed.pop("roofline")
-        line.update(value=mixed["value"], ms_per_step=mixed["value"] * 1e3, dtype="f32 inner / f64 outer",
-                    roofline={**mroof, "peak_source": peak_src, "hbm_frac": mroof["frac"],
-                              "traffic": ncu_traffic(f"phase1_f32_{args.workload}")})
-        line["fp64"] = fp64_part
-        line["mixed"] = mixed
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "rmat20":
-        full = oracle_full_counts(args.workload)
-        dt, st = oracle_sample(g, k, tol, u0_h.numpy(), SAMPLE_STEPS)
-        if full is not None:
-            line["cpu_baseline"] = {"value": project_oracle(st, full), "unit": "s", "cores": 1, "kind": "oracle",
-                                    "sample": sample_text(st, full), "sample_seconds": dt}
+    if calib is not None:
+        line["config"]["calibration"] = calib
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in SAMPLE_CAPS:
+        t_stage = time.perf_counter()
+        counts, src = oracle_counts(args.workload)
+        if counts is None:
+            s64 = st_head[-1] if head == "fp64" else st_oth[-1]
+            counts = {"inner_iters": s64["inner_iters"], "w_columns": s64["w_columns"],
+                      "outer_steps": s64["outer_steps"]}
+            src = {"file": "unit counts of the GPU FP64 solve of this run (same algorithm, same eps)"}
+        dt, st = oracle_sample(g, k, eps, u0_h.numpy(), args.workload)
+        line["cpu_baseline"] = {"value": project(st, counts), "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": sample_text(st, counts, src["file"]), "sample_seconds": dt,
+                                "host": host_cpu()}
+        stages["cpu_baseline_s"] = time.perf_counter() - t_stage
     if rank == 0:
         print(json.dumps(line), flush=True)
-    s64.close()
-    smx.close()
+    for s in solvers.values():
+        s.close()
     if dist is not None:
         dist.destroy_process_group()
 

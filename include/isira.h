@@ -51,7 +51,9 @@ typedef enum {
     ISIRA_ERR_CUDA = 5,            /* a CUDA runtime call failed */
     ISIRA_ERR_OOM = 6,             /* device or pinned allocation failed */
     ISIRA_ERR_NOT_SOLVED = 7,      /* eigpairs requested before a successful solve */
-    ISIRA_ERR_LIMIT = 8            /* request exceeds the fixed scratch of isira_apply_operator_noalloc */
+    ISIRA_ERR_LIMIT = 8,           /* request exceeds the fixed scratch of isira_apply_operator_noalloc */
+    ISIRA_ERR_DEVICE_TIMEOUT = 9   /* a bounded wait inside a kernel ran out; the call's results are not
+                                      valid (the device context stays usable) */
 } isira_status;
 
 enum { ISIRA_FP64 = 0,   /* inner solve in FP64 ("plain") */
@@ -83,17 +85,24 @@ typedef struct {
                              reuse in the SpMV; vectors at the API stay in the caller's numbering;
                              0: use the caller's numbering (default 1) */
     int gather_block;     /* threads per CTA of the SpMV gather kernels: 256 (as many CTAs per SM as
-                             registers and shared memory allow, at most 6) or 1024 (one CTA per
-                             SM); 0: 1024 with relabelling, else 256 */
+                             registers and shared memory allow, at most 8) or 1024 (one CTA per
+                             SM); 0: autotuned (timed at create on graphs with n >= 100000, cached
+                             per graph-statistics bucket; else 1024 with relabelling, 256 without) */
     int hub_kb;           /* with relabelling, each gather CTA copies the vector entries of the first
                              (highest-degree) vertices into this many KB of shared memory with one
-                             bulk asynchronous copy; 0: 192 (capped by the device), < 0: none */
+                             bulk asynchronous copy; 0: autotuned among 192 KB (1024-thread CTAs),
+                             48 KB (256-thread CTAs) and none; < 0: none */
     int gather_sched;     /* 0: gather warps take work units from a device counter as they finish
                              (balanced whatever the row costs); 1: a static partition by estimated
-                             cost.  Results are identical either way. */
+                             cost (CSR tiles only: ignored with sell = 1).  Results are identical
+                             either way. */
     int index_vec;        /* 1: with relabelling, read column indices in 128-bit chunks of the
                              solver's padded copy; 0: 32-bit loads (default) */
     int gather_chunk;     /* work units a gather warp takes at a time (1..32); 0: 2 */
+    int sell;             /* 1 (default): with relabelling, the rows of degree <= 64 are gathered from a
+                             sliced ELL copy (slices of 32 rows, column-major, so every index load
+                             of a warp is one 128-byte line); 0: from CSR tiles with spmv_lanes
+                             lanes per row.  Sums differ only by rounding order. */
 } isira_opts;
 
 typedef struct {
@@ -118,8 +127,13 @@ typedef struct {
     long long kernel_launches;    /* kernels launched by the last isira_solve */
     int gather_block;             /* threads per gather CTA in use */
     int hub_bytes;                /* shared memory of a gather CTA holding hub vector entries */
-    long long hub_timeouts;       /* gather CTAs whose staging copy missed its wait limit (they then
-                                     read every entry from global memory; results unchanged) */
+    long long hub_timeouts;       /* gather CTAs whose staging copy missed its wait limit (the call
+                                     that saw one returned ISIRA_ERR_DEVICE_TIMEOUT) */
+    double inner_rows_ms;         /* summed device time of the phase-1 row kernels (profiling on only) */
+    double inner_phase2_ms;       /* summed device time of the phase-2 kernels (profiling on only) */
+    long long w_columns;          /* sum over outer steps of the search-space size k: the columns of
+                                     W_k = (L + delta V V^T) U_k that Algorithm 2 as printed recomputes */
+    long long sell_entries;       /* stored entries (with padding) of the sliced ELL copy (0: none) */
 } isira_stats;
 
 /* Fills *opts with the defaults listed above (precision = ISIRA_MIXED). */

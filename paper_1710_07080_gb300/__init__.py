@@ -24,6 +24,7 @@ ISIRA_ERR_CUDA = 5
 ISIRA_ERR_OOM = 6
 ISIRA_ERR_NOT_SOLVED = 7
 ISIRA_ERR_LIMIT = 8
+ISIRA_ERR_DEVICE_TIMEOUT = 9
 
 ISIRA_FP64 = 0
 ISIRA_MIXED = 1
@@ -41,7 +42,7 @@ class isira_opts(C.Structure):
                 ("sigma_omega", C.c_double), ("drop_rank1", C.c_int), ("validate", C.c_int), ("seed", C.c_uint64),
                 ("spmv_lanes", C.c_int), ("inner_chunk", C.c_int), ("inner_graph", C.c_int),
                 ("reorder", C.c_int), ("gather_block", C.c_int), ("hub_kb", C.c_int),
-                ("gather_sched", C.c_int), ("index_vec", C.c_int), ("gather_chunk", C.c_int)]
+                ("gather_sched", C.c_int), ("index_vec", C.c_int), ("gather_chunk", C.c_int), ("sell", C.c_int)]
 
 
 class isira_stats(C.Structure):
@@ -52,7 +53,9 @@ class isira_stats(C.Structure):
                 ("inner_iters", C.c_longlong), ("inner_solves", C.c_longlong), ("spmv_launches", C.c_longlong),
                 ("solve_ms", C.c_double), ("inner_phase1_ms", C.c_double), ("inner_phase1_timed", C.c_longlong),
                 ("inner_phase1_csum", C.c_longlong), ("kernel_launches", C.c_longlong),
-                ("gather_block", C.c_int), ("hub_bytes", C.c_int), ("hub_timeouts", C.c_longlong)]
+                ("gather_block", C.c_int), ("hub_bytes", C.c_int), ("hub_timeouts", C.c_longlong),
+                ("inner_rows_ms", C.c_double), ("inner_phase2_ms", C.c_double), ("w_columns", C.c_longlong),
+                ("sell_entries", C.c_longlong)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -132,6 +135,73 @@ def _ptr(t) -> int | None:
     return None if t is None else t.data_ptr()
 
 
+# ------------------------------------------------------------------ argument checks
+# Every tensor handed to the library is checked here first (dtype, shape, layout, then device):
+# the C entry points take raw pointers and cannot tell a float32 buffer from a float64 one.
+
+def _check_tensor(t, name: str, dtypes: tuple, shape: tuple, cuda: bool = True):
+    """Raises ValueError unless t has one of `dtypes`, exactly `shape` (None = any extent in that
+    dimension), is contiguous and (with cuda) lives on a CUDA device."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch.Tensor")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name} must have dtype {' or '.join(str(d) for d in dtypes)}, not {t.dtype}")
+    if t.dim() != len(shape) or any(want is not None and got != want for got, want in zip(t.shape, shape)):
+        raise ValueError(f"{name} must have shape {tuple('*' if w is None else w for w in shape)}, "
+                         f"not {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if cuda:
+        _check_cuda(**{name: t})
+
+
+def _check_cuda(**tensors):
+    """Raises ValueError unless every given tensor (None skipped) is on one and the same CUDA device."""
+    dev = None
+    for name, t in tensors.items():
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if dev is not None and t.device != dev:
+            raise ValueError(f"{name} must be on the same device as the other arguments")
+        dev = t.device
+
+
+def _check_csr(row_ptr, col_idx, cuda: bool = True):
+    import torch
+    _check_tensor(row_ptr, "row_ptr", (torch.int64,), (None,), cuda=False)
+    _check_tensor(col_idx, "col_idx", (torch.int32,), (None,), cuda=False)
+    if row_ptr.numel() < 2:
+        raise ValueError("row_ptr must have n + 1 >= 2 entries")
+    if cuda:
+        _check_cuda(row_ptr=row_ptr, col_idx=col_idx)
+
+
+def _check_x(x, n: int, name: str = "x", cuda: bool = True):
+    """An operator input: float32 (ISIRA_MIXED) or float64 (ISIRA_FP64) n-vector; returns the precision."""
+    import torch
+    _check_tensor(x, name, (torch.float32, torch.float64), (n,), cuda=cuda)
+    return ISIRA_MIXED if x.dtype == torch.float32 else ISIRA_FP64
+
+
+def _check_y(y, x, name: str = "y", cuda: bool = True):
+    _check_tensor(y, name, (x.dtype,), (x.numel(),), cuda=cuda)
+
+
+def _check_V(V, n: int, cmax: int = 31, cuda: bool = True):
+    """Deflation vectors: float64 n-by-c with c <= cmax (None = no deflation)."""
+    import torch
+    if V is None:
+        return 0
+    _check_tensor(V.contiguous() if isinstance(V, torch.Tensor) else V, "V", (torch.float64,), (n, None),
+                  cuda=cuda)
+    if V.shape[1] > cmax:
+        raise ValueError(f"V may have at most {cmax} columns, not {V.shape[1]}")
+    return int(V.shape[1])
+
+
 def _stream_ptr(stream=None) -> int | None:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -151,13 +221,9 @@ class Solver:
     """Owns an isira handle for one graph (CSR on the GPU, kept alive by this object)."""
 
     def __init__(self, row_ptr, col_idx, stream=None, **opts):
-        import torch
-        if row_ptr.dtype != torch.int64 or col_idx.dtype != torch.int32:
-            raise TypeError("row_ptr must be int64 and col_idx int32")
-        if not (row_ptr.is_cuda and col_idx.is_cuda):
-            raise TypeError("the CSR arrays must be CUDA tensors")
-        self.row_ptr = row_ptr.contiguous()
-        self.col_idx = col_idx.contiguous()
+        _check_csr(row_ptr, col_idx)
+        self.row_ptr = row_ptr
+        self.col_idx = col_idx
         self.n = self.row_ptr.numel() - 1
         self.nnz = self.col_idx.numel()
         self.opts = default_opts(**opts)
@@ -198,6 +264,9 @@ class Solver:
         """Algorithm 2.  tol: absolute bound on ||r||_2 (the paper's epsilon); default rel_tol * 2 max degree."""
         if tol is None:
             tol = rel_tol * self.stats()["norm_L"]
+        if u0 is not None:
+            import torch
+            _check_tensor(u0, "u0", (torch.float64,), (self.n,))
         st = lib.isira_solve(self.h, int(k), float(sigma), float(tol), _ptr(u0))
         self._last_status = st
         if raise_on_error and st not in (ISIRA_OK,):
@@ -222,23 +291,25 @@ class Solver:
     def apply_operator(self, x, sigma: float = 0.0, V=None):
         """y = trimmed, shifted, deflated operator (Eq. 2.14) applied in n-space."""
         import torch
-        prec = ISIRA_MIXED if x.dtype == torch.float32 else ISIRA_FP64
+        prec = _check_x(x, self.n)
+        c = _check_V(V, self.n)
         y = torch.empty_like(x)
-        c = 0 if V is None else V.shape[1]
         Vc = None if V is None else V.t().contiguous()   # column-major n-by-c
-        check(lib.isira_apply_operator(self.h, prec, float(sigma), c, _ptr(Vc), _ptr(x.contiguous()), _ptr(y)),
+        check(lib.isira_apply_operator(self.h, prec, float(sigma), c, _ptr(Vc), _ptr(x), _ptr(y)),
               "isira_apply_operator")
         return y
 
     def inner_solve(self, r, sigma: float = 0.0, V=None, tau: float = 1e-3, max_it: int = 5000,
                     precision: int = ISIRA_MIXED):
         import torch
-        z = torch.empty_like(r, dtype=torch.float64)
-        c = 0 if V is None else V.shape[1]
+        _check_tensor(r, "r", (torch.float64,), (self.n,), cuda=False)
+        c = _check_V(V, self.n, cuda=False)
+        _check_cuda(r=r, V=V, row_ptr=self.row_ptr)
+        z = torch.empty_like(r)
         Vc = None if V is None else V.t().contiguous()
         its = C.c_int(0)
         rel = C.c_double(0.0)
-        check(lib.isira_inner_solve(self.h, precision, float(sigma), c, _ptr(Vc), _ptr(r.contiguous()), float(tau),
+        check(lib.isira_inner_solve(self.h, precision, float(sigma), c, _ptr(Vc), _ptr(r), float(tau),
                                     int(max_it), _ptr(z), C.byref(its), C.byref(rel)), "isira_inner_solve")
         return z, its.value, rel.value
 
@@ -246,6 +317,9 @@ class Solver:
 def sym_eig(H):
     """All eigenpairs of a symmetric k-by-k CUDA float64 matrix on the GPU (k <= 64)."""
     import torch
+    if not isinstance(H, torch.Tensor) or H.dim() != 2 or H.shape[0] != H.shape[1] or not 1 <= H.shape[0] <= 64:
+        raise ValueError("H must be a square matrix of order 1..64")
+    _check_tensor(H.contiguous(), "H", (torch.float64,), (H.shape[0], H.shape[0]))   # includes the device
     k = H.shape[0]
     Hc = H.t().contiguous()          # column-major
     th = torch.empty(k, dtype=torch.float64, device=H.device)
@@ -259,10 +333,15 @@ def apply_operator_noalloc(row_ptr, col_idx, x, trim: int, sigma: float = 0.0, d
     """Handle-free operator apply that allocates no device memory inside the library (see
     isira_apply_operator_noalloc in include/isira.h).  Pass y to avoid the output allocation here too."""
     import torch
-    prec = ISIRA_MIXED if x.dtype == torch.float32 else ISIRA_FP64
+    _check_csr(row_ptr, col_idx, cuda=False)
+    n = row_ptr.numel() - 1
+    prec = _check_x(x, n, cuda=False)
+    c = _check_V(V, n, cuda=False)          # the scratch limit (c <= 8) is the library's to report
+    if y is not None:
+        _check_y(y, x, cuda=False)
+    _check_cuda(row_ptr=row_ptr, col_idx=col_idx, x=x, y=y, V=V)
     if y is None:
         y = torch.empty_like(x)
-    c = 0 if V is None else V.shape[1]
     Vc = None if V is None else V.t().contiguous()
     check(lib.isira_apply_operator_noalloc(row_ptr.numel() - 1, col_idx.numel(), _ptr(row_ptr), _ptr(col_idx),
                                            int(trim), prec, float(sigma), float(delta), int(bool(drop_rank1)), c,
@@ -278,7 +357,9 @@ class Batch:
     def __init__(self, graphs, **opts):
         """graphs: list of (row_ptr int64 CUDA tensor, col_idx int32 CUDA tensor)."""
         import numpy as np
-        self.graphs = [(rp.contiguous(), ci.contiguous()) for rp, ci in graphs]
+        for rp, ci in graphs:
+            _check_csr(rp, ci)
+        self.graphs = list(graphs)
         G = len(self.graphs)
         self.n = [rp.numel() - 1 for rp, _ in self.graphs]
         n = np.array(self.n, dtype=np.int64)

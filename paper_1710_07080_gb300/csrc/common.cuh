@@ -35,7 +35,8 @@ struct HostStatus {
     int inner_done;
     int inner_iters;
     int eig_sweeps;        // Jacobi sweeps used (-1: not converged)
-    int pad;
+    int dev_error;         // bit 0: a gather CTA's staging copy missed its wait limit (set by the
+                           // device, cleared by the host at the start of each entry point)
 };
 
 // ------------------------------------------------------------------ reductions
@@ -196,7 +197,19 @@ struct RowSched {
     unsigned* sched;                        // [next unit, warps finished], zero between launches
     int chunk;                              // units per take (1..32)
     unsigned* hub_timeouts;                 // CTAs whose staging copy missed the wait limit
+    int* err;                               // device alias of HostStatus::dev_error (may be null)
+    // sliced ELL copy of the light rows (see build_sell): with sell = 1 the rows [light0, n) are
+    // gathered from sell_ci in slices of 32 rows instead of CSR tiles, and rows below light0 are
+    // exactly the long rows (the degree-descending numbering puts them first)
+    const int32_t* __restrict__ sell_ci;
+    const int64_t* __restrict__ sell_off;   // n_slices + 1 offsets (multiples of 32)
+    int64_t light0;
+    int n_slices;
+    int sell;
     __host__ __device__ int grid() const { return n_warps / (tpb / 32); }
+    __host__ __device__ int n_units() const {
+        return n_items + (sell ? n_slices : (int)((n + 31) / 32));
+    }
 };
 
 constexpr int kBigBlock = 1024;             // one gather CTA per SM holding a large hub block
@@ -242,13 +255,14 @@ __device__ __forceinline__ T gather_x(const T* __restrict__ x, const T* sx, int 
 extern __shared__ __align__(128) unsigned char g_dyn_smem[];
 
 constexpr int kHubWaitPolls = 1 << 20;      // x ~64 ns: a bound far above the copy's microseconds
+constexpr int kHubDrainPolls = 1 << 24;     // second bound, for a copy still in flight after a timeout
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
-    for (int i = 0; i < kHubWaitPolls; ++i) {
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, int polls) {
+    for (int i = 0; i < polls; ++i) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -262,9 +276,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
 
 // Copies x[0:hub) into shared memory with one bulk asynchronous copy (the tensor memory
 // accelerator) that an mbarrier tracks; returns the number of staged entries (a multiple of
-// 16 bytes).  Should the copy not land within the wait limit, the CTA waits once more for the
-// copy in flight, counts the event and gathers everything from global memory (hub 0), which
-// gives the same sums.
+// 16 bytes).  Should the copy not land within the wait limit, the CTA counts the event, sets
+// bit 0 of the host-visible error word (the solve then fails with a device-timeout status),
+// waits once more, with a longer but still finite limit, for the copy in flight, so that it
+// does not leave while the copy can still write its shared memory, and returns -1: the CTA then
+// gathers nothing.
 template <typename T>
 __device__ __forceinline__ int stage_hub(const RowSched& S, const T* __restrict__ x, T* sx) {
     constexpr int kUnit = 16 / (int)sizeof(T);
@@ -290,10 +306,13 @@ __device__ __forceinline__ int stage_hub(const RowSched& S, const T* __restrict_
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                      :: "r"(smem_u32(sx)), "l"(x), "r"(bytes), "r"(bar_a) : "memory");
     }
-    if (__syncthreads_and(mbar_wait_bounded(bar_a, 0))) return hub;
-    const bool landed = __syncthreads_and(mbar_wait_bounded(bar_a, 0));
-    if (threadIdx.x == 0) atomicAdd(S.hub_timeouts, 1u);
-    return landed ? hub : 0;
+    if (__syncthreads_and(mbar_wait_bounded(bar_a, 0, kHubWaitPolls))) return hub;
+    if (threadIdx.x == 0) {
+        atomicAdd(S.hub_timeouts, 1u);
+        if (S.err) atomicOr_system(S.err, 1);
+    }
+    (void)__syncthreads_and(mbar_wait_bounded(bar_a, 0, kHubDrainPolls));
+    return -1;
 }
 
 // Partial sum over the stored entries [beg, end) of ci taken by sub-lane j of a group of W lanes.
@@ -391,6 +410,22 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
     T* sx = reinterpret_cast<T*>(g_dyn_smem);
     const int hub = stage_hub<T>(S, x, sx);
     const int lane = threadIdx.x & 31;
+    // dynamic distribution: every warp reports once that it has finished taking units; the last
+    // one resets the counters for the next launch
+    auto finish_dyn = [&]() {
+        if (lane == 0) {
+            const unsigned n_warps = gridDim.x * (blockDim.x >> 5);
+            __threadfence();
+            if (atomicAdd(S.sched + 1, 1u) == n_warps - 1) {
+                S.sched[0] = 0u;
+                S.sched[1] = 0u;
+            }
+        }
+    };
+    if (hub < 0) {                      // staging timed out (reported): this CTA takes no units
+        if (S.dyn) finish_dyn();
+        return;
+    }
     // long rows: finished rows are collected one per lane and their epilogues run 32 at a time,
     // so the epilogue arithmetic uses every lane of the warp
     T* part = static_cast<T*>(S.item_partial);
@@ -494,19 +529,56 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
         }
         if (light) epi(row, deg, mine);
     };
+    // sliced light rows: one lane per row, two slices at a time so that each lane keeps eight index
+    // loads (four per row) in flight; a lane adds its row's entries in slice order
+    auto do_slices = [&](int s0, int s1) {
+        for (int sa = s0; sa < s1; sa += 2) {
+            const bool two = sa + 1 < s1;
+            const int64_t ra = S.light0 + (int64_t)sa * 32 + lane;
+            const int64_t rb = ra + 32;
+            const int64_t oa = S.sell_off[sa], ea = S.sell_off[sa + 1];
+            const int64_t ob = two ? ea : 0, eb = two ? S.sell_off[sa + 2] : 0;
+            const int wa = (int)((ea - oa) >> 5), wb = (int)((eb - ob) >> 5);
+            const int w = wa > wb ? wa : wb;
+            T s_a = 0, s_b = 0;
+            for (int q = 0; q < w; q += 4) {
+                int32_t ia[4], ib[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ia[u] = q + u < wa ? __ldcs(S.sell_ci + oa + (int64_t)(q + u) * 32 + lane) : -1;
+                    ib[u] = q + u < wb ? __ldcs(S.sell_ci + ob + (int64_t)(q + u) * 32 + lane) : -1;
+                }
+                T va[4], vb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    va[u] = ia[u] >= 0 ? gather_x(x, sx, hub, ia[u]) : T(0);
+                    vb[u] = ib[u] >= 0 ? gather_x(x, sx, hub, ib[u]) : T(0);
+                }
+                s_a += (va[0] + va[1]) + (va[2] + va[3]);
+                s_b += (vb[0] + vb[1]) + (vb[2] + vb[3]);
+            }
+            if (ra < S.n) epi(ra, 0, ra == skip ? T(0) : s_a);
+            if (two && rb < S.n) epi(rb, 0, rb == skip ? T(0) : s_b);
+        }
+    };
     auto do_range = [&](int u0, int u1) {             // u1 - u0 <= 32
         if (u0 < S.n_items) load_headers(u0, u1);
         for (int u = u0; u < u1;) {
             if (u + 1 < u1 && u + 1 < S.n_items) {
                 do_item_pair(u, u - u0);
                 u += 2;
+            } else if (u >= S.n_items && S.sell) {
+                do_slices(u - S.n_items, u1 - S.n_items);
+                break;
             } else {
                 if (u < S.n_items) do_item(u, u - u0); else do_tile(u - S.n_items);
                 u += 1;
             }
         }
     };
-    const int n_units = S.n_items + (int)((S.n + 31) / 32);
+    // a trimmed long row is skipped by its items; with slices no tile writes its zero sum
+    if (S.sell && skip >= 0 && skip < S.light0 && blockIdx.x == 0 && threadIdx.x == 0) epi(skip, 0, T(0));
+    const int n_units = S.n_units();
     if (S.dyn) {
         // dynamic: warps take chunks of S.chunk units from a counter; the last warp to finish
         // resets it for the next launch.  Which warp takes a unit never changes its sum.
@@ -517,14 +589,7 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
             if (u0 >= n_units) break;             // the failing take precedes the fence below
             do_range(u0, u0 + S.chunk < n_units ? u0 + S.chunk : n_units);
         }
-        if (lane == 0) {
-            const unsigned n_warps = gridDim.x * (blockDim.x >> 5);
-            __threadfence();
-            if (atomicAdd(S.sched + 1, 1u) == n_warps - 1) {
-                S.sched[0] = 0u;
-                S.sched[1] = 0u;
-            }
-        }
+        finish_dyn();
     } else {
         const int gw = blockIdx.x * (int)(blockDim.x >> 5) + (threadIdx.x >> 5);
         const int u_beg = S.warp_start[gw], u_end = S.warp_start[gw + 1];

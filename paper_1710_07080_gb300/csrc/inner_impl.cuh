@@ -45,54 +45,59 @@ __device__ __forceinline__ T* wbuf(const InnerArgs<T>& a, int j) {
     return r == 0 ? a.wb0 : (r == 1 ? a.wb1 : a.wb2);
 }
 
+// ------------------------------------------------------------------ vector access
+// The row kernels move VN = 16 / sizeof(T) consecutive rows per thread with 16-byte loads and
+// stores.  Every n-vector has ld >= n rows (ld a multiple of 32), so a vector access never leaves
+// its buffer; rows >= n and the trimmed row are masked with selects (padding may hold anything).
+template <typename T> struct Vec;
+template <> struct Vec<float> { static constexpr int N = 4; using V = float4; using I = int4; };
+template <> struct Vec<double> { static constexpr int N = 2; using V = double2; using I = int2; };
+
+template <typename T>
+__device__ __forceinline__ void vld(const T* __restrict__ p, T (&v)[Vec<T>::N]) {
+    const typename Vec<T>::V q = __ldg(reinterpret_cast<const typename Vec<T>::V*>(p));
+    if constexpr (Vec<T>::N == 4) { v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w; }
+    else { v[0] = q.x; v[1] = q.y; }
+}
+
+// plain (coherent) load for buffers the kernel also writes
+template <typename T>
+__device__ __forceinline__ void vld_rw(const T* p, T (&v)[Vec<T>::N]) {
+    const typename Vec<T>::V q = *reinterpret_cast<const typename Vec<T>::V*>(p);
+    if constexpr (Vec<T>::N == 4) { v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w; }
+    else { v[0] = q.x; v[1] = q.y; }
+}
+
+template <typename T>
+__device__ __forceinline__ void vst(T* p, const T (&v)[Vec<T>::N]) {
+    typename Vec<T>::V q;
+    if constexpr (Vec<T>::N == 4) { q.x = v[0]; q.y = v[1]; q.z = v[2]; q.w = v[3]; }
+    else { q.x = v[0]; q.y = v[1]; }
+    *reinterpret_cast<typename Vec<T>::V*>(p) = q;
+}
+
+template <typename T>
+__device__ __forceinline__ void vld_deg(const int32_t* __restrict__ p, int (&v)[Vec<T>::N]) {
+    const typename Vec<T>::I q = __ldg(reinterpret_cast<const typename Vec<T>::I*>(p));
+    if constexpr (Vec<T>::N == 4) { v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w; }
+    else { v[0] = q.x; v[1] = q.y; }
+}
+
+// deflation columns the per-thread accumulators of a bucket hold: c <= kCMax - 1 in every solve
+template <int NC>
+struct Ncols { static constexpr int value = NC < kCMax ? NC : kCMax - 1; };
+
 // ------------------------------------------------------------------ phase 1
-
-template <typename T, int NC>
-struct Phase1Epi {
-    int64_t trim, ldv;
-    T sigma;
-    int c;
-    const T* Vt;
-    const T* dinv;
-    T* Y; T* x;
-    const T* zc; const T* zp; const T* wo2; const T* wo1; T* wn;
-    T inv_beta, cprev, inv_oldb, s_term, oldeps, dlt, inv_gamma, phi;
-    int has_prev;
-    const T* u1s;          // shared memory, c entries
-    T acc[1 + NC];
-
-    __device__ __forceinline__ void operator()(int64_t r, int64_t deg, T gsum) {
-        if (r == trim) {
-            Y[r] = T(0);
-            if (has_prev) wn[r] = T(0);
-            return;
-        }
-        const T degT = (T)deg;
-        const T zr = zc[r];
-        const T D = precond_diag(degT, sigma);
-        T vdot = 0;
-#pragma unroll
-        for (int t = 0; t < NC; ++t)
-            if (t < c) vdot += Vt[(int64_t)t * ldv + r] * u1s[t];
-        T y1 = ((degT - sigma) * zr - gsum + s_term) * inv_beta + vdot;
-        if (has_prev) {
-            const T zpr = zp[r];
-            y1 -= cprev * D * zpr;
-            // deferred update of iteration k-1: w_{k-1} and x
-            const T v = zpr * inv_oldb;
-            const T w = (v - oldeps * wo2[r] - dlt * wo1[r]) * inv_gamma;
-            wn[r] = w;
-            x[r] += phi * w;
-        }
-        Y[r] = y1;
-        acc[0] += zr * inv_beta * y1;
-        if (NC == 0) return;
-        const T yd = y1 * inv_diag(dinv, r, D);
-#pragma unroll
-        for (int t = 0; t < NC; ++t)   // second read of the row of Vh: an L1 hit
-            if (t < c) acc[1 + t] += Vt[(int64_t)t * ldv + r] * yd;
-    }
-};
+// Row epilogue of the operator from the gathered neighbour sums, one pass over the rows:
+//   y'_r = ((deg_r - sigma) z_r - g_r + (sigma/n) s) / beta_k - (beta_k / beta_{k-1}) D_r zp_r   (r != trim)
+// i.e. Mh v_k - (beta_k/beta_{k-1}) P z_{k-1} without their deflation parts, which phase 2 adds
+// as Vh u1 (so phase 1 reads each Vh entry once and uses it at once).  Also the deferred w/x
+// update of iteration k-1, and the reductions
+//   alpha' = v_k^T y',   a_t = (Vh^T D^{-1} y')_t,   g_t = (Vh^T z_k)_t.
+// The last CTA turns them into u1 = delta (g / beta_k - (beta_k / beta_{k-1}) g_prev),
+// alpha_k = alpha' + (g / beta_k)^T u1, and phase 2's SMW coefficient
+//   tv = C^{-1} Vh^T D^{-1} y,  Vh^T D^{-1} y = a + G u1 - (alpha_k / beta_k)(g + delta G g),
+// with G = Vh^T D^{-1} Vh (so Vh^T D^{-1} (Vh u1) needs no pass over Vh).
 
 // Gather of phase 1: g_r = sum_{c in N(r)} z_k[c] (the trimmed row gathers nothing).  Only this
 // kernel walks the CSR; it keeps few registers so many warps keep loads in flight.
@@ -106,80 +111,142 @@ __global__ void __launch_bounds__(TPB, TPB == kThreads ? 4 : 1) k_phase1_gather(
     for_each_row_gather<T, G>(a.rs, zc, epi, a.trim);
 }
 
-// Row epilogue of phase 1, one thread per row (coalesced): the operator value from the gathered
-// sum, the Lanczos update, the deferred w/x update, and the reductions alpha_k, Vh^T D^{-1} y1.
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
+    constexpr int VN = Vec<T>::N;
+    constexpr int NE = Ncols<NC>::value;
+    constexpr int NA = 1 + 2 * NE;
     InnerState<T>* st = a.st;
     if (st->done) return;
     const int k = st->itn + 1;
     const int c = st->p_c;
-    __shared__ T u1s[NC > 0 ? NC : 1];
-    __shared__ T red[1 + NC];
-    Phase1Epi<T, NC> epi;
-    epi.trim = a.trim;
-    epi.ldv = a.ldv;
-    epi.sigma = st->p_sigma;
-    epi.c = c;
-    epi.Vt = a.Vt;
-    epi.dinv = a.dinv;
-    epi.Y = a.Y;
-    epi.x = a.x;
-    epi.zc = ((k - 1) & 1) ? a.z1 : a.z0;
-    epi.zp = (k & 1) ? a.z1 : a.z0;
+    const T sigma = st->p_sigma;
+    const T* __restrict__ zc = ((k - 1) & 1) ? a.z1 : a.z0;
+    const T* __restrict__ zp = (k & 1) ? a.z1 : a.z0;
     const T beta = st->beta, oldb = st->oldb;
-    epi.inv_beta = T(1) / beta;
-    epi.has_prev = k >= 2;
-    epi.cprev = epi.has_prev ? beta / oldb : T(0);
-    epi.inv_oldb = epi.has_prev ? T(1) / oldb : T(0);
-    epi.s_term = st->p_sig_n * st->s_cur;
+    const T inv_beta = T(1) / beta;
+    const bool has_prev = k >= 2;
+    const T cprev = has_prev ? beta / oldb : T(0);
+    const T inv_oldb = has_prev ? T(1) / oldb : T(0);
+    const T s_term = st->p_sig_n * st->s_cur;
     const int j = k - 1;                    // iteration whose w/x update is deferred to here
-    epi.wo2 = wbuf(a, j + 1);               // w_{j-2}
-    epi.wo1 = wbuf(a, j + 2);               // w_{j-1}
-    epi.wn = wbuf(a, j);                    // w_j
-    epi.oldeps = st->w_oldeps;
-    epi.dlt = st->w_dlt;
-    epi.inv_gamma = st->w_inv_gamma;
-    epi.phi = st->w_phi;
-    for (int t = threadIdx.x; t < c; t += blockDim.x) u1s[t] = st->u1[t];
-    epi.u1s = u1s;
+    const T* __restrict__ wo2 = wbuf(a, j + 1);   // w_{j-2}
+    const T* __restrict__ wo1 = wbuf(a, j + 2);   // w_{j-1}
+    T* __restrict__ wn = wbuf(a, j);              // w_j
+    const T oldeps = st->w_oldeps, dlt = st->w_dlt, inv_gamma = st->w_inv_gamma, phi = st->w_phi;
+    T acc[NA];
 #pragma unroll
-    for (int t = 0; t < 1 + NC; ++t) epi.acc[t] = T(0);
-    __syncthreads();
-
-    const int64_t n = a.rs.n;
-    const int64_t* __restrict__ rp = a.rs.rp;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-        epi(r, rp[r + 1] - rp[r], a.gsum[r]);
-
-    if (block_partials_arrive<T, 1 + NC>(epi.acc, 1 + c, a.partial, a.pstride, a.counter)) {
-        last_block_sum(a.partial, a.pstride, gridDim.x, 1 + c, red, a.counter);
-        // alpha_k and the SMW coefficient of phase 2:
-        //   Vh^T D^{-1} y = h1 - (alpha/beta) (g + delta G g),  tv = C^{-1} (that)
-        __shared__ double rhs[kCMax];
-        const T alpha = red[0];
-        const double coef = (double)alpha / (double)beta;
+    for (int t = 0; t < NA; ++t) acc[t] = T(0);
+    const int64_t n = a.rs.n, trim = a.trim;
+    const T* __restrict__ Vt = a.Vt;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
+    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
+        T g[VN], z[VN], y[VN], yd[VN];
+        int dg[VN];
+        bool ok[VN];
+        vld(a.gsum + r0, g);
+        vld(zc + r0, z);
+        vld_deg<T>(a.deg + r0, dg);
+        T dinv[VN];
+        if (a.dinv) vld(a.dinv + r0, dinv);
+        T zpv[VN], w2[VN], w1[VN], xv[VN], wv[VN];
+        if (has_prev) {
+            vld(zp + r0, zpv);
+            vld(wo2 + r0, w2);
+            vld(wo1 + r0, w1);
+            vld_rw(a.x + r0, xv);
+        }
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+            const int64_t r = r0 + e;
+            ok[e] = r < n && r != trim;
+            const T degT = (T)dg[e];
+            const T D = precond_diag(degT, sigma);
+            const T di = a.dinv ? dinv[e] : T(1) / D;
+            T base = ((degT - sigma) * z[e] - g[e] + s_term) * inv_beta;
+            if (has_prev) {
+                base -= cprev * D * zpv[e];
+                const T w = (zpv[e] * inv_oldb - oldeps * w2[e] - dlt * w1[e]) * inv_gamma;
+                wv[e] = ok[e] ? w : T(0);
+                xv[e] += ok[e] ? phi * w : T(0);
+            }
+            y[e] = ok[e] ? base : T(0);
+            yd[e] = ok[e] ? base * di : T(0);           // padding rows may have D = 0
+            z[e] = ok[e] ? z[e] : T(0);
+            acc[0] += z[e] * inv_beta * y[e];
+        }
+        vst(a.Y + r0, y);
+        if (has_prev) {
+            vst(wn + r0, wv);
+            vst(a.x + r0, xv);
+        }
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {
+            if (t < c) {
+                T v[VN];
+                vld(Vt + (int64_t)t * a.ldv + r0, v);
+#pragma unroll
+                for (int e = 0; e < VN; ++e) {
+                    const T vm = ok[e] ? v[e] : T(0);
+                    acc[1 + t] += vm * yd[e];
+                    acc[1 + NE + t] += vm * z[e];
+                }
+            }
+        }
+    }
+    __shared__ T red[NA];
+    if (block_partials_arrive<T, NA>(acc, NE > 0 ? NA : 1, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, NE > 0 ? NA : 1, red, a.counter);
+        __shared__ double u1d[kCMax], gcd[kCMax], rhs[kCMax];
+        __shared__ double alpha_s;
+        const double delta = (double)a.delta;
+        const double cp = (double)cprev, bt = (double)beta;
         for (int t = threadIdx.x; t < c; t += blockDim.x) {
-            double gg = 0.0;
-            for (int s = 0; s < c; ++s) gg += a.Gm[t + s * c] * (double)st->g_cur[s];
-            rhs[t] = (double)red[1 + t] - coef * ((double)st->g_cur[t] + (double)a.delta * gg);
+            const double gp = has_prev ? (double)st->g_cur[t] : 0.0;
+            const double gn = (double)red[1 + NE + t];
+            gcd[t] = gn;
+            u1d[t] = delta * (gn / bt - cp * gp);
+            st->g_prev[t] = (T)gp;
+            st->g_cur[t] = (T)gn;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double al = (double)red[0];
+            for (int t = 0; t < c; ++t) al += gcd[t] / bt * u1d[t];
+            alpha_s = al;
+            st->alpha = (T)al;
+        }
+        __syncthreads();
+        const double coef = alpha_s / bt;
+        for (int t = threadIdx.x; t < c; t += blockDim.x) {
+            double gu = 0.0, gg = 0.0;
+            for (int q = 0; q < c; ++q) {
+                gu += a.Gm[t + q * c] * u1d[q];
+                gg += a.Gm[t + q * c] * gcd[q];
+            }
+            rhs[t] = (double)red[1 + t] + gu - coef * (gcd[t] + delta * gg);
         }
         __syncthreads();
         for (int t = threadIdx.x; t < c; t += blockDim.x) {
             double tv = 0.0;
-            for (int s = 0; s < c; ++s) tv += a.Cinv[t + s * c] * rhs[s];
+            for (int q = 0; q < c; ++q) tv += a.Cinv[t + q * c] * rhs[q];
             st->tv[t] = (T)tv;
-            st->qv[t] = (T)(coef * (double)a.delta * (double)st->g_cur[t]);
+            st->qv[t] = (T)(coef * delta * gcd[t]);
+            st->u1[t] = (T)u1d[t];
         }
-        if (threadIdx.x == 0) st->alpha = alpha;
     }
 }
 
 // ------------------------------------------------------------------ phase 2
-
+// y = y' - (alpha_k / beta_k) D z_k + Vh (u1 - qv)        (the Lanczos vector, qv = coef delta g)
+// z_{k+1} = D^{-1} (y - Vh tv)                           (the SMW preconditioner, Eq. 3.6)
+// and the reductions y^T z_{k+1} (= beta_{k+1}^2) and 1^T z_{k+1}.  Each Vh entry is read once and
+// feeds both combinations.  The last CTA runs the Givens step and the stopping test.
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, cudaGraphConditionalHandle cond,
                                                      int has_cond) {
+    constexpr int VN = Vec<T>::N;
+    constexpr int NE = Ncols<NC>::value;
     InnerState<T>* st = a.st;
     if (!init && st->done) {
         // nothing left to do: make sure a surrounding WHILE node stops
@@ -189,52 +256,64 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, c
     const int k = init ? 0 : st->itn + 1;
     const int c = st->p_c;
     const T sigma = st->p_sigma;
-    const T* zc = ((k - 1) & 1) ? a.z1 : a.z0;
-    T* zn = (k & 1) ? a.z1 : a.z0;
+    const T* __restrict__ zc = ((k - 1) & 1) ? a.z1 : a.z0;
+    T* __restrict__ zn = (k & 1) ? a.z1 : a.z0;
     const T coef = init ? T(0) : st->alpha / st->beta;
-    __shared__ T qvs[NC > 0 ? NC : 1], tvs[NC > 0 ? NC : 1];
-    __shared__ T red[2 + NC];
-    // y = Y - coef D z_k - Vh qv and z = D^{-1}(y - Vh tv) need only Vh (qv + tv) per row;
-    // y^T z = z^T D z + tv^T (Vh^T z) (since y = D z + Vh tv) is finished by the last block
+    __shared__ T as_[NE > 0 ? NE : 1], ts_[NE > 0 ? NE : 1];
+    __shared__ T red[2];
     for (int t = threadIdx.x; t < c; t += blockDim.x) {
-        tvs[t] = st->tv[t];
-        qvs[t] = (init ? T(0) : st->qv[t]) + tvs[t];
+        ts_[t] = st->tv[t];
+        as_[t] = init ? T(0) : st->u1[t] - st->qv[t];
     }
     __syncthreads();
-    T acc[2 + NC];
+    T acc[2] = {T(0), T(0)};
+    const int64_t n = a.rs.n, trim = a.trim;
+    const T* __restrict__ Vt = a.Vt;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
+    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
+        T yv[VN], zcv[VN], ya[VN], zt[VN], dinv[VN];
+        int dg[VN];
+        vld(a.Y + r0, yv);
+        if (!init) vld(zc + r0, zcv);
+        vld_deg<T>(a.deg + r0, dg);
+        if (a.dinv) vld(a.dinv + r0, dinv);
 #pragma unroll
-    for (int t = 0; t < 2 + NC; ++t) acc[t] = T(0);
-    const int64_t n = a.rs.n;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        if (r == a.trim) {
-            zn[r] = T(0);
-            continue;
+        for (int e = 0; e < VN; ++e) { ya[e] = T(0); zt[e] = T(0); }
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {
+            if (t < c) {
+                T v[VN];
+                vld(Vt + (int64_t)t * a.ldv + r0, v);
+                const T ca = as_[t], ct = ts_[t];
+#pragma unroll
+                for (int e = 0; e < VN; ++e) {
+                    ya[e] += v[e] * ca;
+                    zt[e] += v[e] * ct;
+                }
+            }
         }
-        const T degT = (T)(a.rs.rp[r + 1] - a.rs.rp[r]);
-        const T D = precond_diag(degT, sigma);
-        T q = 0;
+        T zo[VN];
 #pragma unroll
-        for (int t = 0; t < NC; ++t)
-            if (t < c) q += a.Vt[(int64_t)t * a.ldv + r] * qvs[t];
-        T y = a.Y[r];
-        if (!init) y -= coef * D * zc[r];
-        const T z = (y - q) * inv_diag(a.dinv, r, D);
-        zn[r] = z;
-        acc[0] += D * z * z;
-        acc[1] += z;
-#pragma unroll
-        for (int t = 0; t < NC; ++t)   // second read of the row of Vh: an L1 hit
-            if (t < c) acc[2 + t] += a.Vt[(int64_t)t * a.ldv + r] * z;
+        for (int e = 0; e < VN; ++e) {
+            const int64_t r = r0 + e;
+            const bool ok = r < n && r != trim;
+            const T degT = (T)dg[e];
+            const T D = precond_diag(degT, sigma);
+            const T di = a.dinv ? dinv[e] : T(1) / D;
+            T y = yv[e] + ya[e];
+            if (!init) y -= coef * D * zcv[e];
+            const T z = (y - zt[e]) * di;
+            zo[e] = ok ? z : T(0);
+            acc[0] += ok ? y * z : T(0);
+            acc[1] += zo[e];
+        }
+        vst(zn + r0, zo);
     }
-    if (block_partials_arrive<T, 2 + NC>(acc, 2 + c, a.partial, a.pstride, a.counter)) {
-        last_block_sum(a.partial, a.pstride, gridDim.x, 2 + c, red, a.counter);
-        __shared__ T bnew_s, bold_s;
+    if (block_partials_arrive<T, 2>(acc, 2, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, 2, red, a.counter);
         if (threadIdx.x == 0) {
-            T bb = red[0];
-            for (int t = 0; t < c; ++t) bb += tvs[t] * red[2 + t];
+            const T bb = red[0];
             const T bnew = bb > T(0) ? sqrt(bb) : T(0);
-            bold_s = st->beta;
-            bnew_s = bnew;
             int done;
             if (init) {
                 st->beta1 = bnew;
@@ -284,20 +363,50 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, c
             a.hs->inner_iters = st->itn;
             a.hs->inner_relres = st->beta1 > T(0) ? (double)(st->phibar / st->beta1) : 0.0;
         }
-        __syncthreads();
-        // c-vectors for the next phase 1: g_prev <- g_cur, g_cur <- Vh^T z_{k+1},
-        // u1 = delta (g_cur / beta_{k+1} - (beta_{k+1} / beta_k) g_prev)
-        const T bnew = bnew_s, bold = bold_s;
-        for (int t = threadIdx.x; t < c; t += blockDim.x) {
-            const T gp = init ? T(0) : st->g_cur[t];
-            const T gn = red[2 + t];
-            st->g_prev[t] = gp;
-            st->g_cur[t] = gn;
-            if (bnew > T(0))
-                st->u1[t] = a.delta * (gn / bnew - (init ? T(0) : (bnew / bold) * gp));
-            else
-                st->u1[t] = T(0);
+    }
+}
+
+// ------------------------------------------------------------------ stand-alone operator apply
+// y_r = (deg_r - sigma) x_r - g_r + (sigma/n) 1^T x + delta (Vh (Vh^T x))_r for r != trim, y_trim = 0, with
+// x in z0, its gathered sums in gsum and 1^T x, delta Vh^T x left in s_cur, u1 by k_opstats.
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_apply_rows(InnerArgs<T> a) {
+    constexpr int VN = Vec<T>::N;
+    constexpr int NE = Ncols<NC>::value;
+    const InnerState<T>* st = a.st;
+    const int c = st->p_c;
+    const T sigma = st->p_sigma;
+    const T s_term = st->p_sig_n * st->s_cur;
+    __shared__ T u1s[NE > 0 ? NE : 1];
+    for (int t = threadIdx.x; t < c; t += blockDim.x) u1s[t] = st->u1[t];
+    __syncthreads();
+    const int64_t n = a.rs.n, trim = a.trim;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
+    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
+        T g[VN], z[VN], y[VN], vd[VN];
+        int dg[VN];
+        vld(a.gsum + r0, g);
+        vld(a.z0 + r0, z);
+        vld_deg<T>(a.deg + r0, dg);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) vd[e] = T(0);
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {
+            if (t < c) {
+                T v[VN];
+                vld(a.Vt + (int64_t)t * a.ldv + r0, v);
+#pragma unroll
+                for (int e = 0; e < VN; ++e) vd[e] += v[e] * u1s[t];
+            }
         }
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+            const int64_t r = r0 + e;
+            const T degT = (T)dg[e];
+            const T v = ((degT - sigma) * z[e] - g[e] + s_term) + vd[e];
+            y[e] = (r < n && r != trim) ? v : T(0);
+        }
+        vst(a.Y + r0, y);
     }
 }
 
@@ -613,15 +722,23 @@ cudaError_t inner_gather_attrs(int bytes) {
         if (e == cudaSuccess) e = wave_register((const void*)k_phase2<T, NC>);                          \
         if (e == cudaSuccess) e = wave_register((const void*)k_prep<T, NC>);                            \
         if (e == cudaSuccess) e = wave_register((const void*)k_opstats<T, NC>);                         \
+        if (e == cudaSuccess) e = wave_register((const void*)k_apply_rows<T, NC>);                      \
     } while (0)
     for (int nc : {0, 8, 12, 16, 24, 32}) ISIRA_NC_DISPATCH(nc, LW);
 #undef LW
     return e;
 }
 
+// grid of the vectorised row kernels: one thread per Vec<T>::N rows, at most ew_blocks CTAs
+template <typename T>
+inline int vec_blocks(const InnerArgs<T>& a) {
+    const int64_t want = (a.rs.n + (int64_t)kThreads * Vec<T>::N - 1) / ((int64_t)kThreads * Vec<T>::N);
+    return (int)(want < a.ew_blocks ? (want > 0 ? want : 1) : a.ew_blocks);
+}
+
 template <typename T>
 void inner_rows(const InnerArgs<T>& a, cudaStream_t s) {
-#define L1(NC) k_phase1<T, NC><<<wave_grid((const void*)k_phase1<T, NC>, a.ew_blocks), kThreads, 0, s>>>(a)
+#define L1(NC) k_phase1<T, NC><<<wave_grid((const void*)k_phase1<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a)
     ISIRA_NC_DISPATCH(a.c, L1);
 #undef L1
 }
@@ -633,15 +750,23 @@ void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s) {
 }
 
 template <typename T>
+void inner_apply(const InnerArgs<T>& a, int lanes, cudaStream_t s) {
+    inner_gather<T>(a, lanes, s);
+#define LA(NC) k_apply_rows<T, NC><<<wave_grid((const void*)k_apply_rows<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a)
+    ISIRA_NC_DISPATCH(a.c, LA);
+#undef LA
+}
+
+template <typename T>
 void inner_phase2(const InnerArgs<T>& a, int init, cudaStream_t s) {
-#define L2(NC) k_phase2<T, NC><<<wave_grid((const void*)k_phase2<T, NC>, a.ew_blocks), kThreads, 0, s>>>(a, init, 0, 0)
+#define L2(NC) k_phase2<T, NC><<<wave_grid((const void*)k_phase2<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a, init, 0, 0)
     ISIRA_NC_DISPATCH(a.c, L2);
 #undef L2
 }
 
 template <typename T>
 void inner_phase2_cond(const InnerArgs<T>& a, cudaGraphConditionalHandle cond, cudaStream_t s) {
-#define L2C(NC) k_phase2<T, NC><<<wave_grid((const void*)k_phase2<T, NC>, a.ew_blocks), kThreads, 0, s>>>(a, 0, cond, 1)
+#define L2C(NC) k_phase2<T, NC><<<wave_grid((const void*)k_phase2<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a, 0, cond, 1)
     ISIRA_NC_DISPATCH(a.c, L2C);
 #undef L2C
 }
@@ -684,6 +809,7 @@ void copy_vcol(const double* src, T* dst, int64_t n, cudaStream_t s) {
 
 #define ISIRA_INSTANTIATE_INNER(T)                                                                        \
     template void inner_phase1<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
+    template void inner_apply<T>(const InnerArgs<T>&, int, cudaStream_t);                                \
     template void inner_gather<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
     template void inner_rows<T>(const InnerArgs<T>&, cudaStream_t);                                      \
     template void inner_phase2<T>(const InnerArgs<T>&, int, cudaStream_t);                               \

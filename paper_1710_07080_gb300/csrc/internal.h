@@ -41,6 +41,7 @@ struct InnerArgs {
     T* z0; T* z1; T* Y; T* wb0; T* wb1; T* wb2; T* x;
     T* dinv;                    // FP64 mode: 1/D per row, written by the prep kernel (nullptr: divide)
     T* gsum;                    // per-row neighbour sums written by the gather kernel
+    const int32_t* deg;         // degree per row (ld entries, zero padding)
     T* partial; int pstride;
     unsigned* counter;
     InnerState<T>* st;
@@ -56,6 +57,8 @@ template <typename T> void inner_prep_launch(const InnerArgs<T>& a, const double
                                              cudaStream_t s);
 template <typename T> void inner_phase1(const InnerArgs<T>& a, int lanes, cudaStream_t s);   // gather + rows
 template <typename T> void inner_gather(const InnerArgs<T>& a, int lanes, cudaStream_t s);
+// stand-alone operator apply: gather of z0, then Y = operator(z0) (after inner_opstats on z0)
+template <typename T> void inner_apply(const InnerArgs<T>& a, int lanes, cudaStream_t s);
 // every gather kernel of precision T may take up to `bytes` of dynamic shared memory
 template <typename T> cudaError_t inner_gather_attrs(int bytes);
 template <typename T> void inner_rows(const InnerArgs<T>& a, cudaStream_t s);
@@ -120,6 +123,8 @@ struct DegreeInfo { int64_t max_degree, argmax; int64_t n_long, n_items; };
 // Counts (and, when item_row is given and n_items <= cap, fills) the long-row work items.
 void setup_degrees(const int64_t* rp, int64_t n, int light_deg, int32_t* item_row, int32_t* item_k, int64_t cap,
                    int64_t* scratch, DegreeInfo* out, cudaStream_t s);
+// deg[r] = row_ptr[r+1] - row_ptr[r] for r < n, 0 for n <= r < ld
+void setup_deg32(const int64_t* rp, int64_t n, int64_t ld, int32_t* deg, cudaStream_t s);
 // Equal-cost ranges of work units (items, then light tiles) for n_warps warps.
 void setup_partition(const int64_t* rp, int64_t n, const int32_t* item_row, const int32_t* item_k, int64_t n_items,
                      int light_deg, int n_warps, int64_t* cost_tmp, int64_t* prefix_tmp, int32_t* warp_start,
@@ -127,6 +132,10 @@ void setup_partition(const int64_t* rp, int64_t n, const int32_t* item_row, cons
 // vertex relabelling by descending degree (reorder.cu)
 cudaError_t build_reordered_graph(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int64_t maxdeg,
                                   int64_t* rp2, int32_t* ci2, int32_t* perm, int32_t* inv, cudaStream_t s);
+// sliced ELL copy of the light rows [light0, n): off (n_slices + 1 entries, caller-allocated) receives
+// the slice offsets, *sci a new device array of *total entries (-1 padding)
+cudaError_t build_sell(const int64_t* rp, const int32_t* ci, int64_t n, int64_t light0, int64_t n_slices,
+                       int64_t* off, int32_t** sci, int64_t* total, cudaStream_t s);
 template <typename T> void to_internal(const T* src, const int32_t* perm, int64_t n, T* dst, cudaStream_t s);
 template <typename T> void to_external(const T* src, const int32_t* perm, int64_t n, T* dst, cudaStream_t s);
 int validate_csr(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int* d_flag, cudaStream_t s);

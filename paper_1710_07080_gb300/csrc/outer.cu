@@ -847,6 +847,17 @@ void setup_degrees(const int64_t* rp, int64_t n, int light_deg, int32_t* item_ro
         k_deg_fill<<<kSetupBlocks, kThreads, 0, s>>>(rp, n, chunk, light_deg, scratch, item_row, item_k);
 }
 
+// degree of every row as int32 (the row kernels read 4 bytes per row instead of two row pointers);
+// rows n .. ld-1 get 0
+__global__ void __launch_bounds__(kThreads) k_deg32(const int64_t* rp, int64_t n, int64_t ld, int32_t* deg) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < ld; r += (int64_t)gridDim.x * blockDim.x)
+        deg[r] = r < n ? (int32_t)(rp[r + 1] - rp[r]) : 0;
+}
+
+void setup_deg32(const int64_t* rp, int64_t n, int64_t ld, int32_t* deg, cudaStream_t s) {
+    k_deg32<<<1024, kThreads, 0, s>>>(rp, n, ld, deg);
+}
+
 // ------------------------------------------------------------------ balanced work partition
 
 __global__ void __launch_bounds__(kThreads) k_unit_cost(const int64_t* rp, int64_t n, const int32_t* item_row,

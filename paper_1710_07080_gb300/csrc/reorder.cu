@@ -90,6 +90,67 @@ done:
     return e;
 }
 
+// ------------------------------------------------------------------ sliced ELL copy of the light rows
+// Rows [light0, n) in slices of 32 consecutive rows.  Slice s has width w_s = the largest degree
+// among its rows; entry q of its lane l (row light0 + 32 s + l) sits at off[s] + 32 q + l, so a
+// warp reads one 128-byte line per q.  Rows shorter than w_s are padded with -1.  With the
+// degree-descending numbering the rows of a slice have nearly equal degrees (little padding).
+
+__global__ void __launch_bounds__(kThreads) k_sell_widths(const int64_t* rp, int64_t n, int64_t light0,
+                                                          int64_t n_slices, int64_t* w32) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n_slices;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        int64_t w = 0;
+        if (s < n_slices)
+            for (int64_t r = light0 + 32 * s; r < light0 + 32 * s + 32 && r < n; ++r) {
+                const int64_t d = rp[r + 1] - rp[r];
+                w = d > w ? d : w;
+            }
+        w32[s] = 32 * w;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sell_fill(const int64_t* rp, const int32_t* ci, int64_t n,
+                                                        int64_t light0, int64_t n_slices, const int64_t* off,
+                                                        int32_t* sci) {
+    const int64_t total = n_slices * 32;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = t >> 5, lane = t & 31;
+        const int64_t row = light0 + t;
+        const int64_t w = (off[s + 1] - off[s]) >> 5;
+        const int64_t b = row < n ? rp[row] : 0;
+        const int64_t d = row < n ? rp[row + 1] - b : 0;
+        for (int64_t q = 0; q < w; ++q) sci[off[s] + 32 * q + lane] = q < d ? ci[b + q] : -1;
+    }
+}
+
+cudaError_t build_sell(const int64_t* rp, const int32_t* ci, int64_t n, int64_t light0, int64_t n_slices,
+                       int64_t* off, int32_t** sci, int64_t* total, cudaStream_t s) {
+    *sci = nullptr;
+    *total = 0;
+    int64_t* w32 = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    cudaError_t e = cudaSuccess;
+#define CK(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
+    CK(cudaMalloc(&w32, sizeof(int64_t) * (size_t)(n_slices + 1)));
+    k_sell_widths<<<1024, kThreads, 0, s>>>(rp, n, light0, n_slices, w32);
+    CK(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, w32, off, (int)(n_slices + 1), s));
+    CK(cudaMalloc(&tmp, tmp_bytes));
+    CK(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, w32, off, (int)(n_slices + 1), s));
+    CK(cudaMemcpyAsync(total, off + n_slices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMalloc(sci, sizeof(int32_t) * (size_t)(*total > 0 ? *total : 1)));
+    if (*total > 0) k_sell_fill<<<2048, kThreads, 0, s>>>(rp, ci, n, light0, n_slices, off, *sci);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+#undef CK
+done:
+    if (w32) cudaFree(w32);
+    if (tmp) cudaFree(tmp);
+    return e;
+}
+
 template <typename T>
 void to_internal(const T* src, const int32_t* perm, int64_t n, T* dst, cudaStream_t s) {
     k_gather_perm<T><<<608, kThreads, 0, s>>>(src, perm, n, dst);

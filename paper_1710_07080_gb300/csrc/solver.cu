@@ -8,6 +8,9 @@
 // device-side stopping test has fired, so a chunk may end with a few empty launches.
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -57,6 +60,11 @@ struct isira_handle_s {
     double* item_partial = nullptr;
     unsigned* item_count = nullptr;
     int32_t* warp_start = nullptr;
+    int32_t* deg32 = nullptr;      // degree per row (solver numbering), ld entries
+    int64_t* sell_off = nullptr;   // sliced ELL copy of the light rows (with relabelling)
+    int32_t* sell_ci = nullptr;
+    int64_t sell_total = 0;
+    int smem_max = 0;
     // optional internal relabelling (opts.reorder): owned CSR, perm[new] = old, inv[old] = new
     int64_t* own_rp = nullptr;
     int32_t* own_ci = nullptr;
@@ -136,6 +144,7 @@ InnerArgs<T> make_args(isira_handle h, InnerBuffers<T>& b, double sigma, int c, 
     a.x = v + 6 * ld;
     a.dinv = sizeof(T) == sizeof(double) ? v + 7 * ld : nullptr;
     a.gsum = reinterpret_cast<T*>(h->gsum);
+    a.deg = h->deg32;
     a.partial = reinterpret_cast<T*>(h->partial);
     a.pstride = (int)(h->partial_elems / 512);
     a.counter = h->counter;
@@ -171,6 +180,13 @@ OuterArgs make_outer(isira_handle h) {
 void sync(isira_handle h) {
     ck(cudaStreamSynchronize(h->stream));
     ck(cudaGetLastError());
+    if (h->hs && (static_cast<volatile HostStatus*>(h->hs)->dev_error & 1))
+        throw StatusError{ISIRA_ERR_DEVICE_TIMEOUT};
+}
+
+// start of an entry point: no device error recorded yet
+void clear_dev_error(isira_handle h) {
+    if (h->hs) static_cast<volatile HostStatus*>(h->hs)->dev_error = 0;
 }
 
 volatile HostStatus* hst(isira_handle h) { return h->hs; }
@@ -233,11 +249,13 @@ int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* 
     while (true) {
         const bool prof = h->profiling != 0;
         for (int i = 0; i < chunk; ++i) {
-            if (prof) ck(cudaEventRecord(h->ev[2 * i], s));
+            if (prof) ck(cudaEventRecord(h->ev[4 * i], s));
             inner_gather<T>(a, h->lanes, s);
-            if (prof) ck(cudaEventRecord(h->ev[2 * i + 1], s));
+            if (prof) ck(cudaEventRecord(h->ev[4 * i + 1], s));
             inner_rows<T>(a, s);
+            if (prof) ck(cudaEventRecord(h->ev[4 * i + 2], s));
             inner_phase2<T>(a, 0, s);
+            if (prof) ck(cudaEventRecord(h->ev[4 * i + 3], s));
         }
         h->stats.spmv_launches += chunk;
         h->stats.kernel_launches += 3 * chunk;
@@ -246,9 +264,13 @@ int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* 
         if (prof) {
             for (int i = 0; i < chunk; ++i) {
                 if (launched + i + 1 > itn) break;   // launches after the stop returned at once
-                float ms = 0.f;
-                ck(cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]));
+                float ms = 0.f, ms_rows = 0.f, ms_p2 = 0.f;
+                ck(cudaEventElapsedTime(&ms, h->ev[4 * i], h->ev[4 * i + 1]));
+                ck(cudaEventElapsedTime(&ms_rows, h->ev[4 * i + 1], h->ev[4 * i + 2]));
+                ck(cudaEventElapsedTime(&ms_p2, h->ev[4 * i + 2], h->ev[4 * i + 3]));
                 h->stats.inner_phase1_ms += ms;
+                h->stats.inner_rows_ms += ms_rows;
+                h->stats.inner_phase2_ms += ms_p2;
                 h->stats.inner_phase1_timed += 1;
                 h->stats.inner_phase1_csum += c;
             }
@@ -315,57 +337,134 @@ bool expand_basis(isira_handle h, int k, int c) {
     return false;
 }
 
-void choose_lanes(isira_handle h) {
-    if (h->opts.spmv_lanes > 0) {
-        int l = h->opts.spmv_lanes;
-        h->lanes = (l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32) ? l : 8;
-        return;
+// Gather launch shape: threads per CTA (kThreads: as many CTAs per SM as fit, at most 8;
+// kBigBlock: one per SM) and the shared-memory bytes of the hub block x[0:hub) (0: none).
+void apply_gather_shape(isira_handle h, int tpb, int hub_bytes) {
+    RowSched& rs = h->rs;
+    rs.tpb = tpb;
+    rs.hub = hub_bytes > 0 ? (int)h->n : 0;
+    rs.hub_bytes = hub_bytes > 0 ? hub_bytes : 0;
+    const int wpb = tpb / 32;
+    int ctas = gather_ctas_per_sm(tpb, rs.hub_bytes);
+    if (tpb == kThreads) ctas = std::min(ctas, 8);
+    if (ctas < 1) throw StatusError{ISIRA_ERR_INVALID_ARG};
+    const int64_t n_units = rs.n_units();
+    rs.n_warps = (int)std::max<int64_t>(wpb, std::min<int64_t>((int64_t)h->nsm * ctas * wpb,
+                                                               (n_units + wpb - 1) / wpb * wpb));
+}
+
+// hub block bytes for a cap (bytes of shared memory), rounded to 128 and never above the vector
+int hub_bytes_for(isira_handle h, int64_t cap) {
+    cap = std::min<int64_t>(cap, h->smem_max) / 128 * 128;
+    return (int)std::min<int64_t>(cap, (h->n * (int64_t)sizeof(double) + 127) / 128 * 128);
+}
+
+struct TuneKey {
+    int dev, prec, sell, reorder, lanes_fixed, logn, mdeg, logmax, gb, hub_kb;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dev, prec, sell, reorder, lanes_fixed, logn, mdeg, logmax, gb, hub_kb) <
+               std::tie(o.dev, o.prec, o.sell, o.reorder, o.lanes_fixed, o.logn, o.mdeg, o.logmax, o.gb, o.hub_kb);
     }
-    const double mean = (double)h->nnz / (double)h->n;
-    int heur = mean <= 3.0 ? 1 : (mean <= 6.0 ? 2 : (mean <= 12.0 ? 4 : 8));
-    h->lanes = heur;
-    if (h->n < 200000) return;
-    // time the phase-1 kernel of the handle's precision for every lane count
+};
+struct TuneVal { int tpb, hub_bytes, lanes; };
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+template <typename T>
+float time_gather(isira_handle h, InnerBuffers<T>& b, int lanes, cudaEvent_t e0, cudaEvent_t e1) {
     cudaStream_t s = h->stream;
+    InnerArgs<T> a = make_args<T>(h, b, 0.0, 0, nullptr, h->ld, 1e-3, 1);
+    inner_opstats<T>(a, a.z0, s);          // a fresh state: not done, iteration 0
+    float tot = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+        ck(cudaEventRecord(e0, s));
+        inner_gather<T>(a, lanes, s);
+        ck(cudaEventRecord(e1, s));
+        sync(h);
+        float ms = 0.f;
+        ck(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) tot += ms;
+    }
+    return tot;
+}
+
+// Autotuner of the inner SpMV gather: times the gather kernel of the handle's precision on this
+// graph for every candidate launch shape (and lane count of the CSR tiles, when the light rows
+// are not sliced), keeps the fastest, and caches the choice per device, precision and graph-
+// statistics bucket (log2 n, mean degree in half-octaves, log2 of the maximum degree), so graphs
+// of the same kind (a batch) are timed once.  Small graphs (n < 100k, launch-bound) get the
+// default shape without timing.
+void autotune_gather(isira_handle h) {
+    const isira_opts& o = h->opts;
+    RowSched& rs = h->rs;
+    const double mean = (double)h->nnz / (double)h->n;
+    const int heur = mean <= 3.0 ? 1 : (mean <= 6.0 ? 2 : (mean <= 12.0 ? 4 : 8));
+    const bool lanes_fixed = o.spmv_lanes > 0;
+    int l = o.spmv_lanes;
+    const int lanes0 = lanes_fixed ? ((l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32) ? l : 8) : heur;
+    // candidate shapes, filtered by the options the caller fixed
+    std::vector<std::pair<int, int>> shapes;
+    const int big_hub = (h->perm && o.hub_kb >= 0)
+                            ? hub_bytes_for(h, o.hub_kb > 0 ? (int64_t)o.hub_kb * 1024 : (int64_t)kDefaultHubBytes) : 0;
+    const int small_hub = (h->perm && o.hub_kb >= 0)
+                              ? hub_bytes_for(h, o.hub_kb > 0 ? (int64_t)o.hub_kb * 1024 : (int64_t)48 * 1024) : 0;
+    const int order_perm[2] = {kBigBlock, kThreads}, order_plain[2] = {kThreads, kBigBlock};
+    for (int tpb : h->perm ? order_perm : order_plain) {
+        if (o.gather_block != 0 && o.gather_block != tpb) continue;
+        const int hub = tpb == kBigBlock ? big_hub : small_hub;
+        if (o.hub_kb >= 0 && hub > 0) shapes.push_back({tpb, hub});
+        if (o.hub_kb <= 0 || !h->perm) shapes.push_back({tpb, 0});
+    }
+    if (shapes.empty()) shapes.push_back({kThreads, 0});
+    // default (untimed) shape: the first candidate
+    apply_gather_shape(h, shapes[0].first, shapes[0].second);
+    h->lanes = lanes0;
+    if (h->n < 100000 || (shapes.size() == 1 && (lanes_fixed || rs.sell))) return;
+    int dev = 0;
+    ck(cudaGetDevice(&dev));
+    auto ilog2 = [](double v) { return (int)std::floor(std::log2(std::max(1.0, v))); };
+    const TuneKey key{dev, o.precision, rs.sell, o.reorder, lanes_fixed ? lanes0 : 0, ilog2((double)h->n),
+                      (int)std::floor(2.0 * std::log2(std::max(1.0, mean))), ilog2((double)h->max_degree),
+                      o.gather_block, o.hub_kb};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            apply_gather_shape(h, it->second.tpb, it->second.hub_bytes);
+            h->lanes = it->second.lanes;
+            return;
+        }
+    }
+    std::vector<int> lane_list;
+    if (lanes_fixed || rs.sell) lane_list.push_back(lanes0);
+    else lane_list = {1, 2, 4, 8, 16, 32};
     cudaEvent_t e0, e1;
     ck(cudaEventCreate(&e0));
     ck(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_l = heur;
-    for (int l : {1, 2, 4, 8, 16, 32}) {
-        float tot = 0.f;
-        for (int rep = 0; rep < 4; ++rep) {
-            if (h->opts.precision == ISIRA_MIXED) {
-                InnerArgs<float> a = make_args<float>(h, h->fb, 0.0, 0, nullptr, h->ld, 1e-3, 1);
-                inner_opstats<float>(a, a.z0, s);
-                ck(cudaEventRecord(e0, s));
-                inner_phase1<float>(a, l, s);
-                ck(cudaEventRecord(e1, s));
-            } else {
-                InnerArgs<double> a = make_args<double>(h, h->db, 0.0, 0, nullptr, h->ld, 1e-3, 1);
-                inner_opstats<double>(a, a.z0, s);
-                ck(cudaEventRecord(e0, s));
-                inner_phase1<double>(a, l, s);
-                ck(cudaEventRecord(e1, s));
+    TuneVal bv{shapes[0].first, shapes[0].second, lanes0};
+    for (const auto& sh : shapes) {
+        apply_gather_shape(h, sh.first, sh.second);
+        for (int ln : lane_list) {
+            const float t = o.precision == ISIRA_MIXED ? time_gather<float>(h, h->fb, ln, e0, e1)
+                                                       : time_gather<double>(h, h->db, ln, e0, e1);
+            if (t < best) {
+                best = t;
+                bv = TuneVal{sh.first, sh.second, ln};
             }
-            sync(h);
-            float ms = 0.f;
-            ck(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0) tot += ms;
-        }
-        if (tot < best) {
-            best = tot;
-            best_l = l;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->lanes = best_l;
+    apply_gather_shape(h, bv.tpb, bv.hub_bytes);
+    h->lanes = bv.lanes;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = bv;
 }
 
 void free_handle(isira_handle h) {
     if (!h) return;
-    void* ptrs[] = {h->gsum, h->own_rp, h->own_ci, h->perm, h->inv, h->item_row, h->item_k, h->item_partial,
+    void* ptrs[] = {h->gsum, h->deg32, h->sell_off, h->sell_ci, h->own_rp, h->own_ci, h->perm, h->inv, h->item_row, h->item_k, h->item_partial,
                     h->item_count, h->warp_start, h->U, h->W, h->V, h->H, h->theta, h->S, h->R, h->Z, h->dscratch,
                     h->partial, h->counter, h->Gm, h->Cinv, h->lam_dev, h->tres_dev, h->fb.base, h->fb.st,
                     h->db.base, h->db.st, h->Vt_f};
@@ -419,7 +518,7 @@ void apply_operator_t(isira_handle h, InnerBuffers<T>& b, double sigma, int c, c
     else ck(cudaMemcpyAsync(a.z0, d_x, sizeof(T) * h->n, cudaMemcpyDeviceToDevice, s));
     ck(cudaMemsetAsync(a.z0 + h->trim, 0, sizeof(T), s));   // x_i is treated as 0
     inner_opstats<T>(a, a.z0, s);
-    inner_phase1<T>(a, h->lanes, s);
+    inner_apply<T>(a, h->lanes, s);
     if (h->perm) to_external<T>(a.Y, h->perm, h->n, d_y, s);
     else ck(cudaMemcpyAsync(d_y, a.Y, sizeof(T) * h->n, cudaMemcpyDeviceToDevice, s));
     sync(h);
@@ -454,6 +553,7 @@ void isira_default_opts(isira_opts* o) {
     o->gather_sched = 0;
     o->index_vec = 0;
     o->gather_chunk = 0;
+    o->sell = 1;
 }
 
 const char* isira_error_string(isira_status s) {
@@ -467,6 +567,7 @@ const char* isira_error_string(isira_status s) {
         case ISIRA_ERR_OOM: return "out of memory";
         case ISIRA_ERR_NOT_SOLVED: return "no successful solve on this handle";
         case ISIRA_ERR_LIMIT: return "request exceeds the fixed scratch of the allocation-free entry point (c <= 8)";
+        case ISIRA_ERR_DEVICE_TIMEOUT: return "a bounded wait inside a kernel ran out (the results of the call are not valid)";
     }
     return "unknown status";
 }
@@ -563,53 +664,43 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         rs.n_items = (int)di.n_items;
         rs.light_deg = light_deg;
         rs.ci_vec = h->own_ci != nullptr && h->opts.index_vec == 1;
-        rs.dyn = h->opts.gather_sched == 0;
         rs.chunk = (h->opts.gather_chunk >= 1 && h->opts.gather_chunk <= 32) ? h->opts.gather_chunk : kUnitChunk;
-        // Gather launch shape.  With the hubs numbered first (relabelling on) one 1024-thread CTA
-        // per SM stages the largest block x[0:hub) that fits in shared memory, so most gathered
-        // entries are shared-memory reads; otherwise 256-thread CTAs, up to 6 per SM.
+        // sliced ELL copy of the light rows: the degree-descending numbering puts the long rows first
+        rs.sell = 0;
+        rs.n_slices = 0;
+        rs.light0 = n;
+        if (h->perm && h->opts.sell != 0) {
+            const int64_t ns = (n - di.n_long + 31) / 32;
+            if (ns > INT32_MAX / 2) throw StatusError{ISIRA_ERR_INVALID_ARG};
+            ck(cudaMalloc(&h->sell_off, sizeof(int64_t) * (size_t)(ns + 1)));
+            ck(build_sell(d_row_ptr, d_col_idx, n, di.n_long, ns, h->sell_off, &h->sell_ci, &h->sell_total, s));
+            rs.sell_ci = h->sell_ci;
+            rs.sell_off = h->sell_off;
+            rs.n_slices = (int)ns;
+            rs.light0 = di.n_long;
+            rs.sell = 1;
+        }
+        // slices are always taken dynamically; the static partition's cost model knows CSR tiles only
+        rs.dyn = h->opts.gather_sched == 0 || rs.sell;
+        if (rs.n_units() > INT32_MAX / 2) throw StatusError{ISIRA_ERR_INVALID_ARG};
         {
             int optin = 0;
             ck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-            const int smem_max = std::max(0, optin - 1024);          // room for static shared memory
-            ck(inner_gather_attrs<float>(smem_max));
-            ck(inner_gather_attrs<double>(smem_max));
-            ck(outer_gather_attrs(smem_max));
-            const int gb = h->opts.gather_block;
-            rs.tpb = (gb == kThreads || gb == kBigBlock) ? gb : (h->perm ? kBigBlock : kThreads);
-            int64_t cap = h->opts.hub_kb > 0 ? (int64_t)h->opts.hub_kb * 1024 : (int64_t)kDefaultHubBytes;
-            cap = std::min<int64_t>(cap, smem_max) / 128 * 128;
-            rs.hub = (h->perm && h->opts.hub_kb >= 0) ? (int)n : 0;
-            rs.hub_bytes = rs.hub ? (int)std::min<int64_t>(cap, (n * (int64_t)sizeof(double) + 127) / 128 * 128) : 0;
+            h->smem_max = std::max(0, optin - 1024);          // room for static shared memory
+            ck(inner_gather_attrs<float>(h->smem_max));
+            ck(inner_gather_attrs<double>(h->smem_max));
+            ck(outer_gather_attrs(h->smem_max));
         }
-        const int wpb = rs.tpb / 32;
-        int ctas = gather_ctas_per_sm(rs.tpb, rs.hub_bytes);
-        if (rs.tpb == kThreads) ctas = std::min(ctas, 6);
-        if (ctas < 1) throw StatusError{ISIRA_ERR_INVALID_ARG};
-        // one launch wave of gather warps, each with an equal share of the estimated cost
-        const int64_t n_units = di.n_items + (n + 31) / 32;
-        if (n_units > INT32_MAX) throw StatusError{ISIRA_ERR_INVALID_ARG};
-        rs.n_warps = (int)std::max<int64_t>(wpb, std::min<int64_t>((int64_t)h->nsm * ctas * wpb,
-                                                                   (n_units + wpb - 1) / wpb * wpb));
-        ck(cudaMalloc(&h->warp_start, sizeof(int32_t) * (size_t)(rs.n_warps + 1)));
-        {
-            int64_t* cost = nullptr;
-            int64_t* prefix = nullptr;
-            ck(cudaMalloc(&cost, sizeof(int64_t) * (size_t)n_units));
-            ck(cudaMalloc(&prefix, sizeof(int64_t) * (size_t)(n_units + 1)));
-            setup_partition(d_row_ptr, n, h->item_row, h->item_k, di.n_items, light_deg, rs.n_warps, cost, prefix,
-                            h->warp_start, s);
-            sync(h);
-            cudaFree(cost);
-            cudaFree(prefix);
-        }
+        // the launch shape is chosen at the end of create (autotune_gather); buffers are sized for
+        // every candidate: at most 8 CTAs of 8 warps per SM
+        ck(cudaMalloc(&h->warp_start, sizeof(int32_t) * (size_t)(h->nsm * 64 + 1)));
         rs.warp_start = h->warp_start;
         // up to 8 CTAs per SM (a full SM of 256-thread CTAs); register-heavy row kernels are cut to
         // one wave of their resident CTAs at launch
         h->ew_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)h->nsm * 8));
         h->ts_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64, (int64_t)h->nsm * 6));
         // shared scratch for block partial sums: 512 slots x the largest grid
-        const int64_t maxgrid = std::max<int64_t>({(int64_t)rs.grid(), (int64_t)h->ew_blocks, (int64_t)h->ts_blocks});
+        const int64_t maxgrid = std::max<int64_t>({(int64_t)h->nsm * 8, (int64_t)h->ew_blocks, (int64_t)h->ts_blocks});
         h->partial_elems = (size_t)512 * (size_t)maxgrid;
         ck(cudaMalloc(&h->partial, sizeof(double) * h->partial_elems));
         ck(cudaMalloc(&h->counter, sizeof(unsigned) * 8));
@@ -622,6 +713,9 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         ck(cudaMalloc(&h->R, sizeof(double) * (size_t)h->ld));
         ck(cudaMalloc(&h->Z, sizeof(double) * (size_t)h->ld));
         ck(cudaMalloc(&h->gsum, sizeof(double) * (size_t)h->ld));
+        ck(cudaMemsetAsync(h->gsum, 0, sizeof(double) * (size_t)h->ld, s));
+        ck(cudaMalloc(&h->deg32, sizeof(int32_t) * (size_t)h->ld));
+        setup_deg32(d_row_ptr, n, h->ld, h->deg32, s);
         ck(cudaMalloc(&h->dscratch, sizeof(double) * 512));
         ck(cudaMalloc(&h->Gm, sizeof(double) * kCMax * kCMax));
         ck(cudaMalloc(&h->Cinv, sizeof(double) * kCMax * kCMax));
@@ -630,12 +724,25 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         ck(cudaHostAlloc(&h->hs, sizeof(HostStatus), cudaHostAllocMapped));
         std::memset(h->hs, 0, sizeof(HostStatus));
         ck(cudaHostGetDevicePointer((void**)&h->hs_dev, h->hs, 0));
+        h->rs.err = &h->hs_dev->dev_error;
         if (h->opts.precision == ISIRA_MIXED) alloc_inner(h, h->fb); else alloc_inner(h, h->db);
         int chunk = h->opts.inner_chunk > 0 ? h->opts.inner_chunk : 16;
-        h->ev.resize(2 * chunk);
+        h->ev.resize(4 * chunk);
         for (auto& e : h->ev) ck(cudaEventCreate(&e));
         sync(h);
-        choose_lanes(h);
+        autotune_gather(h);
+        if (!rs.dyn) {   // static partition of the CSR work units for the chosen shape
+            const int64_t n_units = rs.n_units();
+            int64_t* cost = nullptr;
+            int64_t* prefix = nullptr;
+            ck(cudaMalloc(&cost, sizeof(int64_t) * (size_t)n_units));
+            ck(cudaMalloc(&prefix, sizeof(int64_t) * (size_t)(n_units + 1)));
+            setup_partition(d_row_ptr, n, h->item_row, h->item_k, di.n_items, light_deg, rs.n_warps, cost, prefix,
+                            h->warp_start, s);
+            sync(h);
+            cudaFree(cost);
+            cudaFree(prefix);
+        }
         h->stats.n = n;
         h->stats.nnz = nnz;
         h->stats.trim_index = h->trim_user;
@@ -647,6 +754,7 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         h->stats.n_work_items = h->n_items;
         h->stats.gather_block = h->rs.tpb;
         h->stats.hub_bytes = h->rs.hub_bytes;
+        h->stats.sell_entries = h->sell_total;
     } catch (CudaError& e) {
         isira_status st = map_cuda(e.e);
         free_handle(h);
@@ -686,6 +794,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
     const auto t0 = std::chrono::steady_clock::now();
     isira_status status = ISIRA_OK;
     h->solved = false;
+    clear_dev_error(h);
     try {
         const isira_opts& o = h->opts;
         int m = o.m > 0 ? o.m : std::max(20, 2 * d + 10);
@@ -711,6 +820,9 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         h->stats.inner_phase1_ms = 0.0;
         h->stats.inner_phase1_timed = 0;
         h->stats.inner_phase1_csum = 0;
+        h->stats.inner_rows_ms = 0.0;
+        h->stats.inner_phase2_ms = 0.0;
+        h->stats.w_columns = 0;
         h->stats.kernel_launches = 0;
         (void)keep;
         h->lam.assign(d, 0.0);
@@ -729,6 +841,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         while (true) {
             if (h->stats.outer_steps >= max_outer) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
             h->stats.outer_steps += 1;
+            h->stats.w_columns += k;
             outer_sym_eig(h->H, kMMax, k, h->theta, h->S, kMMax, h->hs_dev, warm_w, s);   // Rayleigh-Ritz
             warm_w = k;
             outer_residual(oa, k, s);                                              // residual
@@ -837,6 +950,8 @@ isira_status isira_eigpairs(isira_handle h, double* h_eigvals, double* d_eigvecs
         if (n_out) *n_out = c;
     } catch (CudaError& e) {
         return map_cuda(e.e);
+    } catch (StatusError& e) {
+        return e.s;
     }
     return ISIRA_OK;
 }
@@ -846,6 +961,7 @@ isira_status isira_apply_operator(isira_handle h, int precision, double sigma, i
     if (!h || !d_x || !d_y || c < 0 || c >= kCMax || (c > 0 && !d_V) ||
         (precision != ISIRA_FP64 && precision != ISIRA_MIXED))
         return ISIRA_ERR_INVALID_ARG;
+    clear_dev_error(h);
     try {
         if (precision == ISIRA_MIXED)
             apply_operator_t<float>(h, h->fb, sigma, c, d_V, static_cast<const float*>(d_x), static_cast<float*>(d_y));
@@ -854,6 +970,8 @@ isira_status isira_apply_operator(isira_handle h, int precision, double sigma, i
                                      static_cast<double*>(d_y));
     } catch (CudaError& e) {
         return map_cuda(e.e);
+    } catch (StatusError& e) {
+        return e.s;
     }
     return ISIRA_OK;
 }
@@ -863,6 +981,7 @@ isira_status isira_inner_solve(isira_handle h, int precision, double sigma, int 
     if (!h || !d_r || !d_z || c < 0 || c >= kCMax || (c > 0 && !d_V) || !(tau > 0.0) || max_it < 1 ||
         (precision != ISIRA_FP64 && precision != ISIRA_MIXED))
         return ISIRA_ERR_INVALID_ARG;
+    clear_dev_error(h);
     try {
         cudaStream_t s = h->stream;
         // the right-hand side goes through the residual buffer, its norm through the scalar area
@@ -894,6 +1013,8 @@ isira_status isira_inner_solve(isira_handle h, int precision, double sigma, int 
         if (relres) *relres = hst(h)->inner_relres;
     } catch (CudaError& e) {
         return map_cuda(e.e);
+    } catch (StatusError& e) {
+        return e.s;
     }
     return ISIRA_OK;
 }

@@ -231,7 +231,7 @@ def rgg(n: int, mean_degree: float = 12.0, seed: int = 1, lcc: bool = True) -> G
     """Random geometric graph in the unit square (not a torus).
 
     Point t has coordinates (uniform01(seed, 2t), uniform01(seed, 2t+1)); two
-    points are joined when their distance is below r = sqrt(mean_degree/(pi n))
+    points are joined when their distance is at most r = sqrt(mean_degree/(pi n))
     (boundary effects ignored when choosing r).
     """
     from scipy.spatial import cKDTree
@@ -378,7 +378,16 @@ def rmat_gpu(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19
         keys.append(u * n + v)
         keys.append(v * n + u)
         del e, x, down, right
-    key = torch.unique(torch.cat(keys))          # sorted, deduplicated
+    return _csr_lcc_gpu(torch.cat(keys), n)
+
+
+def _csr_lcc_gpu(keys, n):
+    """CSR (row_ptr int64, col_idx int32, device tensors) of the largest connected component of the
+    graph whose directed edge keys u * n + v (both directions present) are given, with the same
+    deduplication, tie rule and ascending relabelling as largest_component()."""
+    import torch
+    device = keys.device
+    key = torch.unique(keys)                     # sorted, deduplicated
     del keys
     rows = key // n
     cols = key - rows * n
@@ -408,3 +417,44 @@ def rmat_gpu(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19
     rp = torch.zeros(m + 1, dtype=torch.int64, device=device)
     rp[1:] = torch.cumsum(torch.bincount(r2, minlength=m), 0)
     return rp, c2.to(torch.int32)
+
+
+def rgg_gpu(n: int, mean_degree: float = 12.0, seed: int = 1, device: str = "cuda", batch: int = 1 << 22):
+    """The graph of rgg(n, mean_degree, seed) (same points, pairs at distance <= r, largest
+    component, ascending relabelling) built with torch on the GPU from a cell list: the unit
+    square is cut into square cells of side >= r, so every pair within distance r lies in the
+    same or in adjacent cells.  Returns (row_ptr, col_idx) as device tensors (int64, int32)."""
+    import torch
+    r = math.sqrt(mean_degree / (math.pi * n))
+    t = torch.arange(n, dtype=torch.int64, device=device)
+    px = _uniform01_torch(seed, 2 * t)
+    py = _uniform01_torch(seed, 2 * t + 1)
+    nc = max(1, int(math.floor(1.0 / r)))        # cells per side, side 1/nc >= r
+    cx = torch.clamp((px * nc).to(torch.int64), max=nc - 1)
+    cy = torch.clamp((py * nc).to(torch.int64), max=nc - 1)
+    cell = cx * nc + cy
+    order = torch.argsort(cell)
+    cell_sorted = cell[order]
+    start = torch.zeros(nc * nc + 1, dtype=torch.int64, device=device)
+    start[1:] = torch.cumsum(torch.bincount(cell_sorted, minlength=nc * nc), 0)
+    r2 = r * r
+    keys = []
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for b0 in range(0, n, batch):
+                i = order[b0:b0 + batch]                  # points, in cell order
+                ncx, ncy = cx[i] + dx, cy[i] + dy
+                ok = (ncx >= 0) & (ncx < nc) & (ncy >= 0) & (ncy < nc)
+                i = i[ok]
+                c2 = (ncx * nc + ncy)[ok]
+                cnt = start[c2 + 1] - start[c2]
+                ii = torch.repeat_interleave(i, cnt)
+                off = torch.repeat_interleave(start[c2] - torch.cumsum(cnt, 0) + cnt, cnt)
+                jj = order[off + torch.arange(ii.numel(), dtype=torch.int64, device=device)]
+                d2 = (px[ii] - px[jj]) ** 2 + (py[ii] - py[jj]) ** 2
+                keep = (d2 <= r2) & (ii < jj)
+                u, v = ii[keep], jj[keep]
+                keys.append(u * n + v)
+                keys.append(v * n + u)
+                del ii, jj, off, d2, keep
+    return _csr_lcc_gpu(torch.cat(keys), n)

@@ -1,7 +1,9 @@
-"""Full-size parity on the benchmark workload (R-MAT scale 20 LCC, n = 646,379, nnz = 31.4 M,
-k = 10), in the launch configuration bench.py times, against stored eigenvalues of the FP64
-oracle's full run (tests/golden/, written by tests/golden/make_golden.py from oracle/ only) and
-against residuals the oracle recomputes from the GPU eigenvectors."""
+"""Full-size parity on the benchmark workloads, in the launch configuration bench.py times:
+ * 3-D grid 128^3 (n = 2,097,152), k = 20, against the closed-form spectrum and eigenvectors
+   (Kronecker sums of path Laplacians), at the tolerance that meets both accuracy bars;
+ * R-MAT scale 20 LCC (n = 646,379, nnz = 31.4 M), k = 10, against stored eigenvalues of the FP64
+   oracle's full runs (tests/golden/, written by tests/golden/make_golden.py from oracle/ only)
+   and against residuals the oracle recomputes from the GPU eigenvectors."""
 import json
 import math
 import os
@@ -9,8 +11,10 @@ import os
 import numpy as np
 import pytest
 
+import bench
 import oracle
 import synthgraphs as sg
+from tests import closed_forms as cf
 from tests.gpu_util import dev_graph, need_gpu, torch
 
 pytestmark = pytest.mark.gpu
@@ -28,12 +32,13 @@ def golden(name):
     return json.load(open(os.path.join(HERE, "golden", name)))
 
 
-def solve(g, prec, eps_rel):
+def solve(g, prec, eps_rel=None, k=10, eps_abs=None):
     import paper_1710_07080_gb300 as isira
     rp, ci = dev_graph(g)
     u0 = torch.from_numpy(sg.start_vector(g.n, 1)).cuda()
     p = isira.ISIRA_FP64 if prec == "fp64" else isira.ISIRA_MIXED
-    return isira.solve(rp, ci, 10, tol=eps_rel * 2.0 * g.degrees.max(), u0=u0, precision=p)
+    tol = eps_abs if eps_abs is not None else eps_rel * 2.0 * g.degrees.max()
+    return isira.solve(rp, ci, k, tol=tol, u0=u0, precision=p)
 
 
 def oracle_residuals(g, lam, V):
@@ -80,3 +85,106 @@ def test_rmat20_benchmark_tolerance(rmat20, prec):
         # same algorithm, same readings: the FP64 oracle's run at this tolerance took as many steps
         st = golden("rmat20_bench.json")["oracle_stats"]
         assert abs(res.stats["outer_steps"] - st["outer_steps"]) <= 3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_rmat20_accuracy_tolerance_matches_oracle(rmat20, prec):
+    """At the tolerance that meets both bars (eps from the accuracy rule with the oracle's
+    eigenvalue estimates at residual 1e-8): every eigenvalue within 1e-9 (relative) of the
+    oracle's tight run and of the oracle's run at the same eps, every true residual <= 1e-8."""
+    g = rmat20
+    normL = 2.0 * g.degrees.max()
+    eps = bench.accuracy_eps(golden("rmat20_bench.json")["eigvals"], normL)
+    c4 = golden("rmat20_c4.json")
+    assert abs(eps - c4["eps_abs"]) <= 1e-3 * eps
+    res = solve(g, prec, eps_abs=eps)
+    assert res.status == 0
+    lam = res.eigvals.numpy()
+    V = res.eigvecs.cpu().numpy()
+    r = oracle_residuals(g, lam, V)
+    assert r.max() <= 1e-8 and r.max() * normL <= 1.01 * eps
+    for ref in (golden("rmat20_tight.json")["eigvals"], c4["eigvals"]):
+        np.testing.assert_allclose(lam, ref, rtol=1e-9)
+    np.testing.assert_allclose(V.T @ V, np.eye(10), atol=1e-10)
+
+
+# ----------------------------------------------------------------------------------- 3-D grid 128^3
+
+N3 = 128
+
+
+@pytest.fixture(scope="module")
+def grid128():
+    need_gpu()
+    return sg.grid3d(N3, N3, N3)
+
+
+def _path_vec(i, N=N3):
+    """Unit eigenvector of the path Laplacian for 2 - 2 cos(pi i / N): cos(pi i (a + 1/2) / N)."""
+    v = np.cos(np.pi * i * (np.arange(N) + 0.5) / N)
+    return v / np.linalg.norm(v)
+
+
+def _grid_vec(ijk):
+    """Eigenvector of the grid Laplacian for the index triple (vertex (a, b, c) has id (a N + b) N + c)."""
+    a, b, c = (_path_vec(t) for t in ijk)
+    return (a[:, None, None] * b[None, :, None] * c[None, None, :]).ravel()
+
+
+def _grid_clusters(count):
+    """The `count` smallest positive eigenvalues of the 128^3 grid as clusters of equal value:
+    list of (eigenvalue, [index triples]) in ascending order, covering at least `count` pairs."""
+    mu = 2.0 - 2.0 * np.cos(np.pi * np.arange(6) / N3)
+    trip = sorted(((mu[i] + mu[j] + mu[l], (i, j, l)) for i in range(6) for j in range(6) for l in range(6)
+                   if (i, j, l) != (0, 0, 0)), key=lambda t: t[0])
+    out = []
+    for lam, ijk in trip:
+        if out and abs(lam - out[-1][0]) <= 1e-12 * lam:
+            out[-1][1].append(ijk)
+        else:
+            if sum(len(c[1]) for c in out) >= count:
+                break
+            out.append((lam, [ijk]))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_grid128_closed_form_at_accuracy_tolerance(grid128, prec):
+    """k = 20 at eps = min(1e-8 ||L||, sqrt(1e-10 lambda gap)) = 1e-5 lambda_1 (the rule with the
+    closed-form spectrum; bench.py reaches the same value from its Ritz estimates): eigenvalues
+    within 1e-9 of the closed form, residuals <= 1e-8, and for every complete cluster of equal
+    eigenvalues the computed invariant subspace matches the closed-form one within the
+    Davis-Kahan bound; the cluster that k = 20 cuts is checked by the distance of its computed
+    vector from the cluster's eigenspace."""
+    g = grid128
+    k = 20
+    normL = 2.0 * g.degrees.max()
+    ref = cf.grid3d(N3, N3, N3)[1:k + 1]
+    eps = bench.accuracy_eps(ref, normL)
+    assert abs(eps - 1e-5 * ref[0]) <= 1e-12
+    res = solve(g, prec, k=k, eps_abs=eps)
+    assert res.status == 0
+    lam = res.eigvals.numpy()
+    V = res.eigvecs.cpu().numpy()
+    np.testing.assert_allclose(lam, ref, rtol=1e-9)
+    rabs = oracle_residuals(g, lam, V) * normL
+    assert rabs.max() / normL <= 1e-8 and rabs.max() <= 1.01 * eps
+    np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-10)
+    assert np.abs(V.sum(axis=0)).max() <= 1e-9 * math.sqrt(g.n)
+    clusters = _grid_clusters(k)
+    pos = 0
+    for ci, (mu, trips) in enumerate(clusters):
+        X = np.stack([_grid_vec(t) for t in trips], axis=1)
+        m = len(trips)
+        take = min(m, k - pos)
+        Vc = V[:, pos:pos + take]
+        # distance to the rest of the spectrum (the next cluster above, the previous below)
+        gaps = [abs(mu - c[0]) for c in clusters[max(0, ci - 1):ci + 2] if c[0] != mu]
+        bound = 10.0 * math.sqrt(take) * rabs[pos:pos + take].max() / min(gaps)
+        R = Vc - X @ (X.T @ Vc)                       # components outside the cluster's eigenspace
+        assert np.linalg.norm(R, 2) <= bound, (ci, np.linalg.norm(R, 2), bound)
+        if take == m:                                 # complete cluster: the subspaces coincide
+            assert abs(np.linalg.svd(X.T @ Vc, compute_uv=False).min() - 1.0) <= bound
+        pos += take
+        if pos >= k:
+            break

@@ -115,7 +115,7 @@ def test_operator_independent_of_gather_launch_shape(isira, name, dtype, index_v
     tx = torch.from_numpy(x).cuda()
     tV = torch.from_numpy(V).cuda()
     if dtype == "fp32":
-        tx, tV = tx.float(), tV.float()
+        tx = tx.float()                 # the deflation vectors stay float64 (the C ABI's type)
     prec = isira.ISIRA_MIXED if dtype == "fp32" else isira.ISIRA_FP64
     outs = []
     for block, hub, sched in [(256, -1, 1), (256, 16, 0), (1024, -1, 0), (1024, 1, 1), (1024, 0, 0), (256, 0, 1)]:

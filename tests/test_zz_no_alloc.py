@@ -2,15 +2,14 @@
 callers that cannot let a library allocate device memory (a pre-reserved pool with a fixed
 budget, latency-critical loops where cudaMalloc/cudaFree may synchronise the device, plug-in
 hosts that forbid allocations).  Checked through the C ABI against isira_apply_operator, on two
-calls in a row (the static scratch keeps the first call's contents), in FP64 and FP32.
+calls in a row (the static scratch keeps the first call's contents), in FP64 and FP32, and
+elementwise against the FP64 oracle's trimmed operator (Theorem 2.6) on the same inputs.
 
 This file is named so that pytest collects it last."""
-import ctypes as C
-
 import numpy as np
 import pytest
 
-import oracle  # noqa: F401  (kept importable alongside; not used for the comparison)
+import oracle
 import synthgraphs as sg
 from tests.gpu_util import abs_adjacency_apply, dev_graph, need_gpu, orthonormal_columns, torch
 
@@ -62,11 +61,18 @@ def test_noalloc_matches_handle_entry_point_on_two_calls(prec, name):
             assert st2 == isira.ISIRA_OK and free1 == free0
             np.testing.assert_array_equal(y_out.double().cpu().numpy(), y)   # deterministic
             assert y[trim] == 0.0 and np.all(np.isfinite(y))
+            # the oracle's operator on the (n-1)-vector with the trimmed entry removed
+            x0 = x.copy()
+            x0[trim] = 0.0
+            yh = oracle.trimmed_apply(g.row_ptr, g.col_idx, trim, sigma, delta, V, np.delete(x0, trim))
+            y_or = np.insert(yh, trim, 0.0)
             if prec == "fp64":
                 np.testing.assert_allclose(y, y_ref, rtol=0, atol=1e-12 * np.abs(y_ref).max())
+                np.testing.assert_allclose(y, y_or, rtol=0, atol=1e-12 * np.abs(y_or).max())
             else:
                 bound = fp32_bound(g, x, V, sigma, delta, c)
                 assert np.all(np.abs(y - y_ref) <= 4 * bound + 1e-30)
+                assert np.all(np.abs(y - y_or) <= 2 * bound + 1e-30)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
