@@ -81,18 +81,18 @@ def _load():
 def _bind(lib):
     """Declares the C signatures on a loaded oracle library."""
     P = C.c_void_p
-    lib.or_laplacian_apply.argtypes = [C.c_int64, P, P, P, P]
+    lib.or_laplacian_apply.argtypes = [C.c_int64, P, P, P, P, P]
     lib.or_sym_eig.argtypes = [C.c_int, P, P, P, C.c_int]
     lib.or_sym_eig.restype = C.c_int
-    lib.or_dense_laplacian_eig.argtypes = [C.c_int64, P, P, P, P]
-    lib.or_trimmed_apply.argtypes = [C.c_int64, P, P, C.c_int64, C.c_double, C.c_double, P, C.c_int,
+    lib.or_dense_laplacian_eig.argtypes = [C.c_int64, P, P, P, P, P]
+    lib.or_trimmed_apply.argtypes = [C.c_int64, P, P, P, C.c_int64, C.c_double, C.c_double, P, C.c_int,
                                      C.c_int, P, P]
     lib.or_backmap.argtypes = [C.c_int64, C.c_int64, P, P]
-    lib.or_precond_apply.argtypes = [C.c_int64, P, C.c_int64, C.c_double, C.c_double, P, C.c_int, P, P]
-    lib.or_inner_solve.argtypes = [C.c_int64, P, P, C.c_int64, C.c_double, C.c_double, P, C.c_int,
+    lib.or_precond_apply.argtypes = [C.c_int64, P, P, C.c_int64, C.c_double, C.c_double, P, C.c_int, P, P]
+    lib.or_inner_solve.argtypes = [C.c_int64, P, P, P, C.c_int64, C.c_double, C.c_double, P, C.c_int,
                                    C.c_int, P, C.c_double, C.c_int, P, P]
     lib.or_inner_solve.restype = C.c_int
-    lib.or_isira.argtypes = [C.c_int64, P, P, P, C.POINTER(Params), P, P, C.POINTER(Stats)]
+    lib.or_isira.argtypes = [C.c_int64, P, P, P, P, C.POINTER(Params), P, P, C.POINTER(Stats)]
     lib.or_isira.restype = C.c_int
     return lib
 
@@ -105,15 +105,26 @@ def _csr(row_ptr, col_idx):
     return (np.ascontiguousarray(row_ptr, dtype=np.int64), np.ascontiguousarray(col_idx, dtype=np.int32))
 
 
-def laplacian_apply(row_ptr, col_idx, x) -> np.ndarray:
-    """y = L x, L = D - A (paper Eq. 1.1). x may be (n,) or (n, b)."""
+def _w(weights, nnz):
+    """Edge weights as a contiguous float64 array aligned with col_idx (None: unit weights)."""
+    if weights is None:
+        return None, None
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    if w.shape != (nnz,):
+        raise ValueError(f"weights must have shape ({nnz},)")
+    return w, _p(w)
+
+
+def laplacian_apply(row_ptr, col_idx, x, weights=None) -> np.ndarray:
+    """y = L x, L = D - A (paper Eq. 1.1), or the weighted L_w x. x may be (n,) or (n, b)."""
     rp, ci = _csr(row_ptr, col_idx)
     x = np.asarray(x, dtype=np.float64)
     if x.ndim == 2:
-        return np.stack([laplacian_apply(rp, ci, x[:, t]) for t in range(x.shape[1])], axis=1)
+        return np.stack([laplacian_apply(rp, ci, x[:, t], weights) for t in range(x.shape[1])], axis=1)
     x = np.ascontiguousarray(x)
     y = np.empty_like(x)
-    _load().or_laplacian_apply(rp.shape[0] - 1, _p(rp), _p(ci), _p(x), _p(y))
+    w, wp = _w(weights, ci.shape[0])
+    _load().or_laplacian_apply(rp.shape[0] - 1, _p(rp), _p(ci), wp, _p(x), _p(y))
     return y
 
 
@@ -127,13 +138,14 @@ def sym_eig(A, max_sweeps: int = 100):
     return th, S, sw
 
 
-def dense_laplacian_eig(row_ptr, col_idx):
-    """All eigenpairs of L by dense Jacobi (definition oracle, small n)."""
+def dense_laplacian_eig(row_ptr, col_idx, weights=None):
+    """All eigenpairs of L (or L_w) by dense Jacobi (definition oracle, small n)."""
     rp, ci = _csr(row_ptr, col_idx)
     n = rp.shape[0] - 1
     lam = np.empty(n)
     X = np.empty((n, n), order="F")
-    _load().or_dense_laplacian_eig(n, _p(rp), _p(ci), _p(lam), _p(X))
+    w, wp = _w(weights, ci.shape[0])
+    _load().or_dense_laplacian_eig(n, _p(rp), _p(ci), wp, _p(lam), _p(X))
     return lam, X
 
 
@@ -144,14 +156,15 @@ def _vmat(V, n):
     return V, V.shape[1]
 
 
-def trimmed_apply(row_ptr, col_idx, trim, sigma, delta, V, xh, drop_rank1=False) -> np.ndarray:
+def trimmed_apply(row_ptr, col_idx, trim, sigma, delta, V, xh, drop_rank1=False, weights=None) -> np.ndarray:
     """Theorem 2.6 operator on an (n-1)-vector."""
     rp, ci = _csr(row_ptr, col_idx)
     n = rp.shape[0] - 1
     V, c = _vmat(V, n)
     xh = np.ascontiguousarray(xh, dtype=np.float64)
     yh = np.empty(n - 1)
-    _load().or_trimmed_apply(n, _p(rp), _p(ci), int(trim), float(sigma), float(delta), _p(V), c,
+    w, wp = _w(weights, ci.shape[0])
+    _load().or_trimmed_apply(n, _p(rp), _p(ci), wp, int(trim), float(sigma), float(delta), _p(V), c,
                              int(bool(drop_rank1)), _p(xh), _p(yh))
     return yh
 
@@ -164,17 +177,19 @@ def backmap(n, trim, zh) -> np.ndarray:
     return z
 
 
-def precond_apply(row_ptr, trim, sigma, delta, V, xh) -> np.ndarray:
+def precond_apply(row_ptr, trim, sigma, delta, V, xh, weights=None) -> np.ndarray:
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     n = rp.shape[0] - 1
     V, c = _vmat(V, n)
     xh = np.ascontiguousarray(xh, dtype=np.float64)
     ph = np.empty(n - 1)
-    _load().or_precond_apply(n, _p(rp), int(trim), float(sigma), float(delta), _p(V), c, _p(xh), _p(ph))
+    w, wp = _w(weights, int(rp[-1]))
+    _load().or_precond_apply(n, _p(rp), wp, int(trim), float(sigma), float(delta), _p(V), c, _p(xh), _p(ph))
     return ph
 
 
-def inner_solve(row_ptr, col_idx, trim, sigma, delta, V, r, tau=1e-10, max_it=100000, drop_rank1=False):
+def inner_solve(row_ptr, col_idx, trim, sigma, delta, V, r, tau=1e-10, max_it=100000, drop_rank1=False,
+                weights=None):
     """Trimmed MINRES solve + back-map: returns (zstar, iterations, relative residual estimate)."""
     rp, ci = _csr(row_ptr, col_idx)
     n = rp.shape[0] - 1
@@ -182,7 +197,8 @@ def inner_solve(row_ptr, col_idx, trim, sigma, delta, V, r, tau=1e-10, max_it=10
     r = np.ascontiguousarray(r, dtype=np.float64)
     z = np.empty(n)
     rr = C.c_double(0.0)
-    it = _load().or_inner_solve(n, _p(rp), _p(ci), int(trim), float(sigma), float(delta), _p(V), c,
+    w, wp = _w(weights, ci.shape[0])
+    it = _load().or_inner_solve(n, _p(rp), _p(ci), wp, int(trim), float(sigma), float(delta), _p(V), c,
                                 int(bool(drop_rank1)), _p(r), float(tau), int(max_it), _p(z), C.byref(rr))
     return z, it, rr.value
 
@@ -195,8 +211,9 @@ def default_mq(d: int) -> tuple[int, int]:
 
 
 def isira(row_ptr, col_idx, d, u0, eps=1e-10, sigma0=0.0, m=None, q=None, trim=-1, delta=0.0,
-          omega=0.1, tau_inner=1e-10, max_inner=20000, max_outer=100000, drop_rank1=False, seed=2):
-    """Algorithm 2.  Returns (lam[d] in locking order, V n-by-d, stats dict)."""
+          omega=0.1, tau_inner=1e-10, max_inner=20000, max_outer=100000, drop_rank1=False, seed=2, weights=None):
+    """Algorithm 2 (on L, or on the weighted L_w when weights are given).  Returns (lam[d] in locking
+    order, V n-by-d, stats dict)."""
     rp, ci = _csr(row_ptr, col_idx)
     n = rp.shape[0] - 1
     dm, dq = default_mq(d)
@@ -210,7 +227,8 @@ def isira(row_ptr, col_idx, d, u0, eps=1e-10, sigma0=0.0, m=None, q=None, trim=-
     lam = np.zeros(d)
     V = np.zeros((n, d), order="F")
     st = Stats()
-    _load().or_isira(n, _p(rp), _p(ci), _p(u0), C.byref(p), _p(lam), _p(V), C.byref(st))
+    w, wp = _w(weights, ci.shape[0])
+    _load().or_isira(n, _p(rp), _p(ci), wp, _p(u0), C.byref(p), _p(lam), _p(V), C.byref(st))
     stats = {f: getattr(st, f) for f, _ in Stats._fields_}
     stats.update(m=m, q=q)
     return lam, V, stats

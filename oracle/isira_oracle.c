@@ -61,13 +61,26 @@ static double uniform_at(uint64_t seed, uint64_t counter) {
 #define OR_PLANT 0
 #endif
 
-/* ---------------------------------------------------------------- Eq. 1.1 */
+/* ---------------------------------------------------------------- Eq. 1.1 and the weighted Laplacian */
 
-void or_laplacian_apply(int64_t n, const int64_t* rp, const int32_t* ci, const double* x, double* y) {
+/* Weight of stored entry e (1 when the graph is unweighted, w == NULL). */
+static double wt(const double* w, int64_t e) { return w ? w[e] : 1.0; }
+
+/* Diagonal entry of L (or L_w = D_w - W, the weighted Laplacian of the Remark after Theorem 1.2):
+ * the sum of the weights of row r's edges. */
+static double wdeg(const int64_t* rp, const double* w, int64_t r) {
+    if (!w || OR_PLANT == 10) return (double)(rp[r + 1] - rp[r]);
+    double s = 0.0;
+    for (int64_t e = rp[r]; e < rp[r + 1]; ++e) s += w[e];
+    return s;
+}
+
+void or_laplacian_apply(int64_t n, const int64_t* rp, const int32_t* ci, const double* w, const double* x,
+                        double* y) {
     for (int64_t r = 0; r < n; ++r) {
-        double deg = (double)(rp[r + 1] - rp[r]);
+        double deg = wdeg(rp, w, r);
         double s = deg * x[r];
-        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) s -= (OR_PLANT == 1 ? -1.0 : 1.0) * x[ci[e]];
+        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) s -= (OR_PLANT == 1 ? -1.0 : 1.0) * wt(w, e) * x[ci[e]];
         y[r] = s;
     }
 }
@@ -153,11 +166,12 @@ int or_sym_eig(int k, const double* Ain, double* theta, double* S, int max_sweep
     return converged ? sweeps : -1;
 }
 
-int or_dense_laplacian_eig(int64_t n, const int64_t* rp, const int32_t* ci, double* lam, double* X) {
+int or_dense_laplacian_eig(int64_t n, const int64_t* rp, const int32_t* ci, const double* w, double* lam,
+                           double* X) {
     double* L = (double*)calloc((size_t)n * n, sizeof(double));
     for (int64_t r = 0; r < n; ++r) {
-        L[r + r * n] = (double)(rp[r + 1] - rp[r]);
-        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) L[r + (int64_t)ci[e] * n] = -1.0;
+        L[r + r * n] = wdeg(rp, w, r);
+        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) L[r + (int64_t)ci[e] * n] = -wt(w, e);
     }
     int sw = or_sym_eig((int)n, L, lam, X, 100);
     free(L);
@@ -168,8 +182,9 @@ int or_dense_laplacian_eig(int64_t n, const int64_t* rp, const int32_t* ci, doub
 
 static int64_t hat_of(int64_t r, int64_t trim) { return r < trim ? r : r - 1; }
 
-void or_trimmed_apply(int64_t n, const int64_t* rp, const int32_t* ci, int64_t trim, double sigma,
-                      double delta, const double* V, int c, int drop_rank1, const double* xh, double* yh) {
+void or_trimmed_apply(int64_t n, const int64_t* rp, const int32_t* ci, const double* w, int64_t trim,
+                      double sigma, double delta, const double* V, int c, int drop_rank1, const double* xh,
+                      double* yh) {
     int64_t nh = n - 1;
     double s1 = 0.0;
     for (int64_t t = 0; t < nh; ++t) s1 += xh[t];
@@ -180,12 +195,12 @@ void or_trimmed_apply(int64_t n, const int64_t* rp, const int32_t* ci, int64_t t
     for (int64_t r = 0; r < n; ++r) {
         if (r == trim) continue;
         int64_t rh = hat_of(r, trim);
-        double deg = (double)(rp[r + 1] - rp[r]);       /* diagonal of Lh is the full degree */
+        double deg = wdeg(rp, w, r);                     /* diagonal of Lh is the full degree */
         double s = (deg - sigma) * xh[rh];
         for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
             int64_t col = ci[e];
             if (col == trim) continue;                 /* column i is deleted */
-            s -= xh[hat_of(col, trim)];
+            s -= wt(w, e) * xh[hat_of(col, trim)];
         }
         if (!drop_rank1 && OR_PLANT != 3) s += (sigma / (double)n) * s1;
         for (int j = 0; j < c; ++j) s += (OR_PLANT == 4 ? -delta : delta) * V[r + (int64_t)j * n] * g[j];
@@ -207,6 +222,7 @@ typedef struct {
     int64_t n, trim;
     const int64_t* rp;
     const int32_t* ci;
+    const double* w;  /* edge weights (NULL: unit) */
     double sigma, delta;
     const double* V;
     int c, drop_rank1;
@@ -247,15 +263,15 @@ static void lu_solve(int c, const double* K, const int* piv, double* x) {
     }
 }
 
-static void ctx_init(op_ctx* x, int64_t n, const int64_t* rp, const int32_t* ci, int64_t trim, double sigma,
-                     double delta, const double* V, int c, int drop_rank1) {
-    x->n = n; x->rp = rp; x->ci = ci; x->trim = trim; x->sigma = sigma; x->delta = delta;
+static void ctx_init(op_ctx* x, int64_t n, const int64_t* rp, const int32_t* ci, const double* w, int64_t trim,
+                     double sigma, double delta, const double* V, int c, int drop_rank1) {
+    x->n = n; x->rp = rp; x->ci = ci; x->w = w; x->trim = trim; x->sigma = sigma; x->delta = delta;
     x->V = V; x->c = c; x->drop_rank1 = drop_rank1;
     x->mdiag = (double*)malloc(sizeof(double) * (size_t)(n - 1));
     x->tmp = (double*)malloc(sizeof(double) * (size_t)(n - 1));
     for (int64_t r = 0; r < n; ++r) {
         if (r == trim) continue;
-        double deg = (double)(rp[r + 1] - rp[r]);
+        double deg = wdeg(rp, w, r);
         double m = deg - sigma;
         if (m < 0.5 * deg) m = 0.5 * deg;
         x->mdiag[hat_of(r, trim)] = m;
@@ -299,10 +315,10 @@ static void ctx_precond(const op_ctx* x, const double* xh, double* ph) {
     free(b);
 }
 
-void or_precond_apply(int64_t n, const int64_t* rp, int64_t trim, double sigma, double delta,
+void or_precond_apply(int64_t n, const int64_t* rp, const double* w, int64_t trim, double sigma, double delta,
                       const double* V, int c, const double* xh, double* ph) {
     op_ctx x;
-    ctx_init(&x, n, rp, NULL, trim, sigma, delta, V, c, 0);
+    ctx_init(&x, n, rp, NULL, w, trim, sigma, delta, V, c, 0);
     ctx_precond(&x, xh, ph);
     ctx_free(&x);
 }
@@ -329,7 +345,8 @@ static int minres(const op_ctx* cx, const double* b, double* x, double tau, int 
     while (it < max_it) {
         ++it;
         for (int64_t t = 0; t < nh; ++t) v[t] = y[t] / beta;
-        or_trimmed_apply(cx->n, cx->rp, cx->ci, cx->trim, cx->sigma, cx->delta, cx->V, cx->c, cx->drop_rank1, v, y);
+        or_trimmed_apply(cx->n, cx->rp, cx->ci, cx->w, cx->trim, cx->sigma, cx->delta, cx->V, cx->c, cx->drop_rank1,
+                         v, y);
         if (it >= 2)
             for (int64_t t = 0; t < nh; ++t) y[t] -= (beta / oldb) * r1[t];
         double alfa = dot(nh, v, y);
@@ -364,11 +381,11 @@ done:
     return it;
 }
 
-int or_inner_solve(int64_t n, const int64_t* rp, const int32_t* ci, int64_t trim, double sigma, double delta,
-                   const double* V, int c, int drop_rank1, const double* r, double tau, int max_it,
+int or_inner_solve(int64_t n, const int64_t* rp, const int32_t* ci, const double* w, int64_t trim, double sigma,
+                   double delta, const double* V, int c, int drop_rank1, const double* r, double tau, int max_it,
                    double* zstar, double* relres_out) {
     op_ctx cx;
-    ctx_init(&cx, n, rp, ci, trim, sigma, delta, V, c, drop_rank1);
+    ctx_init(&cx, n, rp, ci, w, trim, sigma, delta, V, c, drop_rank1);
     double* rh = (double*)malloc(sizeof(double) * (size_t)(n - 1));
     double* zh = (double*)malloc(sizeof(double) * (size_t)(n - 1));
     for (int64_t t = 0; t < n; ++t)
@@ -438,22 +455,23 @@ static void rotate_basis(int64_t n, double* X, int k, const double* S, int c0, i
     free(T);
 }
 
-int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, const or_params* p,
+int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* w, const double* u0, const or_params* p,
              double* lam, double* Vout, or_stats* st) {
     memset(st, 0, sizeof(*st));
     const double t_start = wall_seconds();
     int d = p->d, m = p->m, q = p->q;
     if (n < 3 || d < 1 || d > n - 2 || q < d || m <= q || m < 2) { st->status = 2; return 2; }
 
-    /* Remark 4.1: trimming index = vertex of maximum degree, delta = 2 max diag(L) */
+    /* Remark 4.1: trimming index = vertex of maximum degree (diagonal entry), delta = 2 max diag(L) */
     int64_t trim = p->trim;
-    int64_t dmax = 0, argmax = 0;
+    double dmax = 0.0;
+    int64_t argmax = 0;
     for (int64_t r = 0; r < n; ++r) {
-        int64_t dg = rp[r + 1] - rp[r];
+        double dg = wdeg(rp, w, r);
         if (dg > dmax) { dmax = dg; argmax = r; }
     }
     if (trim < 0 || trim >= n) trim = argmax;
-    double delta = p->delta > 0.0 ? p->delta : 2.0 * (double)dmax;
+    double delta = p->delta > 0.0 ? p->delta : 2.0 * dmax;
     st->trim = trim;
     st->delta = delta;
 
@@ -486,7 +504,7 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
             for (int a = 0; a < k; ++a) {
                 double* ua = U + (int64_t)a * n;
                 double* wa = W + (int64_t)a * n;
-                or_laplacian_apply(n, rp, ci, ua, wa);
+                or_laplacian_apply(n, rp, ci, w, ua, wa);
                 for (int b = 0; b < c; ++b) vtu[b] = dot(n, V + (int64_t)b * n, ua);
                 for (int b = 0; b < c; ++b)
                     for (int64_t t = 0; t < n; ++t) wa[t] += delta * V[t + (int64_t)b * n] * vtu[b];
@@ -530,7 +548,7 @@ int or_isira(int64_t n, const int64_t* rp, const int32_t* ci, const double* u0, 
                 /* inexact inner solve: trimmed solve (Eq. 2.4 / 2.14) and the back-map (Eq. 2.5) */
                 double rr;
                 const double t_in = wall_seconds();
-                int its = or_inner_solve(n, rp, ci, trim, sigma, delta, V, c, p->drop_rank1, r,
+                int its = or_inner_solve(n, rp, ci, w, trim, sigma, delta, V, c, p->drop_rank1, r,
                                          p->tau_inner, p->max_inner, z, &rr);
                 st->inner_iters += its;
                 st->sec_inner += wall_seconds() - t_in;

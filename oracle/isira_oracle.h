@@ -21,8 +21,13 @@
 extern "C" {
 #endif
 
-/* y = L x with L = D - A (Eq. 1.1). */
-void or_laplacian_apply(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+/* Edge weights.  Every function below that takes `w` accepts either NULL (an unweighted graph:
+ * every stored entry has weight 1, L = D - A of Eq. 1.1) or positive weights w[nnz] aligned with
+ * col_idx and symmetric (w of (r, c) equals w of (c, r)): the weighted Laplacian L_w = D_w - W of
+ * the Remark after Theorem 1.2, whose diagonal entry is the sum of the row's weights. */
+
+/* y = L x with L = D - A (Eq. 1.1), or L_w x. */
+void or_laplacian_apply(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* w,
                         const double* x, double* y);
 
 /* All eigenpairs of a symmetric k-by-k matrix A by cyclic Jacobi rotations
@@ -34,7 +39,7 @@ void or_laplacian_apply(int64_t n, const int64_t* row_ptr, const int32_t* col_id
 int or_sym_eig(int k, const double* A, double* theta, double* S, int max_sweeps);
 
 /* Dense definition oracle: all n eigenpairs of L (n <= a few hundred). */
-int or_dense_laplacian_eig(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+int or_dense_laplacian_eig(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* w,
                            double* lam, double* X);
 
 /* The trimmed, shifted, deflated operator of Theorem 2.6 (Eq. 2.14),
@@ -42,8 +47,8 @@ int or_dense_laplacian_eig(int64_t n, const int64_t* row_ptr, const int32_t* col
  * on (n-1)-vectors, where "h" quantities have row/column `trim` removed.
  * V is n-by-c (full rows; the trimmed row is skipped here).  drop_rank1 = 1
  * omits the (sigma/n) 1h 1h^T term (Remark 3.1). */
-void or_trimmed_apply(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t trim,
-                      double sigma, double delta, const double* V, int c, int drop_rank1,
+void or_trimmed_apply(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* w,
+                      int64_t trim, double sigma, double delta, const double* V, int c, int drop_rank1,
                       const double* xh, double* yh);
 
 /* Back-map of Theorem 2.4 (Eq. 2.5): zstar = [zh(1:i-1); 0; zh(i:n-1)] - (1h^T zh / n) 1. */
@@ -51,14 +56,14 @@ void or_backmap(int64_t n, int64_t trim, const double* zh, double* zstar);
 
 /* Preconditioner of Remark 3.2 with a diagonal Mh_sigma ~ Lh - sigma Ih and the
  * Sherman-Morrison-Woodbury form of Eq. 3.6 when c > 0:  ph = P^{-1} xh. */
-void or_precond_apply(int64_t n, const int64_t* row_ptr, int64_t trim, double sigma, double delta,
-                      const double* V, int c, const double* xh, double* ph);
+void or_precond_apply(int64_t n, const int64_t* row_ptr, const double* w, int64_t trim, double sigma,
+                      double delta, const double* V, int c, const double* xh, double* ph);
 
 /* Solve the trimmed system of Eq. 2.14 with preconditioned MINRES (Paige & Saunders 1975)
  * to relative preconditioned residual tau, then apply the back-map.  r is the
  * n-vector right-hand side; its trimmed row is dropped.  Returns iterations. */
-int or_inner_solve(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t trim,
-                   double sigma, double delta, const double* V, int c, int drop_rank1,
+int or_inner_solve(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* w,
+                   int64_t trim, double sigma, double delta, const double* V, int c, int drop_rank1,
                    const double* r, double tau, int max_it, double* zstar, double* relres_out);
 
 typedef struct {
@@ -93,8 +98,8 @@ typedef struct {
 
 /* Algorithm 2.  u0: unit n-vector orthogonal to 1 (the k0 = 1 start basis).
  * Outputs: lam[d] in locking order, V n-by-d (column-major). */
-int or_isira(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* u0,
-             const or_params* p, double* lam, double* V, or_stats* st);
+int or_isira(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* w,
+             const double* u0, const or_params* p, double* lam, double* V, or_stats* st);
 
 #ifdef __cplusplus
 }

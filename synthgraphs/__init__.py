@@ -303,6 +303,18 @@ def batch_family(G: int = 256, nmin: int = 1000, nmax: int = 200000, seed: int =
     return out
 
 
+# --------------------------------------------------------------------------- edge weights
+
+def edge_weights(g: Graph, seed: int = 1, lo: float = 0.5, hi: float = 2.0) -> np.ndarray:
+    """Positive weights aligned with g.col_idx for the weighted Laplacian: edge {u, v} gets
+    lo + (hi - lo) * uniform01(seed, min(u, v) * n + max(u, v)), so both stored directions of an
+    edge carry the same weight."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
+    cols = g.col_idx.astype(np.int64)
+    key = np.minimum(rows, cols) * np.int64(g.n) + np.maximum(rows, cols)
+    return lo + (hi - lo) * uniform01(seed, key.astype(np.uint64))
+
+
 # --------------------------------------------------------------------------- start vector
 
 def start_vector(n: int, seed: int = 1) -> np.ndarray:

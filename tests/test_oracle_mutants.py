@@ -10,6 +10,7 @@ import oracle
 import synthgraphs as sg
 from tests import closed_forms as cf
 from tests import test_oracle_pins as pins
+from tests import test_oracle_weighted as wpins
 
 pytestmark = pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc is needed to build the variants")
 
@@ -33,6 +34,8 @@ MUTANTS = {
         lambda: pins.test_isira_closed_forms(sg.path(40), cf.path(40), 6)),
     9: ("the restart keeps the q largest Ritz vectors instead of the q smallest (Algorithm 2)",
         lambda: pins.test_isira_restart_branch_keeps_the_closed_form_pairs()),
+    10: ("the diagonal of the weighted Laplacian counts edges instead of summing weights",
+         lambda: wpins.test_weighted_laplacian_definition(sg.grid2d(4, 5))),
 }
 
 
