@@ -507,8 +507,11 @@ def run_batch(args):
             dist.barrier()
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
-    iters = [b.stats(g)["inner_iters"] for g in range(len(graphs))]
+    per = [b.stats(g) for g in range(len(graphs))]
+    iters = [p["inner_iters"] for p in per]
+    solve_s = [p["solve_ms"] / 1e3 for p in per]
     res = [float(b.eigpairs(g)[2].max()) for g in range(len(graphs))]
+    crit = max(range(len(graphs)), key=lambda q: solve_s[q])
     value = max_over_ranks(statistics.mean(times), dist, dev)
     max_res = max_over_ranks(max(res), dist, dev)
     iters_max = max_over_ranks(float(max(iters)), dist, dev)
@@ -520,7 +523,13 @@ def run_batch(args):
                        "sum_n": int(sum(g.n for g in graphs)), "sum_nnz": int(sum(g.nnz for g in graphs)),
                        "resid_rel": rel},
             "batch": {"status": st, "max_true_resid_rel": max_res, "inner_iters_max": int(iters_max),
-                      "graphs_on_rank0": len(graphs), "sharding": "greedy by nnz + 10 n, no collective"}}
+                      "graphs_on_rank0": len(graphs), "sharding": "greedy by nnz + 10 n, no collective",
+                      # the batch can finish no sooner than its slowest graph's own solve (a chain of
+                      # dependent inner iterations): wall time against that bound and against the sum
+                      "critical_graph": {"index": mine[crit], "n": graphs[crit].n, "nnz": graphs[crit].nnz,
+                                         "solve_s": solve_s[crit], "inner_iters": iters[crit]},
+                      "sum_of_graph_solves_s": sum(solve_s),
+                      "wall_over_critical": (statistics.mean(times) / solve_s[crit]) if solve_s[crit] > 0 else None}}
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

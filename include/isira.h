@@ -103,6 +103,13 @@ typedef struct {
                              sliced ELL copy (slices of 32 rows, column-major, so every index load
                              of a warp is one 128-byte line); 0: from CSR tiles with spmv_lanes
                              lanes per row.  Sums differ only by rounding order. */
+    int precond;          /* preconditioner of the inner solve (Remark 3.2 with the deflation term of
+                             Eq. 3.6 by Sherman-Morrison-Woodbury in both cases):
+                             0 (default): the diagonal diag(max(deg - sigma, deg / 2));
+                             1: an aggregation multilevel preconditioner of the trimmed Laplacian
+                             (greedy aggregation, Galerkin coarse Laplacians, one symmetric V-cycle
+                             with damped Jacobi smoothing), standing in for combinatorial multigrid */
+    double ml_alpha;      /* precond = 1: over-correction factor of the coarse-grid correction; <= 0: 1.5 */
 } isira_opts;
 
 typedef struct {
@@ -134,6 +141,8 @@ typedef struct {
     long long w_columns;          /* sum over outer steps of the search-space size k: the columns of
                                      W_k = (L + delta V V^T) U_k that Algorithm 2 as printed recomputes */
     long long sell_entries;       /* stored entries (with padding) of the sliced ELL copy (0: none) */
+    double max_diag;              /* largest diagonal entry of L (the maximum degree; the maximum
+                                     weighted degree for isira_create_weighted) */
 } isira_stats;
 
 /* Fills *opts with the defaults listed above (precision = ISIRA_MIXED). */
@@ -149,6 +158,18 @@ ISIRA_API const char* isira_error_string(isira_status s);
  * receives a handle to release with isira_destroy; on failure *out is NULL. */
 ISIRA_API isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64_t* d_row_ptr,
                           const int32_t* d_col_idx, const isira_opts* opts, void* stream);
+
+/* Same as isira_create for the weighted Laplacian L_w = D_w - W of a graph with positive edge
+ * weights (paper Sec. 1.1, the Remark after Theorem 1.2): d_weights is a device double[nnz] aligned
+ * with d_col_idx, symmetric (the two stored entries of an edge carry the same weight) and
+ * positive; it is borrowed like the CSR.  The diagonal entry of L_w is the row's weight sum; the
+ * trimmed vertex is the one with the largest such entry (smallest id on ties) and delta = 2 x that
+ * entry (Remark 4.1); norm_L (stats) is 2 x that entry.  Every other call works on the handle as on
+ * an unweighted one (isira_apply_operator_noalloc and the batch calls take unweighted graphs only).
+ * Returns ISIRA_ERR_BAD_GRAPH if a vertex has a non-positive weight sum. */
+ISIRA_API isira_status isira_create_weighted(isira_handle* out, int64_t n, int64_t nnz, const int64_t* d_row_ptr,
+                                             const int32_t* d_col_idx, const double* d_weights,
+                                             const isira_opts* opts, void* stream);
 
 /* Algorithm 2: computes the k (the paper's d, 1 <= k <= min(32, n-2)) smallest positive
  * eigenpairs.  sigma: initial shift (the paper uses 0).  tol: the paper's epsilon, an
@@ -199,6 +220,16 @@ ISIRA_API isira_status isira_apply_operator(isira_handle h, int precision, doubl
 ISIRA_API isira_status isira_inner_solve(isira_handle h, int precision, double sigma, int c, const double* d_V,
                                const double* d_r, double tau, int max_it, double* d_z, int* iters,
                                double* relres);
+
+/* The multilevel preconditioner alone (opts.precond = 1; paper Sec. 3.2, where combinatorial
+ * multigrid plays this role): d_y = M^{-1} d_x for one V-cycle of the aggregation hierarchy of the
+ * trimmed Laplacian (Theorem 2.3), without the deflation term.  precision selects float
+ * (ISIRA_MIXED) or double (ISIRA_FP64) n-vectors; the trimmed entry of x is ignored and that of y
+ * is 0.  M^{-1} is symmetric and positive definite on the other entries.  Builds the hierarchy on
+ * first use (for any handle).  *levels and *coarse_n (may be NULL) receive the number of levels and
+ * the size of the coarsest (dense) level. */
+ISIRA_API isira_status isira_precond_apply(isira_handle h, int precision, const void* d_x, void* d_y, int* levels,
+                                           int64_t* coarse_n);
 
 /* All eigenpairs of a symmetric k-by-k matrix (k <= 64), the Rayleigh-Ritz step of Algorithm 2: one CTA of
  * parallel cyclic Jacobi in FP64.  d_H: k-by-k column-major input (not modified);

@@ -29,9 +29,11 @@ ISIRA_ERR_DEVICE_TIMEOUT = 9
 ISIRA_FP64 = 0
 ISIRA_MIXED = 1
 
-EXPORTED = ["isira_default_opts", "isira_error_string", "isira_create", "isira_solve", "isira_eigpairs",
+EXPORTED = ["isira_default_opts", "isira_error_string", "isira_create", "isira_create_weighted", "isira_solve",
+            "isira_eigpairs",
             "isira_get_stats", "isira_set_profiling", "isira_destroy", "isira_apply_operator",
             "isira_inner_solve", "isira_sym_eig", "isira_apply_operator_noalloc", "isira_batch_create",
+            "isira_precond_apply",
             "isira_batch_solve", "isira_batch_status", "isira_batch_eigpairs", "isira_batch_get_stats",
             "isira_batch_destroy"]
 
@@ -42,7 +44,8 @@ class isira_opts(C.Structure):
                 ("sigma_omega", C.c_double), ("drop_rank1", C.c_int), ("validate", C.c_int), ("seed", C.c_uint64),
                 ("spmv_lanes", C.c_int), ("inner_chunk", C.c_int), ("inner_graph", C.c_int),
                 ("reorder", C.c_int), ("gather_block", C.c_int), ("hub_kb", C.c_int),
-                ("gather_sched", C.c_int), ("index_vec", C.c_int), ("gather_chunk", C.c_int), ("sell", C.c_int)]
+                ("gather_sched", C.c_int), ("index_vec", C.c_int), ("gather_chunk", C.c_int), ("sell", C.c_int),
+                ("precond", C.c_int), ("ml_alpha", C.c_double)]
 
 
 class isira_stats(C.Structure):
@@ -55,7 +58,7 @@ class isira_stats(C.Structure):
                 ("inner_phase1_csum", C.c_longlong), ("kernel_launches", C.c_longlong),
                 ("gather_block", C.c_int), ("hub_bytes", C.c_int), ("hub_timeouts", C.c_longlong),
                 ("inner_rows_ms", C.c_double), ("inner_phase2_ms", C.c_double), ("w_columns", C.c_longlong),
-                ("sell_entries", C.c_longlong)]
+                ("sell_entries", C.c_longlong), ("max_diag", C.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -73,6 +76,8 @@ def _load() -> C.CDLL:
     lib.isira_error_string.restype = C.c_char_p
     lib.isira_create.argtypes = [C.POINTER(P), I64, I64, P, P, C.POINTER(isira_opts), P]
     lib.isira_create.restype = I
+    lib.isira_create_weighted.argtypes = [C.POINTER(P), I64, I64, P, P, P, C.POINTER(isira_opts), P]
+    lib.isira_create_weighted.restype = I
     lib.isira_solve.argtypes = [P, I, D, D, P]
     lib.isira_solve.restype = I
     lib.isira_eigpairs.argtypes = [P, P, P, P, C.POINTER(I)]
@@ -87,6 +92,8 @@ def _load() -> C.CDLL:
     lib.isira_apply_operator.restype = I
     lib.isira_inner_solve.argtypes = [P, I, D, I, P, P, D, I, P, C.POINTER(I), C.POINTER(D)]
     lib.isira_inner_solve.restype = I
+    lib.isira_precond_apply.argtypes = [P, I, P, P, C.POINTER(I), C.POINTER(I64)]
+    lib.isira_precond_apply.restype = I
     lib.isira_sym_eig.argtypes = [I, P, P, P, P]
     lib.isira_sym_eig.restype = I
     lib.isira_apply_operator_noalloc.argtypes = [I64, I64, P, P, I64, I, D, D, I, I, P, P, P, P]
@@ -220,17 +227,28 @@ class Result:
 class Solver:
     """Owns an isira handle for one graph (CSR on the GPU, kept alive by this object)."""
 
-    def __init__(self, row_ptr, col_idx, stream=None, **opts):
-        _check_csr(row_ptr, col_idx)
+    def __init__(self, row_ptr, col_idx, stream=None, weights=None, **opts):
+        """weights: optional float64 CUDA tensor [nnz] of positive, symmetric edge weights (the
+        weighted Laplacian, isira_create_weighted)."""
+        import torch
+        _check_csr(row_ptr, col_idx, cuda=False)
+        if weights is not None:
+            _check_tensor(weights, "weights", (torch.float64,), (col_idx.numel(),), cuda=False)
+        _check_cuda(row_ptr=row_ptr, col_idx=col_idx, weights=weights)
         self.row_ptr = row_ptr
         self.col_idx = col_idx
+        self.weights = weights
         self.n = self.row_ptr.numel() - 1
         self.nnz = self.col_idx.numel()
         self.opts = default_opts(**opts)
         self.stream = _stream_ptr(stream)
         h = C.c_void_p()
-        check(lib.isira_create(C.byref(h), self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col_idx),
-                               C.byref(self.opts), self.stream), "isira_create")
+        if weights is None:
+            check(lib.isira_create(C.byref(h), self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col_idx),
+                                   C.byref(self.opts), self.stream), "isira_create")
+        else:
+            check(lib.isira_create_weighted(C.byref(h), self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col_idx),
+                                            _ptr(weights), C.byref(self.opts), self.stream), "isira_create_weighted")
         self.h = h
         self._last_status = None
 
@@ -298,6 +316,19 @@ class Solver:
         check(lib.isira_apply_operator(self.h, prec, float(sigma), c, _ptr(Vc), _ptr(x), _ptr(y)),
               "isira_apply_operator")
         return y
+
+    def precond_apply(self, x):
+        """y = M^{-1} x, one V-cycle of the multilevel preconditioner (isira_precond_apply); returns
+        (y, levels, coarsest size)."""
+        import torch
+        prec = _check_x(x, self.n, cuda=False)
+        _check_cuda(x=x, row_ptr=self.row_ptr)
+        y = torch.empty_like(x)
+        lv = C.c_int(0)
+        nc = C.c_int64(0)
+        check(lib.isira_precond_apply(self.h, prec, _ptr(x), _ptr(y), C.byref(lv), C.byref(nc)),
+              "isira_precond_apply")
+        return y, lv.value, nc.value
 
     def inner_solve(self, r, sigma: float = 0.0, V=None, tau: float = 1e-3, max_it: int = 5000,
                     precision: int = ISIRA_MIXED):
@@ -407,9 +438,10 @@ class Batch:
 
 
 def solve(row_ptr, col_idx, k: int, sigma: float = 0.0, tol: float | None = None, rel_tol: float = 1e-8, u0=None,
-          **opts) -> Result:
-    """Computes the k smallest positive eigenpairs of the Laplacian of the graph (row_ptr, col_idx)."""
-    with Solver(row_ptr, col_idx, **opts) as s:
+          weights=None, **opts) -> Result:
+    """Computes the k smallest positive eigenpairs of the Laplacian (weighted, with weights) of the graph
+    (row_ptr, col_idx)."""
+    with Solver(row_ptr, col_idx, weights=weights, **opts) as s:
         status = s.solve(k, sigma, tol, u0=u0, rel_tol=rel_tol, raise_on_error=False)
         if status not in (ISIRA_OK, ISIRA_ERR_NO_CONVERGENCE, ISIRA_ERR_NOT_CONNECTED):
             raise IsiraError(status, "isira_solve")

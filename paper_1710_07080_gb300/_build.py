@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libisira.so")
-SOURCES = ["inner_f32.cu", "inner_f64.cu", "outer.cu", "solver.cu", "noalloc.cu", "batch.cu", "reorder.cu"]
+SOURCES = ["inner_f32.cu", "inner_f64.cu", "outer.cu", "solver.cu", "noalloc.cu", "batch.cu", "reorder.cu",
+           "multilevel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

@@ -206,11 +206,36 @@ struct RowSched {
     int64_t light0;
     int n_slices;
     int sell;
+    // weighted Laplacian (all null: unit weights): edge weights aligned with ci and with sell_ci
+    // (0 in the padding), in FP32 and FP64, and the weighted degrees (ld entries)
+    const float* __restrict__ wf;
+    const double* __restrict__ wd;
+    const float* __restrict__ swf;
+    const double* __restrict__ swd;
+    const float* __restrict__ degwf;
+    const double* __restrict__ degwd;
+    template <typename T> __host__ __device__ const T* wts() const;
+    template <typename T> __host__ __device__ const T* swts() const;
+    template <typename T> __host__ __device__ const T* degw() const;
     __host__ __device__ int grid() const { return n_warps / (tpb / 32); }
     __host__ __device__ int n_units() const {
         return n_items + (sell ? n_slices : (int)((n + 31) / 32));
     }
 };
+
+template <> __host__ __device__ inline const float* RowSched::wts<float>() const { return wf; }
+template <> __host__ __device__ inline const double* RowSched::wts<double>() const { return wd; }
+template <> __host__ __device__ inline const float* RowSched::swts<float>() const { return swf; }
+template <> __host__ __device__ inline const double* RowSched::swts<double>() const { return swd; }
+template <> __host__ __device__ inline const float* RowSched::degw<float>() const { return degwf; }
+template <> __host__ __device__ inline const double* RowSched::degw<double>() const { return degwd; }
+
+// degree of row r in precision T: the weighted degree when the graph has weights
+template <typename T>
+__device__ __forceinline__ T row_degree(const RowSched& S, int64_t r) {
+    const T* dw = S.degw<T>();
+    return dw ? dw[r] : (T)(S.rp[r + 1] - S.rp[r]);
+}
 
 constexpr int kBigBlock = 1024;             // one gather CTA per SM holding a large hub block
 constexpr int kDefaultHubBytes = 192 * 1024;  // hub block of a 1024-thread gather CTA
@@ -351,16 +376,22 @@ __device__ __forceinline__ T seg_sum_vec(const int32_t* __restrict__ ci, const T
     return s0 + s1;
 }
 
-// One pass of the scalar form: sub-lane j takes entries e + W*q, q < Q (e = pass base + j).
+// One pass of the scalar form: sub-lane j takes entries e + W*q, q < Q (e = pass base + j); with
+// weights (wt not null) every gathered value is scaled by its edge's weight.
 template <typename T, int W, int Q>
-__device__ __forceinline__ void scalar_pass(const int32_t* __restrict__ ci, const T* __restrict__ x, const T* sx,
-                                            int hub, int64_t e, int64_t end, T& s0, T& s1) {
+__device__ __forceinline__ void scalar_pass(const int32_t* __restrict__ ci, const T* __restrict__ wt,
+                                            const T* __restrict__ x, const T* sx, int hub, int64_t e, int64_t end,
+                                            T& s0, T& s1) {
     int32_t c[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) c[q] = (e + W * q < end) ? __ldcs(ci + e + W * q) : -1;
     T v[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) v[q] = c[q] >= 0 ? gather_x(x, sx, hub, c[q]) : T(0);
+    if (wt) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v[q] *= c[q] >= 0 ? __ldcs(wt + e + W * q) : T(0);
+    }
     if constexpr (Q == 8) {
         s0 += (v[0] + v[1]) + (v[2] + v[3]);
         s1 += (v[4] + v[5]) + (v[6] + v[7]);
@@ -373,15 +404,16 @@ __device__ __forceinline__ void scalar_pass(const int32_t* __restrict__ ci, cons
 // Whole-warp segments (W = 32) end with a half-width pass when at most 4W entries remain, so
 // the tail adds fewer padding zeros.
 template <typename T, int W>
-__device__ __forceinline__ T seg_sum_scalar(const int32_t* __restrict__ ci, const T* __restrict__ x, const T* sx,
-                                            int hub, int64_t beg, int64_t end, int j) {
+__device__ __forceinline__ T seg_sum_scalar(const int32_t* __restrict__ ci, const T* __restrict__ wt,
+                                            const T* __restrict__ x, const T* sx, int hub, int64_t beg, int64_t end,
+                                            int j) {
     T s0 = 0, s1 = 0;
     for (int64_t base = beg; base < end;) {
         if (W == 32 && end - base <= 4 * W) {
-            scalar_pass<T, W, 4>(ci, x, sx, hub, base + j, end, s0, s1);
+            scalar_pass<T, W, 4>(ci, wt, x, sx, hub, base + j, end, s0, s1);
             base += 4 * W;
         } else {
-            scalar_pass<T, W, 8>(ci, x, sx, hub, base + j, end, s0, s1);
+            scalar_pass<T, W, 8>(ci, wt, x, sx, hub, base + j, end, s0, s1);
             base += 8 * W;
         }
     }
@@ -395,8 +427,9 @@ struct VecChunks { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
 template <typename T, int W>
 __device__ __forceinline__ T seg_sum(const RowSched& S, const T* __restrict__ x, const T* sx, int hub, int64_t beg,
                                      int64_t end, int j) {
+    // the 128-bit index path is for unweighted graphs (the solver turns it off with weights)
     return S.ci_vec ? seg_sum_vec<T, W, VecChunks<T>::value>(S.ci, x, sx, hub, beg, end, j)
-                    : seg_sum_scalar<T, W>(S.ci, x, sx, hub, beg, end, j);
+                    : seg_sum_scalar<T, W>(S.ci, S.wts<T>(), x, sx, hub, beg, end, j);
 }
 
 // Calls epi(row, degree, sum_{c in N(row)} x[c]) exactly once for every row 0..n-1 (with a
@@ -531,6 +564,7 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
     };
     // sliced light rows: one lane per row, two slices at a time so that each lane keeps eight index
     // loads (four per row) in flight; a lane adds its row's entries in slice order
+    const T* __restrict__ sw = S.swts<T>();
     auto do_slices = [&](int s0, int s1) {
         for (int sa = s0; sa < s1; sa += 2) {
             const bool two = sa + 1 < s1;
@@ -553,6 +587,13 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
                 for (int u = 0; u < 4; ++u) {
                     va[u] = ia[u] >= 0 ? gather_x(x, sx, hub, ia[u]) : T(0);
                     vb[u] = ib[u] >= 0 ? gather_x(x, sx, hub, ib[u]) : T(0);
+                }
+                if (sw) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        va[u] *= ia[u] >= 0 ? __ldcs(sw + oa + (int64_t)(q + u) * 32 + lane) : T(0);
+                        vb[u] *= ib[u] >= 0 ? __ldcs(sw + ob + (int64_t)(q + u) * 32 + lane) : T(0);
+                    }
                 }
                 s_a += (va[0] + va[1]) + (va[2] + va[3]);
                 s_b += (vb[0] + vb[1]) + (vb[2] + vb[3]);
@@ -581,13 +622,22 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
     const int n_units = S.n_units();
     if (S.dyn) {
         // dynamic: warps take chunks of S.chunk units from a counter; the last warp to finish
-        // resets it for the next launch.  Which warp takes a unit never changes its sum.
+        // resets it for the next launch.  Which warp takes a unit never changes its sum.  With
+        // sliced light rows only the long-row items are taken this way: the slices are many and
+        // of nearly equal cost, so the warps walk them in a fixed grid-strided order instead of
+        // contending for one counter.
+        const int n_dyn = S.sell ? S.n_items : n_units;
         for (;;) {
             int u0 = 0;
             if (lane == 0) u0 = (int)atomicAdd(S.sched, (unsigned)S.chunk);
             u0 = __shfl_sync(kFull, u0, 0);
-            if (u0 >= n_units) break;             // the failing take precedes the fence below
-            do_range(u0, u0 + S.chunk < n_units ? u0 + S.chunk : n_units);
+            if (u0 >= n_dyn) break;               // the failing take precedes the fence below
+            do_range(u0, u0 + S.chunk < n_dyn ? u0 + S.chunk : n_dyn);
+        }
+        if (S.sell) {
+            const int gw = blockIdx.x * (int)(blockDim.x >> 5) + (threadIdx.x >> 5);
+            const int nw = gridDim.x * (int)(blockDim.x >> 5);
+            for (int s0 = 2 * gw; s0 < S.n_slices; s0 += 2 * nw) do_slices(s0, s0 + 2 < S.n_slices ? s0 + 2 : S.n_slices);
         }
         finish_dyn();
     } else {

@@ -83,9 +83,82 @@ __device__ __forceinline__ void vld_deg(const int32_t* __restrict__ p, int (&v)[
     else { v[0] = q.x; v[1] = q.y; }
 }
 
+// degrees of VN consecutive rows in precision T: the weighted degrees when the graph has weights,
+// else the int32 degree array
+template <typename T>
+__device__ __forceinline__ void vld_degree(const InnerArgs<T>& a, int64_t r0, T (&d)[Vec<T>::N]) {
+    const T* dw = a.rs.template degw<T>();
+    if (dw) {
+        vld(dw + r0, d);
+    } else {
+        int dg[Vec<T>::N];
+        vld_deg<T>(a.deg + r0, dg);
+#pragma unroll
+        for (int e = 0; e < Vec<T>::N; ++e) d[e] = (T)dg[e];
+    }
+}
+
 // deflation columns the per-thread accumulators of a bucket hold: c <= kCMax - 1 in every solve
 template <int NC>
 struct Ncols { static constexpr int value = NC < kCMax ? NC : kCMax - 1; };
+
+// ------------------------------------------------------------------ MINRES scalar step
+// Last CTA of phase 2 (one thread): beta_{k+1} = sqrt(bb) with bb = r_{k+1}^T P^{-1} r_{k+1}, then the
+// Givens rotation of column k of the Lanczos tridiagonal matrix (Paige & Saunders 1975), the
+// coefficients of the deferred w/x update, the stopping test phibar <= tau beta_1, and the host
+// status.  init: the first preconditioned vector (k = 0).  ssum = 1^T z_{k+1}.
+template <typename T>
+__device__ __forceinline__ void minres_step(const InnerArgs<T>& a, InnerState<T>* st, T bb, T ssum, int init, int k,
+                                            cudaGraphConditionalHandle cond, int has_cond) {
+    const T bnew = bb > T(0) ? sqrt(bb) : T(0);
+    int done;
+    if (init) {
+        st->beta1 = bnew;
+        st->beta = bnew;
+        st->oldb = T(0);
+        st->phibar = bnew;
+        st->cs = T(-1);
+        st->sn = T(0);
+        st->dbar = T(0);
+        st->epsln = T(0);
+        st->itn = 0;
+        st->pending = 0;
+        done = !(bnew > T(0));
+    } else {
+        const T alpha = st->alpha;
+        const T cs = st->cs, sn = st->sn, dbar = st->dbar;
+        const T oldeps = st->epsln;
+        const T dlt = cs * dbar + sn * alpha;
+        const T gbar = sn * dbar - cs * alpha;
+        const T epsln = sn * bnew;
+        const T dbar2 = -cs * bnew;
+        T gamma = sqrt(gbar * gbar + bnew * bnew);
+        if (!(gamma > T(0))) gamma = T(1e-30);
+        const T cs2 = gbar / gamma, sn2 = bnew / gamma;
+        const T phi = cs2 * st->phibar;
+        const T phibar = sn2 * st->phibar;
+        st->w_oldeps = oldeps;
+        st->w_dlt = dlt;
+        st->w_inv_gamma = T(1) / gamma;
+        st->w_phi = phi;
+        st->cs = cs2;
+        st->sn = sn2;
+        st->dbar = dbar2;
+        st->epsln = epsln;
+        st->phibar = phibar;
+        st->oldb = st->beta;
+        st->beta = bnew;
+        st->itn = k;
+        st->pending = 1;
+        done = (phibar <= a.tau * st->beta1) || (k >= a.max_it) || !(bnew > T(0));
+    }
+    st->s_cur = ssum;
+    st->done = done;
+    if (has_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
+    a.hs->inner_done = done;
+    a.hs->inner_iters = st->itn;
+    a.hs->inner_relres = st->beta1 > T(0) ? (double)(st->phibar / st->beta1) : 0.0;
+}
 
 // ------------------------------------------------------------------ phase 1
 // Row epilogue of the operator from the gathered neighbour sums, one pass over the rows:
@@ -111,11 +184,30 @@ __global__ void __launch_bounds__(TPB, TPB == kThreads ? 4 : 1) k_phase1_gather(
     for_each_row_gather<T, G>(a.rs, zc, epi, a.trim);
 }
 
+// Partial sums of one CTA, already reduced over the CTA, to the per-block slots; returns true in
+// the CTA that arrives last (all partials of all blocks are visible to it then).
+template <typename T>
+__device__ __forceinline__ bool block_values_arrive(const T* bv, int nv, T* partial, int pstride,
+                                                    unsigned* counter) {
+    __shared__ int last;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) partial[(size_t)i * pstride + blockIdx.x] = bv[i];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    return last != 0;
+}
+
+// Rows are taken in tiles of kThreads * VN; after a tile's row arithmetic, z_k and D^{-1} y' of the
+// tile sit in shared memory and every warp reads whole columns of Vh for the tile (coalesced
+// 16-byte loads), so the deflation reductions need a few registers per warp, whatever c is.
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
     constexpr int VN = Vec<T>::N;
     constexpr int NE = Ncols<NC>::value;
     constexpr int NA = 1 + 2 * NE;
+    constexpr int TILE = kThreads * VN;
+    constexpr int QW = (NE + kWarps - 1) / kWarps;          // columns per warp
     InnerState<T>* st = a.st;
     if (st->done) return;
     const int k = st->itn + 1;
@@ -134,68 +226,108 @@ __global__ void __launch_bounds__(kThreads) k_phase1(InnerArgs<T> a) {
     const T* __restrict__ wo1 = wbuf(a, j + 2);   // w_{j-1}
     T* __restrict__ wn = wbuf(a, j);              // w_j
     const T oldeps = st->w_oldeps, dlt = st->w_dlt, inv_gamma = st->w_inv_gamma, phi = st->w_phi;
-    T acc[NA];
+    __shared__ __align__(16) T sz[NE > 0 ? TILE : 1];
+    __shared__ __align__(16) T syd[NE > 0 ? TILE : 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T acc0 = T(0);
+    T ca[QW > 0 ? QW : 1], cg[QW > 0 ? QW : 1];
 #pragma unroll
-    for (int t = 0; t < NA; ++t) acc[t] = T(0);
+    for (int q = 0; q < (QW > 0 ? QW : 1); ++q) { ca[q] = T(0); cg[q] = T(0); }
     const int64_t n = a.rs.n, trim = a.trim;
     const T* __restrict__ Vt = a.Vt;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
-    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
-        T g[VN], z[VN], y[VN], yd[VN];
-        int dg[VN];
-        bool ok[VN];
-        vld(a.gsum + r0, g);
-        vld(zc + r0, z);
-        vld_deg<T>(a.deg + r0, dg);
-        T dinv[VN];
-        if (a.dinv) vld(a.dinv + r0, dinv);
-        T zpv[VN], w2[VN], w1[VN], xv[VN], wv[VN];
-        if (has_prev) {
-            vld(zp + r0, zpv);
-            vld(wo2 + r0, w2);
-            vld(wo1 + r0, w1);
-            vld_rw(a.x + r0, xv);
-        }
+    for (int64_t t0 = (int64_t)blockIdx.x * TILE; t0 < n; t0 += (int64_t)gridDim.x * TILE) {
+        const int64_t r0 = t0 + (int64_t)threadIdx.x * VN;
+        T z[VN], yd[VN];
 #pragma unroll
-        for (int e = 0; e < VN; ++e) {
-            const int64_t r = r0 + e;
-            ok[e] = r < n && r != trim;
-            const T degT = (T)dg[e];
-            const T D = precond_diag(degT, sigma);
-            const T di = a.dinv ? dinv[e] : T(1) / D;
-            T base = ((degT - sigma) * z[e] - g[e] + s_term) * inv_beta;
+        for (int e = 0; e < VN; ++e) { z[e] = T(0); yd[e] = T(0); }
+        if (r0 < n) {
+            T g[VN], y[VN];
+            T dgv[VN];
+            vld(a.gsum + r0, g);
+            vld(zc + r0, z);
+            vld_degree<T>(a, r0, dgv);
+            T dinv[VN];
+            if (a.dinv) vld(a.dinv + r0, dinv);
+            T zpv[VN], w2[VN], w1[VN], xv[VN], wv[VN];
             if (has_prev) {
-                base -= cprev * D * zpv[e];
-                const T w = (zpv[e] * inv_oldb - oldeps * w2[e] - dlt * w1[e]) * inv_gamma;
-                wv[e] = ok[e] ? w : T(0);
-                xv[e] += ok[e] ? phi * w : T(0);
+                vld(zp + r0, zpv);
+                vld(wo2 + r0, w2);
+                vld(wo1 + r0, w1);
+                vld_rw(a.x + r0, xv);
             }
-            y[e] = ok[e] ? base : T(0);
-            yd[e] = ok[e] ? base * di : T(0);           // padding rows may have D = 0
-            z[e] = ok[e] ? z[e] : T(0);
-            acc[0] += z[e] * inv_beta * y[e];
-        }
-        vst(a.Y + r0, y);
-        if (has_prev) {
-            vst(wn + r0, wv);
-            vst(a.x + r0, xv);
-        }
 #pragma unroll
-        for (int t = 0; t < NE; ++t) {
-            if (t < c) {
-                T v[VN];
-                vld(Vt + (int64_t)t * a.ldv + r0, v);
+            for (int e = 0; e < VN; ++e) {
+                const int64_t r = r0 + e;
+                const bool ok = r < n && r != trim;
+                const T degT = dgv[e];
+                const T D = precond_diag(degT, sigma);
+                const T di = a.dinv ? dinv[e] : T(1) / D;
+                T base = ((degT - sigma) * z[e] - g[e] + s_term) * inv_beta;
+                if (has_prev) {
+                    base -= cprev * D * zpv[e];
+                    const T w = (zpv[e] * inv_oldb - oldeps * w2[e] - dlt * w1[e]) * inv_gamma;
+                    wv[e] = ok ? w : T(0);
+                    xv[e] += ok ? phi * w : T(0);
+                }
+                y[e] = ok ? base : T(0);
+                yd[e] = ok ? base * di : T(0);           // padding rows may have D = 0
+                z[e] = ok ? z[e] : T(0);
+                acc0 += z[e] * inv_beta * y[e];
+            }
+            vst(a.Y + r0, y);
+            if (has_prev) {
+                vst(wn + r0, wv);
+                vst(a.x + r0, xv);
+            }
+        }
+        if (NE > 0 && c > 0) {
 #pragma unroll
-                for (int e = 0; e < VN; ++e) {
-                    const T vm = ok[e] ? v[e] : T(0);
-                    acc[1 + t] += vm * yd[e];
-                    acc[1 + NE + t] += vm * z[e];
+            for (int e = 0; e < VN; ++e) {
+                sz[threadIdx.x * VN + e] = z[e];
+                syd[threadIdx.x * VN + e] = yd[e];
+            }
+            __syncthreads();
+            // warp w owns columns w, w + kWarps, ...; a lane reads VN consecutive rows per step
+#pragma unroll
+            for (int q = 0; q < QW; ++q) {
+                const int t = warp + q * kWarps;
+                if (t < c) {
+                    const T* col = Vt + (int64_t)t * a.ldv + t0;
+#pragma unroll
+                    for (int u = 0; u < TILE / (32 * VN); ++u) {
+                        const int rr = (u * 32 + lane) * VN;
+                        if (t0 + rr < n) {
+                            T v[VN];
+                            vld(col + rr, v);
+#pragma unroll
+                            for (int e = 0; e < VN; ++e) {
+                                const T vm = t0 + rr + e < n ? v[e] : T(0);
+                                ca[q] += vm * syd[rr + e];
+                                cg[q] += vm * sz[rr + e];
+                            }
+                        }
+                    }
                 }
             }
+            __syncthreads();
         }
     }
+    // CTA sums: alpha' by a block reduction, the column sums by warp reductions (one warp per column)
+    __shared__ T bv[NA];
+    const T a0 = block_sum0(acc0);
+    if (threadIdx.x == 0) bv[0] = a0;
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+        const int t = warp + q * kWarps;
+        const T sa = warp_sum(ca[q]), sg = warp_sum(cg[q]);
+        if (lane == 0 && t < NE) {
+            bv[1 + t] = t < c ? sa : T(0);
+            bv[1 + NE + t] = t < c ? sg : T(0);
+        }
+    }
+    __syncthreads();
     __shared__ T red[NA];
-    if (block_partials_arrive<T, NA>(acc, NE > 0 ? NA : 1, a.partial, a.pstride, a.counter)) {
+    if (block_values_arrive<T>(bv, NE > 0 ? NA : 1, a.partial, a.pstride, a.counter)) {
         last_block_sum(a.partial, a.pstride, gridDim.x, NE > 0 ? NA : 1, red, a.counter);
         __shared__ double u1d[kCMax], gcd[kCMax], rhs[kCMax];
         __shared__ double alpha_s;
@@ -272,10 +404,10 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, c
     const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
     for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
         T yv[VN], zcv[VN], ya[VN], zt[VN], dinv[VN];
-        int dg[VN];
+        T dgv[VN];
         vld(a.Y + r0, yv);
         if (!init) vld(zc + r0, zcv);
-        vld_deg<T>(a.deg + r0, dg);
+        vld_degree<T>(a, r0, dgv);
         if (a.dinv) vld(a.dinv + r0, dinv);
 #pragma unroll
         for (int e = 0; e < VN; ++e) { ya[e] = T(0); zt[e] = T(0); }
@@ -297,7 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, c
         for (int e = 0; e < VN; ++e) {
             const int64_t r = r0 + e;
             const bool ok = r < n && r != trim;
-            const T degT = (T)dg[e];
+            const T degT = dgv[e];
             const T D = precond_diag(degT, sigma);
             const T di = a.dinv ? dinv[e] : T(1) / D;
             T y = yv[e] + ya[e];
@@ -311,58 +443,7 @@ __global__ void __launch_bounds__(kThreads) k_phase2(InnerArgs<T> a, int init, c
     }
     if (block_partials_arrive<T, 2>(acc, 2, a.partial, a.pstride, a.counter)) {
         last_block_sum(a.partial, a.pstride, gridDim.x, 2, red, a.counter);
-        if (threadIdx.x == 0) {
-            const T bb = red[0];
-            const T bnew = bb > T(0) ? sqrt(bb) : T(0);
-            int done;
-            if (init) {
-                st->beta1 = bnew;
-                st->beta = bnew;
-                st->oldb = T(0);
-                st->phibar = bnew;
-                st->cs = T(-1);
-                st->sn = T(0);
-                st->dbar = T(0);
-                st->epsln = T(0);
-                st->itn = 0;
-                st->pending = 0;
-                done = !(bnew > T(0));
-            } else {
-                // Givens step of MINRES for column k of the Lanczos tridiagonal matrix
-                const T alpha = st->alpha;
-                const T cs = st->cs, sn = st->sn, dbar = st->dbar;
-                const T oldeps = st->epsln;
-                const T dlt = cs * dbar + sn * alpha;
-                const T gbar = sn * dbar - cs * alpha;
-                const T epsln = sn * bnew;
-                const T dbar2 = -cs * bnew;
-                T gamma = sqrt(gbar * gbar + bnew * bnew);
-                if (!(gamma > T(0))) gamma = T(1e-30);
-                const T cs2 = gbar / gamma, sn2 = bnew / gamma;
-                const T phi = cs2 * st->phibar;
-                const T phibar = sn2 * st->phibar;
-                st->w_oldeps = oldeps;
-                st->w_dlt = dlt;
-                st->w_inv_gamma = T(1) / gamma;
-                st->w_phi = phi;
-                st->cs = cs2;
-                st->sn = sn2;
-                st->dbar = dbar2;
-                st->epsln = epsln;
-                st->phibar = phibar;
-                st->oldb = st->beta;
-                st->beta = bnew;
-                st->itn = k;
-                st->pending = 1;
-                done = (phibar <= a.tau * st->beta1) || (k >= a.max_it) || !(bnew > T(0));
-            }
-            st->s_cur = red[1];
-            st->done = done;
-            if (has_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
-            a.hs->inner_done = done;
-            a.hs->inner_iters = st->itn;
-            a.hs->inner_relres = st->beta1 > T(0) ? (double)(st->phibar / st->beta1) : 0.0;
-        }
+        if (threadIdx.x == 0) minres_step(a, st, red[0], red[1], init, k, cond, has_cond);
     }
 }
 
@@ -384,10 +465,10 @@ __global__ void __launch_bounds__(kThreads) k_apply_rows(InnerArgs<T> a) {
     const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
     for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
         T g[VN], z[VN], y[VN], vd[VN];
-        int dg[VN];
+        T dgv[VN];
         vld(a.gsum + r0, g);
         vld(a.z0 + r0, z);
-        vld_deg<T>(a.deg + r0, dg);
+        vld_degree<T>(a, r0, dgv);
 #pragma unroll
         for (int e = 0; e < VN; ++e) vd[e] = T(0);
 #pragma unroll
@@ -402,7 +483,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_rows(InnerArgs<T> a) {
 #pragma unroll
         for (int e = 0; e < VN; ++e) {
             const int64_t r = r0 + e;
-            const T degT = (T)dg[e];
+            const T degT = dgv[e];
             const T v = ((degT - sigma) * z[e] - g[e] + s_term) + vd[e];
             y[e] = (r < n && r != trim) ? v : T(0);
         }
@@ -434,7 +515,7 @@ __global__ void __launch_bounds__(kThreads) k_prep(InnerArgs<T> a, const double*
         a.wb1[r] = T(0);
         a.wb2[r] = T(0);
         if (a.dinv || NC > 0) {
-            const T degT = (T)(a.rs.rp[r + 1] - a.rs.rp[r]);
+            const T degT = row_degree<T>(a.rs, r);
             const T di = T(1) / precond_diag(degT, a.sigma);
             if (a.dinv) a.dinv[r] = di;
             if (NC > 0 && r != a.trim) {
@@ -563,7 +644,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(InnerArgs<T> a, double* G, do
             const int64_t r = r0 + rr;
             double v = 0.0;
             if (r < n && r != a.trim) {
-                const T degT = (T)(a.rs.rp[r + 1] - a.rs.rp[r]);
+                const T degT = row_degree<T>(a.rs, r);
                 v = (double)a.Vt[(int64_t)col * a.ldv + r] * rsqrt((double)precond_diag(degT, a.sigma));
             }
             gsm[col * ldt + rr] = v;
@@ -645,6 +726,358 @@ __global__ void k_copy_vcol(const double* src, T* dst, int64_t n) {
         dst[r] = (T)src[r];
 }
 
+// ------------------------------------------------------------------ multilevel-preconditioned MINRES
+// Preconditioner P = M + delta Vh Vh^T (Remark 3.2, Eq. 3.6) with M^{-1} one V-cycle of the
+// aggregation hierarchy (multilevel.cu); by Sherman-Morrison-Woodbury
+//   P^{-1} r = w - MV C^{-1} Vh^T w,  w = M^{-1} r,  MV = M^{-1} Vh,  C = delta^{-1} I + Vh^T MV.
+// P is not diagonal, so the unpreconditioned Lanczos vectors r_{k-1}, r_k are kept (buffers rp, rc,
+// shifted in place by phase 2a) instead of being rebuilt from z.  One iteration k:
+//   gather(z_k); ml_phase1: y' = ((deg - sigma) z_k - g + (sigma/n) s) / beta_k - (beta_k/beta_{k-1}) r_{k-1},
+//       the deferred w/x update, alpha' = v_k^T y', g_k = Vh^T z_k; last CTA: u1 = delta g_k / beta_k,
+//       alpha_k = alpha' + (g_k / beta_k)^T u1;
+//   ml_phase2a: r_{k+1} = y' + Vh u1 - (alpha_k / beta_k) r_k  (rp <- r_k, rc <- r_{k+1});
+//   V-cycle: w = M^{-1} r_{k+1};
+//   ml_phase2b: Vh^T w, r^T w, r^T MV, 1^T w; last CTA: t = C^{-1} Vh^T w, beta_{k+1}^2 = r^T w - (r^T MV) t,
+//       1^T z = 1^T w - (1^T MV) t, Givens step, stopping test;
+//   ml_phase2c: z_{k+1} = w - MV t.
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_ml_phase1(InnerArgs<T> a) {
+    constexpr int VN = Vec<T>::N;
+    constexpr int NE = Ncols<NC>::value;
+    constexpr int NA = 1 + NE;
+    InnerState<T>* st = a.st;
+    if (st->done) return;
+    const int k = st->itn + 1;
+    const int c = st->p_c;
+    const T sigma = st->p_sigma;
+    const T* __restrict__ zc = ((k - 1) & 1) ? a.z1 : a.z0;
+    const T* __restrict__ zp = (k & 1) ? a.z1 : a.z0;
+    const T beta = st->beta, oldb = st->oldb;
+    const T inv_beta = T(1) / beta;
+    const bool has_prev = k >= 2;
+    const T cprev = has_prev ? beta / oldb : T(0);
+    const T inv_oldb = has_prev ? T(1) / oldb : T(0);
+    const T s_term = st->p_sig_n * st->s_cur;
+    const int j = k - 1;
+    const T* __restrict__ wo2 = wbuf(a, j + 1);
+    const T* __restrict__ wo1 = wbuf(a, j + 2);
+    T* __restrict__ wn = wbuf(a, j);
+    const T oldeps = st->w_oldeps, dlt = st->w_dlt, inv_gamma = st->w_inv_gamma, phi = st->w_phi;
+    T acc[NA];
+#pragma unroll
+    for (int t = 0; t < NA; ++t) acc[t] = T(0);
+    const int64_t n = a.rs.n, trim = a.trim;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
+    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
+        T g[VN], z[VN], y[VN], rpv[VN];
+        T dgv[VN];
+        bool ok[VN];
+        vld(a.gsum + r0, g);
+        vld(zc + r0, z);
+        vld_degree<T>(a, r0, dgv);
+        T zpv[VN], w2[VN], w1[VN], xv[VN], wv[VN];
+        if (has_prev) {
+            vld(a.rprev + r0, rpv);
+            vld(zp + r0, zpv);
+            vld(wo2 + r0, w2);
+            vld(wo1 + r0, w1);
+            vld_rw(a.x + r0, xv);
+        }
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+            const int64_t r = r0 + e;
+            ok[e] = r < n && r != trim;
+            const T degT = dgv[e];
+            T base = ((degT - sigma) * z[e] - g[e] + s_term) * inv_beta;
+            if (has_prev) {
+                base -= cprev * rpv[e];
+                const T w = (zpv[e] * inv_oldb - oldeps * w2[e] - dlt * w1[e]) * inv_gamma;
+                wv[e] = ok[e] ? w : T(0);
+                xv[e] += ok[e] ? phi * w : T(0);
+            }
+            y[e] = ok[e] ? base : T(0);
+            z[e] = ok[e] ? z[e] : T(0);
+            acc[0] += z[e] * inv_beta * y[e];
+        }
+        vst(a.Y + r0, y);
+        if (has_prev) {
+            vst(wn + r0, wv);
+            vst(a.x + r0, xv);
+        }
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {
+            if (t < c) {
+                T v[VN];
+                vld(a.Vt + (int64_t)t * a.ldv + r0, v);
+#pragma unroll
+                for (int e = 0; e < VN; ++e) acc[1 + t] += (ok[e] ? v[e] : T(0)) * z[e];
+            }
+        }
+    }
+    __shared__ T red[NA];
+    if (block_partials_arrive<T, NA>(acc, NE > 0 ? NA : 1, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, NE > 0 ? NA : 1, red, a.counter);
+        if (threadIdx.x == 0) {
+            const double bt = (double)beta, delta = (double)a.delta;
+            double al = (double)red[0];
+            for (int t = 0; t < c; ++t) {
+                const double gn = (double)red[1 + t];
+                const double u = delta * gn / bt;
+                st->g_cur[t] = (T)gn;
+                st->u1[t] = (T)u;
+                al += gn / bt * u;
+            }
+            st->alpha = (T)al;
+        }
+    }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_ml_phase2a(InnerArgs<T> a) {
+    constexpr int VN = Vec<T>::N;
+    constexpr int NE = Ncols<NC>::value;
+    InnerState<T>* st = a.st;
+    if (st->done) return;
+    const int c = st->p_c;
+    const T coef = st->alpha / st->beta;
+    __shared__ T us[NE > 0 ? NE : 1];
+    for (int t = threadIdx.x; t < c; t += blockDim.x) us[t] = st->u1[t];
+    __syncthreads();
+    const int64_t n = a.rs.n, trim = a.trim;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
+    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
+        T y[VN], rc[VN], vu[VN], rn[VN];
+        vld(a.Y + r0, y);
+        vld_rw(a.rcur + r0, rc);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) vu[e] = T(0);
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {
+            if (t < c) {
+                T v[VN];
+                vld(a.Vt + (int64_t)t * a.ldv + r0, v);
+#pragma unroll
+                for (int e = 0; e < VN; ++e) vu[e] += v[e] * us[t];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+            const int64_t r = r0 + e;
+            rn[e] = (r < n && r != trim) ? y[e] + vu[e] - coef * rc[e] : T(0);
+        }
+        vst(a.rprev + r0, rc);
+        vst(a.rcur + r0, rn);
+    }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_ml_phase2b(InnerArgs<T> a, int init, cudaGraphConditionalHandle cond,
+                                                        int has_cond) {
+    constexpr int VN = Vec<T>::N;
+    constexpr int NE = Ncols<NC>::value;
+    constexpr int NA = 2 + 2 * NE;           // r^T w, 1^T w, Vh^T w, r^T MV
+    InnerState<T>* st = a.st;
+    if (!init && st->done) {
+        if (has_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    const int k = init ? 0 : st->itn + 1;
+    const int c = st->p_c;
+    T acc[NA];
+#pragma unroll
+    for (int t = 0; t < NA; ++t) acc[t] = T(0);
+    const int64_t n = a.rs.n, trim = a.trim;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
+    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
+        T w[VN], r[VN];
+        vld(a.wv + r0, w);
+        vld(a.rcur + r0, r);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+            const bool ok = r0 + e < n && r0 + e != trim;
+            w[e] = ok ? w[e] : T(0);
+            r[e] = ok ? r[e] : T(0);
+            acc[0] += r[e] * w[e];
+            acc[1] += w[e];
+        }
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {
+            if (t < c) {
+                T v[VN], m[VN];
+                vld(a.Vt + (int64_t)t * a.ldv + r0, v);
+                vld(a.MV + (int64_t)t * a.ldv + r0, m);
+#pragma unroll
+                for (int e = 0; e < VN; ++e) {
+                    const bool ok = r0 + e < n && r0 + e != trim;
+                    acc[2 + t] += (ok ? v[e] : T(0)) * w[e];
+                    acc[2 + NE + t] += (ok ? m[e] : T(0)) * r[e];
+                }
+            }
+        }
+    }
+    __shared__ T red[NA];
+    if (block_partials_arrive<T, NA>(acc, NE > 0 ? NA : 2, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, NE > 0 ? NA : 2, red, a.counter);
+        if (threadIdx.x == 0) {
+            // t = C^{-1} Vh^T w, then the SMW-corrected r^T z and 1^T z
+            double bb = (double)red[0], ss = (double)red[1];
+            for (int p = 0; p < c; ++p) {
+                double tp = 0.0;
+                for (int q = 0; q < c; ++q) tp += a.Cinv[p + q * c] * (double)red[2 + q];
+                st->tv[p] = (T)tp;
+                bb -= (double)red[2 + NE + p] * tp;
+                ss -= a.mv1[p] * tp;
+            }
+            minres_step(a, st, (T)bb, (T)ss, init, k, cond, has_cond);
+        }
+    }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_ml_phase2c(InnerArgs<T> a, int init) {
+    constexpr int VN = Vec<T>::N;
+    constexpr int NE = Ncols<NC>::value;
+    InnerState<T>* st = a.st;
+    // also runs after the stop (from wv, into the slot of z_{itn+1}, which nothing reads then)
+    const int k = init ? 0 : st->itn;                 // phase 2b already advanced itn to k
+    T* __restrict__ zn = (k & 1) ? a.z1 : a.z0;
+    const int c = st->p_c;
+    __shared__ T ts[NE > 0 ? NE : 1];
+    for (int t = threadIdx.x; t < c; t += blockDim.x) ts[t] = st->tv[t];
+    __syncthreads();
+    const int64_t n = a.rs.n, trim = a.trim;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
+    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
+        T w[VN];
+        vld(a.wv + r0, w);
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {
+            if (t < c) {
+                T m[VN];
+                vld(a.MV + (int64_t)t * a.ldv + r0, m);
+#pragma unroll
+                for (int e = 0; e < VN; ++e) w[e] -= m[e] * ts[t];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < VN; ++e) w[e] = (r0 + e < n && r0 + e != trim) ? w[e] : T(0);
+        vst(zn + r0, w);
+    }
+}
+
+// right-hand side of a multilevel-preconditioned solve: rc = b = R / ||R|| (trimmed entry 0),
+// x = w buffers = 0, state reset
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_ml_prep(InnerArgs<T> a, const double* R, const double* rnorm_dev) {
+    const double rn = *rnorm_dev;
+    const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+    const int64_t n = a.rs.n;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        a.rcur[r] = (r == a.trim) ? T(0) : (T)(R[r] * inv);
+        a.rprev[r] = T(0);
+        a.x[r] = T(0);
+        a.wb0[r] = T(0);
+        a.wb1[r] = T(0);
+        a.wb2[r] = T(0);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        InnerState<T>* st = a.st;
+        st->p_sigma = a.sigma;
+        st->p_sig_n = a.sig_n;
+        st->p_c = a.c;
+        st->done = 0;
+        st->itn = 0;
+        st->pending = 0;
+        st->alpha = T(0);
+        st->beta = T(1);
+    }
+}
+
+// plain gather g = sum over the neighbours of x (the trimmed row gets 0); returns at once once the
+// inner solve has stopped (done != null)
+template <typename T, int G, int TPB>
+__global__ void __launch_bounds__(TPB, TPB == kThreads ? 4 : 1) k_gather_vec(RowSched rs, const T* x, T* g,
+                                                                             int64_t skip, const int* done) {
+    if (done && *done) return;
+    GatherStore<T> epi{g};
+    for_each_row_gather<T, G>(rs, x, epi, skip);
+}
+
+// C = delta^{-1} I + Vh^T MV (symmetrised), its inverse (Cholesky, FP64), and 1^T MV, for the
+// multilevel SMW preconditioner.  One CTA per row tile; the last CTA factors.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_ml_gram(InnerArgs<T> a, double* Cinv, double* mv1, double* partial,
+                                                      int pstride) {
+    const int c = a.c;
+    const int ne = c * c + c;              // all entries of Vh^T MV, then 1^T MV
+    const int64_t n = a.rs.n;
+    constexpr int kPer = 4;                // (31 * 31 + 31) / 256 < 4
+    double acc[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        if (r == a.trim) continue;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int e = threadIdx.x + q * blockDim.x;
+            if (e < c * c) {
+                const int p = e % c, s2 = e / c;
+                acc[q] += (double)a.Vt[(int64_t)p * a.ldv + r] * (double)a.MV[(int64_t)s2 * a.ldv + r];
+            } else if (e < ne) {
+                acc[q] += (double)a.MV[(int64_t)(e - c * c) * a.ldv + r];
+            }
+        }
+    }
+    for (int q = 0; q < kPer; ++q) {
+        const int e = threadIdx.x + q * blockDim.x;
+        if (e < ne) partial[(size_t)e * pstride + blockIdx.x] = acc[q];
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int last;
+    if (threadIdx.x == 0) last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __shared__ double Gs[kCMax * kCMax];
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (size_t)e * pstride + b);
+        if (e < c * c) Gs[e] = s; else mv1[e - c * c] = s;
+    }
+    if (threadIdx.x == 0) *a.counter = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double Lc[kCMax * kCMax];
+        const double dinv = 1.0 / (double)a.delta;
+        for (int s = 0; s < c; ++s) {
+            double d = 0.5 * (Gs[s + s * c] + Gs[s + s * c]) + dinv;
+            for (int t = 0; t < s; ++t) d -= Lc[s + t * c] * Lc[s + t * c];
+            d = sqrt(d > 0.0 ? d : 1e-300);
+            Lc[s + s * c] = d;
+            for (int p = s + 1; p < c; ++p) {
+                double v = 0.5 * (Gs[p + s * c] + Gs[s + p * c]);
+                for (int t = 0; t < s; ++t) v -= Lc[p + t * c] * Lc[s + t * c];
+                Lc[p + s * c] = v / d;
+            }
+        }
+        for (int col = 0; col < c; ++col) {
+            double y[kCMax];
+            for (int p = 0; p < c; ++p) {
+                double v = (p == col) ? 1.0 : 0.0;
+                for (int t = 0; t < p; ++t) v -= Lc[p + t * c] * y[t];
+                y[p] = v / Lc[p + p * c];
+            }
+            for (int p = c - 1; p >= 0; --p) {
+                double v = y[p];
+                for (int t = p + 1; t < c; ++t) v -= Lc[t + p * c] * y[t];
+                y[p] = v / Lc[p + p * c];
+            }
+            for (int p = 0; p < c; ++p) Cinv[p + col * c] = y[p];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 
 // deflation-rank buckets: the kernels keep NC per-thread accumulators, so small buckets save registers
@@ -712,7 +1145,9 @@ cudaError_t inner_gather_attrs(int bytes) {
     cudaError_t e = cudaSuccess;
 #define LA(G, TPB)                                                                                      \
     if (e == cudaSuccess)                                                                               \
-        e = cudaFuncSetAttribute(k_phase1_gather<T, G, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+        e = cudaFuncSetAttribute(k_phase1_gather<T, G, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); \
+    if (e == cudaSuccess)                                                                               \
+        e = cudaFuncSetAttribute(k_gather_vec<T, G, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
     for (int tpb : {kThreads, kBigBlock})
         for (int g : {1, 2, 4, 8, 16, 32}) ISIRA_GATHER_DISPATCH(g, tpb, LA);
 #undef LA
@@ -723,6 +1158,10 @@ cudaError_t inner_gather_attrs(int bytes) {
         if (e == cudaSuccess) e = wave_register((const void*)k_prep<T, NC>);                            \
         if (e == cudaSuccess) e = wave_register((const void*)k_opstats<T, NC>);                         \
         if (e == cudaSuccess) e = wave_register((const void*)k_apply_rows<T, NC>);                      \
+        if (e == cudaSuccess) e = wave_register((const void*)k_ml_phase1<T, NC>);                       \
+        if (e == cudaSuccess) e = wave_register((const void*)k_ml_phase2a<T, NC>);                      \
+        if (e == cudaSuccess) e = wave_register((const void*)k_ml_phase2b<T, NC>);                      \
+        if (e == cudaSuccess) e = wave_register((const void*)k_ml_phase2c<T, NC>);                      \
     } while (0)
     for (int nc : {0, 8, 12, 16, 24, 32}) ISIRA_NC_DISPATCH(nc, LW);
 #undef LW
@@ -772,6 +1211,56 @@ void inner_phase2_cond(const InnerArgs<T>& a, cudaGraphConditionalHandle cond, c
 }
 
 template <typename T>
+void inner_gather_vec(const InnerArgs<T>& a, const T* x, T* g, int lanes, const int* done, cudaStream_t s) {
+#define LGV(G, TPB) k_gather_vec<T, G, TPB><<<a.rs.grid(), TPB, a.rs.hub_bytes, s>>>(a.rs, x, g, a.trim, done)
+    ISIRA_GATHER_DISPATCH(lanes, a.rs.tpb, LGV);
+#undef LGV
+}
+
+template <typename T>
+void ml_inner_prep(const InnerArgs<T>& a, const double* R, const double* rnorm_dev, cudaStream_t s) {
+    k_ml_prep<T><<<a.ew_blocks, kThreads, 0, s>>>(a, R, rnorm_dev);
+}
+
+template <typename T>
+void ml_phase1(const InnerArgs<T>& a, cudaStream_t s) {
+#define L1(NC) k_ml_phase1<T, NC><<<wave_grid((const void*)k_ml_phase1<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a)
+    ISIRA_NC_DISPATCH(a.c, L1);
+#undef L1
+}
+
+template <typename T>
+void ml_phase2a(const InnerArgs<T>& a, cudaStream_t s) {
+#define L2(NC) k_ml_phase2a<T, NC><<<wave_grid((const void*)k_ml_phase2a<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a)
+    ISIRA_NC_DISPATCH(a.c, L2);
+#undef L2
+}
+
+template <typename T>
+void ml_phase2b(const InnerArgs<T>& a, int init, cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s) {
+#define L2(NC)                                                                                              \
+    k_ml_phase2b<T, NC><<<wave_grid((const void*)k_ml_phase2b<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a, init, \
+                                                                                                  cond, has_cond)
+    ISIRA_NC_DISPATCH(a.c, L2);
+#undef L2
+}
+
+template <typename T>
+void ml_phase2c(const InnerArgs<T>& a, int init, cudaStream_t s) {
+#define L2(NC) k_ml_phase2c<T, NC><<<wave_grid((const void*)k_ml_phase2c<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a, init)
+    ISIRA_NC_DISPATCH(a.c, L2);
+#undef L2
+}
+
+template <typename T>
+void ml_gram(const InnerArgs<T>& a, double* Cinv, double* mv1, cudaStream_t s) {
+    if (a.c <= 0) return;
+    const int ps = a.pstride / 2;                      // up to 1024 slots per block
+    const int grid = a.ew_blocks < ps ? a.ew_blocks : ps;
+    k_ml_gram<T><<<grid > 0 ? grid : 1, kThreads, 0, s>>>(a, Cinv, mv1, a.partial_d, ps);
+}
+
+template <typename T>
 void inner_prep_launch(const InnerArgs<T>& a, const double* R, const double* rnorm_dev, cudaStream_t s) {
 #define LP(NC) k_prep<T, NC><<<wave_grid((const void*)k_prep<T, NC>, a.ew_blocks), kThreads, 0, s>>>(a, R, rnorm_dev)
     ISIRA_NC_DISPATCH(a.c, LP);
@@ -810,6 +1299,13 @@ void copy_vcol(const double* src, T* dst, int64_t n, cudaStream_t s) {
 #define ISIRA_INSTANTIATE_INNER(T)                                                                        \
     template void inner_phase1<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
     template void inner_apply<T>(const InnerArgs<T>&, int, cudaStream_t);                                \
+    template void inner_gather_vec<T>(const InnerArgs<T>&, const T*, T*, int, const int*, cudaStream_t);   \
+    template void ml_inner_prep<T>(const InnerArgs<T>&, const double*, const double*, cudaStream_t);      \
+    template void ml_phase1<T>(const InnerArgs<T>&, cudaStream_t);                                       \
+    template void ml_phase2a<T>(const InnerArgs<T>&, cudaStream_t);                                      \
+    template void ml_phase2b<T>(const InnerArgs<T>&, int, cudaGraphConditionalHandle, int, cudaStream_t); \
+    template void ml_phase2c<T>(const InnerArgs<T>&, int, cudaStream_t);                                 \
+    template void ml_gram<T>(const InnerArgs<T>&, double*, double*, cudaStream_t);                       \
     template void inner_gather<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
     template void inner_rows<T>(const InnerArgs<T>&, cudaStream_t);                                      \
     template void inner_phase2<T>(const InnerArgs<T>&, int, cudaStream_t);                               \

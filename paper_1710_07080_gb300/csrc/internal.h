@@ -3,9 +3,59 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+#include <vector>
+
 #include "common.cuh"
 
 namespace isira {
+
+// host-side CUDA error propagation inside setup code
+struct CudaFailure {
+    cudaError_t e;
+};
+#define CUDA_OK(x)                                                   \
+    do {                                                             \
+        cudaError_t e_ = (x);                                        \
+        if (e_ != cudaSuccess) throw ::isira::CudaFailure{e_};       \
+    } while (0)
+
+// ------------------------------------------------------------------ multilevel preconditioner (multilevel.cu)
+template <typename T>
+struct MlLevel {
+    int64_t n = 0;
+    T* dinv = nullptr;                        // 1 / diagonal (0 at the trimmed vertex of level 0)
+    int32_t* rp = nullptr;                    // level >= 1: CSR of the off-diagonal weights
+    int32_t* ci = nullptr;
+    T* w = nullptr;
+    int32_t* agg = nullptr;                   // vertex -> cluster of the next level (-1: none)
+    int64_t* mrp = nullptr;                   // members of each cluster of the next level
+    int32_t* mem = nullptr;
+    T* b = nullptr;                           // right-hand side of this level (levels >= 1)
+    T* x0 = nullptr; T* x1 = nullptr; T* x = nullptr;   // work vectors
+};
+
+template <typename T>
+struct MlHierarchy {
+    int nlev = 0;
+    int64_t n0 = 0, skip = -1, n_coarse = 0;
+    std::vector<MlLevel<T>> lev;
+    T* inv = nullptr;                         // dense inverse of the coarsest level
+};
+
+// g = sum over the neighbours of x (level 0), on stream s
+template <typename T>
+using GatherFn = std::function<void(const T* x, T* g, cudaStream_t s)>;
+
+template <typename T>
+cudaError_t ml_build(MlHierarchy<T>& H, const int64_t* d_rp, const int32_t* d_ci, const double* d_w, int64_t n,
+                     int64_t ld, int64_t skip, cudaStream_t s);
+template <typename T> void ml_free(MlHierarchy<T>& H);
+// out = M^{-1} b, one V-cycle; kernels return at once while *done != 0 (done may be null)
+template <typename T>
+void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather, T omega, T alpha, const int* done,
+               cudaStream_t s);
+template <typename T> int ml_launches(const MlHierarchy<T>& H);
 
 // ------------------------------------------------------------------ inner solve
 // State of one preconditioned MINRES solve (Paige & Saunders 1975) kept in device
@@ -48,6 +98,11 @@ struct InnerArgs {
     HostStatus* hs;             // device alias of the mapped host status
     const double* Cinv;         // c-by-c inverse of C = delta^{-1} I + Vh^T D^{-1} Vh
     const double* Gm;           // c-by-c Vh^T D^{-1} Vh
+    // multilevel preconditioner: stored Lanczos vectors, the V-cycle output, M^{-1} Vh, 1^T M^{-1} Vh
+    T* rprev; T* rcur; T* wv;
+    const T* MV;
+    const double* mv1;
+    double* partial_d;          // the partial-sum buffer viewed as doubles (FP64 Gram sums)
     T tau; int max_it;
     int ew_blocks;              // grid of the row-elementwise kernels
 };
@@ -71,6 +126,17 @@ template <typename T> void inner_opstats(const InnerArgs<T>& a, const T* x, cuda
 template <typename T> void gram_setup(const InnerArgs<T>& a, double* G_out, double* Cinv_out, double* scratch,
                                       cudaStream_t s);
 template <typename T> void copy_vcol(const double* src, T* dst, int64_t n, cudaStream_t s);
+// multilevel-preconditioned MINRES (inner_impl.cuh)
+template <typename T> void inner_gather_vec(const InnerArgs<T>& a, const T* x, T* g, int lanes, const int* done,
+                                            cudaStream_t s);
+template <typename T> void ml_inner_prep(const InnerArgs<T>& a, const double* R, const double* rnorm_dev,
+                                         cudaStream_t s);
+template <typename T> void ml_phase1(const InnerArgs<T>& a, cudaStream_t s);
+template <typename T> void ml_phase2a(const InnerArgs<T>& a, cudaStream_t s);
+template <typename T> void ml_phase2b(const InnerArgs<T>& a, int init, cudaGraphConditionalHandle cond, int has_cond,
+                                      cudaStream_t s);
+template <typename T> void ml_phase2c(const InnerArgs<T>& a, int init, cudaStream_t s);
+template <typename T> void ml_gram(const InnerArgs<T>& a, double* Cinv, double* mv1, cudaStream_t s);
 
 // ------------------------------------------------------------------ outer loop (FP64)
 struct OuterArgs {
@@ -130,12 +196,19 @@ void setup_partition(const int64_t* rp, int64_t n, const int32_t* item_row, cons
                      int light_deg, int n_warps, int64_t* cost_tmp, int64_t* prefix_tmp, int32_t* warp_start,
                      cudaStream_t s);
 // vertex relabelling by descending degree (reorder.cu)
-cudaError_t build_reordered_graph(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int64_t maxdeg,
-                                  int64_t* rp2, int32_t* ci2, int32_t* perm, int32_t* inv, cudaStream_t s);
+// (weights w, if not null, follow their edges into w2)
+cudaError_t build_reordered_graph(const int64_t* rp, const int32_t* ci, const double* w, int64_t n, int64_t nnz,
+                                  int64_t maxdeg, int64_t* rp2, int32_t* ci2, double* w2, int32_t* perm, int32_t* inv,
+                                  cudaStream_t s);
 // sliced ELL copy of the light rows [light0, n): off (n_slices + 1 entries, caller-allocated) receives
 // the slice offsets, *sci a new device array of *total entries (-1 padding)
-cudaError_t build_sell(const int64_t* rp, const int32_t* ci, int64_t n, int64_t light0, int64_t n_slices,
-                       int64_t* off, int32_t** sci, int64_t* total, cudaStream_t s);
+cudaError_t build_sell(const int64_t* rp, const int32_t* ci, const double* w, int64_t n, int64_t light0,
+                       int64_t n_slices, int64_t* off, int32_t** sci, double** sw, int64_t* total, cudaStream_t s);
+// weighted degrees dw[r] = sum of the row's weights (r < n; 0 for n <= r < ld) and their FP32 copy;
+// wf = FP32 copy of the nnz weights (either may be null)
+void setup_weighted(const int64_t* rp, const double* w, int64_t n, int64_t ld, int64_t nnz, double* dw, float* dwf,
+                    float* wf, cudaStream_t s);
+template <typename T> void copy_cast(const double* src, T* dst, int64_t count, cudaStream_t s);
 template <typename T> void to_internal(const T* src, const int32_t* perm, int64_t n, T* dst, cudaStream_t s);
 template <typename T> void to_external(const T* src, const int32_t* perm, int64_t n, T* dst, cudaStream_t s);
 int validate_csr(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int* d_flag, cudaStream_t s);

@@ -492,13 +492,13 @@ __global__ void __launch_bounds__(kThreads) k_expand_rows(OuterArgs a, int k) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += (int64_t)gridDim.x * blockDim.x) {
         const double ur = a.Z[r] * inv;
         u[r] = ur;
-        w[r] = (double)(a.rs.rp[r + 1] - a.rs.rp[r]) * ur - a.gsum[r] * inv;
+        w[r] = row_degree<double>(a.rs, r) * ur - a.gsum[r] * inv;
     }
 }
 
 __global__ void __launch_bounds__(kThreads) k_laplacian_rows(OuterArgs a, const double* x, double* y) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += (int64_t)gridDim.x * blockDim.x)
-        y[r] = (double)(a.rs.rp[r + 1] - a.rs.rp[r]) * x[r] - a.gsum[r];
+        y[r] = row_degree<double>(a.rs, r) * x[r] - a.gsum[r];
 }
 
 static void outer_gather(const OuterArgs& a, const double* x, int lanes, cudaStream_t s) {
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(kThreads) k_trueres_rows(OuterArgs a, const do
     const double lam = lam_dev[j];
     double acc[1] = {0.0};
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += (int64_t)gridDim.x * blockDim.x) {
-        const double d = (double)(a.rs.rp[r + 1] - a.rs.rp[r]) * v[r] - a.gsum[r] - lam * v[r];
+        const double d = row_degree<double>(a.rs, r) * v[r] - a.gsum[r] - lam * v[r];
         acc[0] += d * d;
     }
     if (block_partials_arrive<double, 1>(acc, 1, a.partial, a.pstride, a.counter)) {
@@ -856,6 +856,37 @@ __global__ void __launch_bounds__(kThreads) k_deg32(const int64_t* rp, int64_t n
 
 void setup_deg32(const int64_t* rp, int64_t n, int64_t ld, int32_t* deg, cudaStream_t s) {
     k_deg32<<<1024, kThreads, 0, s>>>(rp, n, ld, deg);
+}
+
+// weighted Laplacian: degrees as weight sums (FP64 and FP32), FP32 copy of the weights
+__global__ void __launch_bounds__(kThreads) k_weighted_degrees(const int64_t* rp, const double* w, int64_t n, int64_t ld,
+                                                               double* dw, float* dwf) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < ld; r += (int64_t)gridDim.x * blockDim.x) {
+        double sum = 0.0;
+        if (r < n)
+            for (int64_t e = rp[r]; e < rp[r + 1]; ++e) sum += w[e];
+        dw[r] = sum;
+        if (dwf) dwf[r] = (float)sum;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_copy_cast(const double* src, T* dst, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (T)src[i];
+}
+
+template <typename T>
+void copy_cast(const double* src, T* dst, int64_t count, cudaStream_t s) {
+    k_copy_cast<T><<<2048, kThreads, 0, s>>>(src, dst, count);
+}
+template void copy_cast<float>(const double*, float*, int64_t, cudaStream_t);
+template void copy_cast<double>(const double*, double*, int64_t, cudaStream_t);
+
+void setup_weighted(const int64_t* rp, const double* w, int64_t n, int64_t ld, int64_t nnz, double* dw, float* dwf,
+                    float* wf, cudaStream_t s) {
+    k_weighted_degrees<<<1024, kThreads, 0, s>>>(rp, w, n, ld, dw, dwf);
+    if (wf) copy_cast<float>(w, wf, nnz, s);
 }
 
 // ------------------------------------------------------------------ balanced work partition

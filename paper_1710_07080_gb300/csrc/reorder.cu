@@ -28,17 +28,20 @@ __global__ void k_new_degrees(const int64_t* rp, const int32_t* perm, int64_t n,
     }
 }
 
-// one warp per new row: copy the old row's neighbours, renamed
-__global__ void __launch_bounds__(kThreads) k_permute_cols(const int64_t* rp, const int32_t* ci, const int32_t* perm,
-                                                           const int32_t* inv, const int64_t* rp2, int64_t n,
-                                                           int32_t* ci2) {
+// one warp per new row: copy the old row's neighbours, renamed (and their weights, if any)
+__global__ void __launch_bounds__(kThreads) k_permute_cols(const int64_t* rp, const int32_t* ci, const double* w,
+                                                           const int32_t* perm, const int32_t* inv, const int64_t* rp2,
+                                                           int64_t n, int32_t* ci2, double* w2) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = w0; i < n; i += nw) {
         const int64_t o = perm[i];
         const int64_t b = rp[o], d = rp[o + 1] - b, b2 = rp2[i];
-        for (int64_t j = lane; j < d; j += 32) ci2[b2 + j] = inv[ci[b + j]];
+        for (int64_t j = lane; j < d; j += 32) {
+            ci2[b2 + j] = inv[ci[b + j]];
+            if (w) w2[b2 + j] = w[b + j];
+        }
     }
 }
 
@@ -54,8 +57,9 @@ __global__ void k_scatter_perm(const T* src, const int32_t* perm, int64_t n, T* 
         dst[perm[i]] = src[i];
 }
 
-cudaError_t build_reordered_graph(const int64_t* rp, const int32_t* ci, int64_t n, int64_t nnz, int64_t maxdeg,
-                                  int64_t* rp2, int32_t* ci2, int32_t* perm, int32_t* inv, cudaStream_t s) {
+cudaError_t build_reordered_graph(const int64_t* rp, const int32_t* ci, const double* w, int64_t n, int64_t nnz,
+                                  int64_t maxdeg, int64_t* rp2, int32_t* ci2, double* w2, int32_t* perm, int32_t* inv,
+                                  cudaStream_t s) {
     uint32_t *k0 = nullptr, *k1 = nullptr;
     int32_t* v0 = nullptr;
     int64_t* deg = nullptr;
@@ -76,7 +80,7 @@ cudaError_t build_reordered_graph(const int64_t* rp, const int32_t* ci, int64_t 
     CK(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k0, k1, v0, perm, (int)n, 0, 32, s));
     k_new_degrees<<<grid, kThreads, 0, s>>>(rp, perm, n, deg, inv);
     CK(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, deg, rp2, (int)(n + 1), s));
-    k_permute_cols<<<grid, kThreads, 0, s>>>(rp, ci, perm, inv, rp2, n, ci2);
+    k_permute_cols<<<grid, kThreads, 0, s>>>(rp, ci, w, perm, inv, rp2, n, ci2, w2);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
 #undef CK
@@ -110,23 +114,27 @@ __global__ void __launch_bounds__(kThreads) k_sell_widths(const int64_t* rp, int
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_sell_fill(const int64_t* rp, const int32_t* ci, int64_t n,
-                                                        int64_t light0, int64_t n_slices, const int64_t* off,
-                                                        int32_t* sci) {
+__global__ void __launch_bounds__(kThreads) k_sell_fill(const int64_t* rp, const int32_t* ci, const double* w,
+                                                        int64_t n, int64_t light0, int64_t n_slices, const int64_t* off,
+                                                        int32_t* sci, double* sw) {
     const int64_t total = n_slices * 32;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = t >> 5, lane = t & 31;
         const int64_t row = light0 + t;
-        const int64_t w = (off[s + 1] - off[s]) >> 5;
+        const int64_t wid = (off[s + 1] - off[s]) >> 5;
         const int64_t b = row < n ? rp[row] : 0;
         const int64_t d = row < n ? rp[row + 1] - b : 0;
-        for (int64_t q = 0; q < w; ++q) sci[off[s] + 32 * q + lane] = q < d ? ci[b + q] : -1;
+        for (int64_t q = 0; q < wid; ++q) {
+            sci[off[s] + 32 * q + lane] = q < d ? ci[b + q] : -1;
+            if (w) sw[off[s] + 32 * q + lane] = q < d ? w[b + q] : 0.0;
+        }
     }
 }
 
-cudaError_t build_sell(const int64_t* rp, const int32_t* ci, int64_t n, int64_t light0, int64_t n_slices,
-                       int64_t* off, int32_t** sci, int64_t* total, cudaStream_t s) {
+cudaError_t build_sell(const int64_t* rp, const int32_t* ci, const double* w, int64_t n, int64_t light0,
+                       int64_t n_slices, int64_t* off, int32_t** sci, double** sw, int64_t* total, cudaStream_t s) {
     *sci = nullptr;
+    if (sw) *sw = nullptr;
     *total = 0;
     int64_t* w32 = nullptr;
     void* tmp = nullptr;
@@ -141,7 +149,8 @@ cudaError_t build_sell(const int64_t* rp, const int32_t* ci, int64_t n, int64_t 
     CK(cudaMemcpyAsync(total, off + n_slices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CK(cudaMalloc(sci, sizeof(int32_t) * (size_t)(*total > 0 ? *total : 1)));
-    if (*total > 0) k_sell_fill<<<2048, kThreads, 0, s>>>(rp, ci, n, light0, n_slices, off, *sci);
+    if (w) CK(cudaMalloc(sw, sizeof(double) * (size_t)(*total > 0 ? *total : 1)));
+    if (*total > 0) k_sell_fill<<<2048, kThreads, 0, s>>>(rp, ci, w, n, light0, n_slices, off, *sci, w ? *sw : nullptr);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
 #undef CK

@@ -41,6 +41,10 @@ template <typename T>
 struct InnerBuffers {
     T* base = nullptr;
     InnerState<T>* st = nullptr;
+    // multilevel preconditioner: 3 n-vectors (r_{k-1}, r_k, V-cycle output) then kCMax columns M^{-1} Vh
+    T* ml = nullptr;
+    int mv_count = 0;                 // columns of M^{-1} Vh valid for the current deflation basis
+    MlHierarchy<T> H;
 };
 
 }  // namespace
@@ -61,6 +65,15 @@ struct isira_handle_s {
     unsigned* item_count = nullptr;
     int32_t* warp_start = nullptr;
     int32_t* deg32 = nullptr;      // degree per row (solver numbering), ld entries
+    // weighted Laplacian (null: unit weights): the caller's weights, the solver's relabelled copy,
+    // FP32 copies, weighted degrees, and the weights of the sliced copy
+    const double* w_user = nullptr;
+    double* own_w = nullptr;
+    float* wf = nullptr;
+    double* degwd = nullptr;
+    float* degwf = nullptr;
+    double* sell_wd = nullptr;
+    float* sell_wf = nullptr;
     int64_t* sell_off = nullptr;   // sliced ELL copy of the light rows (with relabelling)
     int32_t* sell_ci = nullptr;
     int64_t sell_total = 0;
@@ -110,6 +123,9 @@ struct isira_handle_s {
     // device-driven inner loop: one instantiated graph per deflation-rank bucket (c = 0, <=8, <=12, <=16, <=24, <=32)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t inner_graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t ml_graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double* ml_cinv = nullptr;        // kCMax x kCMax: C^{-1} of the multilevel SMW preconditioner
+    double* ml_mv1 = nullptr;         // kCMax: 1^T M^{-1} Vh
     int pending_inner_stats = 0;
 };
 
@@ -150,8 +166,16 @@ InnerArgs<T> make_args(isira_handle h, InnerBuffers<T>& b, double sigma, int c, 
     a.counter = h->counter;
     a.st = b.st;
     a.hs = h->hs_dev;
-    a.Cinv = h->Cinv;
+    a.Cinv = h->opts.precond == 1 ? h->ml_cinv : h->Cinv;
     a.Gm = h->Gm;
+    a.partial_d = h->partial;
+    if (b.ml) {
+        a.rprev = b.ml;
+        a.rcur = b.ml + ld;
+        a.wv = b.ml + 2 * ld;
+        a.MV = b.ml + 3 * ld;
+        a.mv1 = h->ml_mv1;
+    }
     a.tau = (T)tau;
     a.max_it = max_it;
     a.ew_blocks = h->ew_blocks;
@@ -223,8 +247,14 @@ cudaGraphExec_t build_inner_graph(isira_handle h, const InnerArgs<T>& a) {
 // One inner solve on R (right-hand side) into Z (FP64, back-mapped).  Chunked mode returns the
 // iteration count; graph mode returns -1 (the count is read at the next synchronisation).
 template <typename T>
+int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* Vt, int64_t ldv, double tau,
+                 int max_it, bool gram_dirty, const double* R, const double* rnorm_dev, bool allow_graph);
+
+template <typename T>
 int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* Vt, int64_t ldv, double tau,
               int max_it, bool gram_dirty, const double* R, const double* rnorm_dev, bool allow_graph = false) {
+    if (h->opts.precond == 1)
+        return run_inner_ml<T>(h, b, sigma, c, Vt, ldv, tau, max_it, gram_dirty, R, rnorm_dev, allow_graph);
     InnerArgs<T> a = make_args<T>(h, b, sigma, c, Vt, ldv, tau, max_it);
     cudaStream_t s = h->stream;
     if (gram_dirty && c > 0) {
@@ -287,6 +317,150 @@ int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* 
     return its;
 }
 
+// ------------------------------------------------------------------ multilevel-preconditioned inner solve
+constexpr double kMlOmega = 2.0 / 3.0;     // damping of the Jacobi smoother of the V-cycle
+
+template <typename T>
+void ensure_ml(isira_handle h, InnerBuffers<T>& b) {
+    if (!b.ml) {
+        const size_t elems = (size_t)h->ld * (3 + kCMax);
+        ck(cudaMalloc(&b.ml, sizeof(T) * elems));
+        ck(cudaMemsetAsync(b.ml, 0, sizeof(T) * elems, h->stream));
+        b.mv_count = 0;
+    }
+    if (!h->ml_cinv) {
+        ck(cudaMalloc(&h->ml_cinv, sizeof(double) * kCMax * kCMax));
+        ck(cudaMalloc(&h->ml_mv1, sizeof(double) * kCMax));
+    }
+    if (b.H.nlev == 0) ck(ml_build<T>(b.H, h->rs.rp, h->rs.ci, h->rs.wd, h->n, h->ld, h->trim, h->stream));
+}
+
+template <typename T>
+T ml_alpha(isira_handle h) { return (T)(h->opts.ml_alpha > 0.0 ? h->opts.ml_alpha : 1.5); }
+
+// body of one multilevel MINRES iteration (graph capture or chunked launches)
+template <typename T>
+void ml_iteration(isira_handle h, InnerBuffers<T>& b, const InnerArgs<T>& a, cudaGraphConditionalHandle cond,
+                  int has_cond, cudaStream_t s) {
+    const int* done = &a.st->done;
+    GatherFn<T> gather = [&](const T* x, T* g, cudaStream_t st) { inner_gather_vec<T>(a, x, g, h->lanes, done, st); };
+    inner_gather<T>(a, h->lanes, s);
+    ml_phase1<T>(a, s);
+    ml_phase2a<T>(a, s);
+    ml_vcycle<T>(b.H, a.rcur, a.wv, gather, (T)kMlOmega, ml_alpha<T>(h), done, s);
+    ml_phase2b<T>(a, 0, cond, has_cond, s);
+    ml_phase2c<T>(a, 0, s);
+}
+
+template <typename T>
+cudaGraphExec_t build_ml_graph(isira_handle h, InnerBuffers<T>& b, const InnerArgs<T>& a) {
+    if (!h->cap_stream) ck(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    ck(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hc;
+    ck(cudaGraphConditionalHandleCreate(&hc, g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hc;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    ck(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    ck(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    ml_iteration<T>(h, b, a, hc, 1, h->cap_stream);
+    ck(cudaStreamEndCapture(h->cap_stream, &body));
+    cudaGraphExec_t ex = nullptr;
+    ck(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    return ex;
+}
+
+template <typename T>
+int ml_launches_per_iteration(const InnerBuffers<T>& b) { return 5 + ml_launches(b.H) + 2; }
+
+// One inner solve with the multilevel preconditioner; same contract as run_inner.
+template <typename T>
+int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* Vt, int64_t ldv, double tau,
+                 int max_it, bool gram_dirty, const double* R, const double* rnorm_dev, bool allow_graph) {
+    ensure_ml(h, b);
+    InnerArgs<T> a = make_args<T>(h, b, sigma, c, Vt, ldv, tau, max_it);
+    cudaStream_t s = h->stream;
+    GatherFn<T> gather0 = [&](const T* x, T* g, cudaStream_t st) { inner_gather_vec<T>(a, x, g, h->lanes, nullptr, st); };
+    if (c > 0 && (gram_dirty || b.mv_count < c)) {
+        // M^{-1} Vh for the columns added since (M does not depend on sigma), then C^{-1}, 1^T M^{-1} Vh
+        if (b.mv_count > c) b.mv_count = 0;
+        for (int t = b.mv_count; t < c; ++t) {
+            ml_vcycle<T>(b.H, Vt + (size_t)t * ldv, b.ml + (size_t)(3 + t) * h->ld, gather0, (T)kMlOmega,
+                         ml_alpha<T>(h), nullptr, s);
+            h->stats.kernel_launches += ml_launches(b.H);
+        }
+        b.mv_count = c;
+        ml_gram<T>(a, h->ml_cinv, h->ml_mv1, s);
+        h->stats.kernel_launches += 1;
+    }
+    ml_inner_prep<T>(a, R, rnorm_dev, s);
+    ml_vcycle<T>(b.H, a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), nullptr, s);
+    ml_phase2b<T>(a, 1, cudaGraphConditionalHandle{}, 0, s);
+    ml_phase2c<T>(a, 1, s);
+    h->stats.kernel_launches += 3 + ml_launches(b.H);
+    if (allow_graph && h->opts.inner_graph && !h->profiling) {
+        const int bkt = nc_bucket(c);
+        if (!h->ml_graph[bkt]) h->ml_graph[bkt] = build_ml_graph<T>(h, b, a);
+        ck(cudaGraphLaunch(h->ml_graph[bkt], s));
+        inner_finalize_to<T>(a, h->Z, s);
+        h->stats.kernel_launches += 1;
+        h->stats.inner_solves += 1;
+        h->pending_inner_stats = ml_launches_per_iteration(b);
+        return -1;
+    }
+    const int chunk = h->opts.inner_chunk > 0 ? h->opts.inner_chunk : 16;
+    int launched = 0;
+    const int per_it = ml_launches_per_iteration(b);
+    while (true) {
+        const bool prof = h->profiling != 0;
+        for (int i = 0; i < chunk; ++i) {
+            if (prof) ck(cudaEventRecord(h->ev[4 * i], s));
+            inner_gather<T>(a, h->lanes, s);
+            if (prof) ck(cudaEventRecord(h->ev[4 * i + 1], s));
+            ml_phase1<T>(a, s);
+            if (prof) ck(cudaEventRecord(h->ev[4 * i + 2], s));
+            ml_phase2a<T>(a, s);
+            ml_vcycle<T>(b.H, a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), &a.st->done, s);
+            ml_phase2b<T>(a, 0, cudaGraphConditionalHandle{}, 0, s);
+            ml_phase2c<T>(a, 0, s);
+            if (prof) ck(cudaEventRecord(h->ev[4 * i + 3], s));
+        }
+        h->stats.spmv_launches += chunk;
+        h->stats.kernel_launches += (long long)per_it * chunk;
+        sync(h);
+        const int itn = hst(h)->inner_iters;
+        if (prof) {
+            for (int i = 0; i < chunk; ++i) {
+                if (launched + i + 1 > itn) break;
+                float ms = 0.f, ms_rows = 0.f, ms_p2 = 0.f;
+                ck(cudaEventElapsedTime(&ms, h->ev[4 * i], h->ev[4 * i + 1]));
+                ck(cudaEventElapsedTime(&ms_rows, h->ev[4 * i + 1], h->ev[4 * i + 2]));
+                ck(cudaEventElapsedTime(&ms_p2, h->ev[4 * i + 2], h->ev[4 * i + 3]));
+                h->stats.inner_phase1_ms += ms;
+                h->stats.inner_rows_ms += ms_rows;
+                h->stats.inner_phase2_ms += ms_p2;
+                h->stats.inner_phase1_timed += 1;
+                h->stats.inner_phase1_csum += c;
+            }
+        }
+        launched += chunk;
+        if (hst(h)->inner_done) break;
+        if (launched > max_it + 2 * chunk) break;
+    }
+    inner_finalize_to<T>(a, h->Z, s);
+    h->stats.kernel_launches += 1;
+    h->stats.inner_solves += 1;
+    const int its = hst(h)->inner_iters;
+    h->stats.inner_iters += its;
+    return its;
+}
+
 void ensure_outer(isira_handle h, int m, int d) {
     const size_t ld = (size_t)h->ld;
     if (m > h->m_alloc) {
@@ -321,7 +495,7 @@ bool expand_basis(isira_handle h, int k, int c) {
             const int its = hst(h)->inner_iters;
             h->stats.inner_iters += its;
             h->stats.spmv_launches += its;
-            h->stats.kernel_launches += 3 * its;
+            h->stats.kernel_launches += (long long)(h->pending_inner_stats > 1 ? h->pending_inner_stats : 3) * its;
             h->pending_inner_stats = 0;
         }
         const double zin = hst(h)->cgs_in, zout = hst(h)->cgs_out;
@@ -464,12 +638,16 @@ void autotune_gather(isira_handle h) {
 
 void free_handle(isira_handle h) {
     if (!h) return;
-    void* ptrs[] = {h->gsum, h->deg32, h->sell_off, h->sell_ci, h->own_rp, h->own_ci, h->perm, h->inv, h->item_row, h->item_k, h->item_partial,
+    void* ptrs[] = {h->own_w, h->wf, h->degwd, h->degwf, h->sell_wd, h->sell_wf, h->gsum, h->deg32, h->sell_off, h->sell_ci, h->own_rp, h->own_ci, h->perm, h->inv, h->item_row, h->item_k, h->item_partial,
                     h->item_count, h->warp_start, h->U, h->W, h->V, h->H, h->theta, h->S, h->R, h->Z, h->dscratch,
                     h->partial, h->counter, h->Gm, h->Cinv, h->lam_dev, h->tres_dev, h->fb.base, h->fb.st,
-                    h->db.base, h->db.st, h->Vt_f};
+                    h->db.base, h->db.st, h->Vt_f, h->fb.ml, h->db.ml, h->ml_cinv, h->ml_mv1};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    ml_free(h->fb.H);
+    ml_free(h->db.H);
+    for (cudaGraphExec_t g : h->ml_graph)
+        if (g) cudaGraphExecDestroy(g);
     if (h->hs) cudaFreeHost(h->hs);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     for (cudaGraphExec_t g : h->inner_graph)
@@ -527,6 +705,25 @@ void apply_operator_t(isira_handle h, InnerBuffers<T>& b, double sigma, int c, c
 
 }  // namespace
 
+namespace {
+template <typename T>
+void precond_apply_t(isira_handle h, InnerBuffers<T>& b, const T* d_x, T* d_y) {
+    cudaStream_t s = h->stream;
+    alloc_inner(h, b);
+    ensure_ml(h, b);
+    InnerArgs<T> a = make_args<T>(h, b, 0.0, 0, nullptr, h->ld, 1e-3, 1);
+    T* xin = a.rcur;
+    T* yout = a.wv;
+    if (h->perm) to_internal<T>(d_x, h->perm, h->n, xin, s);
+    else ck(cudaMemcpyAsync(xin, d_x, sizeof(T) * h->n, cudaMemcpyDeviceToDevice, s));
+    GatherFn<T> gather = [&](const T* x, T* g, cudaStream_t st) { inner_gather_vec<T>(a, x, g, h->lanes, nullptr, st); };
+    ml_vcycle<T>(b.H, xin, yout, gather, (T)kMlOmega, ml_alpha<T>(h), nullptr, s);
+    if (h->perm) to_external<T>(yout, h->perm, h->n, d_y, s);
+    else ck(cudaMemcpyAsync(d_y, yout, sizeof(T) * h->n, cudaMemcpyDeviceToDevice, s));
+    sync(h);
+}
+}  // namespace
+
 extern "C" {
 
 void isira_default_opts(isira_opts* o) {
@@ -554,6 +751,8 @@ void isira_default_opts(isira_opts* o) {
     o->index_vec = 0;
     o->gather_chunk = 0;
     o->sell = 1;
+    o->precond = 0;
+    o->ml_alpha = 0.0;
 }
 
 const char* isira_error_string(isira_status s) {
@@ -574,6 +773,12 @@ const char* isira_error_string(isira_status s) {
 
 isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64_t* d_row_ptr,
                           const int32_t* d_col_idx, const isira_opts* opts, void* stream) {
+    return isira_create_weighted(out, n, nnz, d_row_ptr, d_col_idx, nullptr, opts, stream);
+}
+
+isira_status isira_create_weighted(isira_handle* out, int64_t n, int64_t nnz, const int64_t* d_row_ptr,
+                                   const int32_t* d_col_idx, const double* d_weights, const isira_opts* opts,
+                                   void* stream) {
     if (!out) return ISIRA_ERR_INVALID_ARG;
     *out = nullptr;
     if (n < 3 || nnz < 2 || nnz > ((int64_t)1 << 40) || !d_row_ptr || !d_col_idx || n > INT32_MAX)
@@ -586,8 +791,10 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         h->ld = (n + 31) / 32 * 32;
         h->rp = d_row_ptr;
         h->ci = d_col_idx;
+        h->w_user = d_weights;
         h->stream = (cudaStream_t)stream;
         if (opts) h->opts = *opts; else isira_default_opts(&h->opts);
+        const double* d_w = d_weights;
         if (h->opts.precision != ISIRA_FP64 && h->opts.precision != ISIRA_MIXED) throw StatusError{ISIRA_ERR_INVALID_ARG};
         int dev = 0;
         ck(cudaGetDevice(&dev));
@@ -615,8 +822,9 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
             ck(cudaMemsetAsync(h->own_ci + nnz, 0, sizeof(int32_t) * (nnz_pad - (size_t)nnz), s));
             ck(cudaMalloc(&h->perm, sizeof(int32_t) * (size_t)n));
             ck(cudaMalloc(&h->inv, sizeof(int32_t) * (size_t)n));
-            ck(build_reordered_graph(d_row_ptr, d_col_idx, n, nnz, di.max_degree, h->own_rp, h->own_ci, h->perm,
-                                     h->inv, s));
+            if (d_weights) ck(cudaMalloc(&h->own_w, sizeof(double) * (size_t)nnz));
+            ck(build_reordered_graph(d_row_ptr, d_col_idx, d_weights, n, nnz, di.max_degree, h->own_rp, h->own_ci,
+                                     h->own_w, h->perm, h->inv, s));
             if (h->opts.trim_index >= 0 && h->opts.trim_index < n) {
                 int32_t t = 0;
                 ck(cudaMemcpy(&t, h->inv + h->opts.trim_index, sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -625,6 +833,7 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
             }
             d_row_ptr = h->own_rp;
             d_col_idx = h->own_ci;
+            if (d_weights) d_w = h->own_w;
             h->rp = d_row_ptr;
             h->ci = d_col_idx;
         }
@@ -640,6 +849,35 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         cudaFree(scratch);
         h->max_degree = di.max_degree;
         if (di.max_degree < 1) throw StatusError{ISIRA_ERR_BAD_GRAPH};
+        double maxdiag = (double)di.max_degree;       // largest diagonal entry of L (Remark 4.1)
+        if (d_w) {
+            // weighted Laplacian: diagonal = weight sums; trimmed vertex = largest diagonal entry
+            // (smallest vertex id of the caller's numbering on ties)
+            ck(cudaMalloc(&h->degwd, sizeof(double) * (size_t)h->ld));
+            ck(cudaMalloc(&h->degwf, sizeof(float) * (size_t)h->ld));
+            ck(cudaMalloc(&h->wf, sizeof(float) * (size_t)std::max<int64_t>(1, nnz)));
+            setup_weighted(d_row_ptr, d_w, n, h->ld, nnz, h->degwd, h->degwf, h->wf, s);
+            std::vector<double> dw((size_t)n);
+            std::vector<int32_t> pm;
+            ck(cudaMemcpyAsync(dw.data(), h->degwd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
+            if (h->perm) {
+                pm.resize((size_t)n);
+                ck(cudaMemcpyAsync(pm.data(), h->perm, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+            }
+            sync(h);
+            int64_t best = -1, best_user = -1;
+            maxdiag = 0.0;
+            for (int64_t r = 0; r < n; ++r) {
+                const int64_t ru = h->perm ? (int64_t)pm[(size_t)r] : r;
+                if (!(dw[(size_t)r] > 0.0)) throw StatusError{ISIRA_ERR_BAD_GRAPH};
+                if (dw[(size_t)r] > maxdiag || (dw[(size_t)r] == maxdiag && ru < best_user)) {
+                    maxdiag = dw[(size_t)r];
+                    best = r;
+                    best_user = ru;
+                }
+            }
+            di.argmax = best;
+        }
         h->trim = (h->opts.trim_index >= 0 && h->opts.trim_index < n) ? h->opts.trim_index : di.argmax;
         h->trim_user = h->trim;
         if (h->perm) {
@@ -648,8 +886,8 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
             h->trim_user = t;
             if (user_trim >= 0) h->opts.trim_index = user_trim;
         }
-        h->delta = h->opts.delta > 0.0 ? h->opts.delta : 2.0 * (double)di.max_degree;
-        h->normL = 2.0 * (double)di.max_degree;
+        h->delta = h->opts.delta > 0.0 ? h->opts.delta : 2.0 * maxdiag;
+        h->normL = 2.0 * maxdiag;
         h->n_long = di.n_long;
         h->n_items = di.n_items;
         if (di.n_items > INT32_MAX) throw StatusError{ISIRA_ERR_INVALID_ARG};
@@ -663,7 +901,11 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         rs.item_count = h->item_count;
         rs.n_items = (int)di.n_items;
         rs.light_deg = light_deg;
-        rs.ci_vec = h->own_ci != nullptr && h->opts.index_vec == 1;
+        rs.ci_vec = h->own_ci != nullptr && h->opts.index_vec == 1 && !d_w;
+        rs.wd = d_w;
+        rs.wf = h->wf;
+        rs.degwd = h->degwd;
+        rs.degwf = h->degwf;
         rs.chunk = (h->opts.gather_chunk >= 1 && h->opts.gather_chunk <= 32) ? h->opts.gather_chunk : kUnitChunk;
         // sliced ELL copy of the light rows: the degree-descending numbering puts the long rows first
         rs.sell = 0;
@@ -673,7 +915,14 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
             const int64_t ns = (n - di.n_long + 31) / 32;
             if (ns > INT32_MAX / 2) throw StatusError{ISIRA_ERR_INVALID_ARG};
             ck(cudaMalloc(&h->sell_off, sizeof(int64_t) * (size_t)(ns + 1)));
-            ck(build_sell(d_row_ptr, d_col_idx, n, di.n_long, ns, h->sell_off, &h->sell_ci, &h->sell_total, s));
+            ck(build_sell(d_row_ptr, d_col_idx, d_w, n, di.n_long, ns, h->sell_off, &h->sell_ci,
+                          d_w ? &h->sell_wd : nullptr, &h->sell_total, s));
+            if (d_w) {
+                ck(cudaMalloc(&h->sell_wf, sizeof(float) * (size_t)std::max<int64_t>(1, h->sell_total)));
+                copy_cast<float>(h->sell_wd, h->sell_wf, h->sell_total, s);
+                rs.swd = h->sell_wd;
+                rs.swf = h->sell_wf;
+            }
             rs.sell_ci = h->sell_ci;
             rs.sell_off = h->sell_off;
             rs.n_slices = (int)ns;
@@ -726,11 +975,16 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         ck(cudaHostGetDevicePointer((void**)&h->hs_dev, h->hs, 0));
         h->rs.err = &h->hs_dev->dev_error;
         if (h->opts.precision == ISIRA_MIXED) alloc_inner(h, h->fb); else alloc_inner(h, h->db);
+        if (h->opts.precond != 0 && h->opts.precond != 1) throw StatusError{ISIRA_ERR_INVALID_ARG};
         int chunk = h->opts.inner_chunk > 0 ? h->opts.inner_chunk : 16;
         h->ev.resize(4 * chunk);
         for (auto& e : h->ev) ck(cudaEventCreate(&e));
         sync(h);
         autotune_gather(h);
+        if (h->opts.precond == 1) {
+            if (h->opts.precision == ISIRA_MIXED) ensure_ml(h, h->fb); else ensure_ml(h, h->db);
+            sync(h);
+        }
         if (!rs.dyn) {   // static partition of the CSR work units for the chosen shape
             const int64_t n_units = rs.n_units();
             int64_t* cost = nullptr;
@@ -755,6 +1009,7 @@ isira_status isira_create(isira_handle* out, int64_t n, int64_t nnz, const int64
         h->stats.gather_block = h->rs.tpb;
         h->stats.hub_bytes = h->rs.hub_bytes;
         h->stats.sell_entries = h->sell_total;
+        h->stats.max_diag = maxdiag;
     } catch (CudaError& e) {
         isira_status st = map_cuda(e.e);
         free_handle(h);
@@ -826,6 +1081,8 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         h->stats.kernel_launches = 0;
         (void)keep;
         h->lam.assign(d, 0.0);
+        h->fb.mv_count = 0;
+        h->db.mv_count = 0;
         OuterArgs oa = make_outer(h);
         ck(cudaMemsetAsync(h->H, 0, sizeof(double) * kMMax * kMMax, s));
         // start basis U_{k0}, k0 = 1 (Algorithm 2 REQUIRE): the given vector, or a SplitMix64 one
@@ -990,6 +1247,8 @@ isira_status isira_inner_solve(isira_handle h, int precision, double sigma, int 
         const double one = 1.0;
         ck(cudaMemcpyAsync(h->dscratch + 300, &one, sizeof(double), cudaMemcpyHostToDevice, s));
         int its = 0;
+        h->fb.mv_count = 0;          // the deflation basis of this call is new
+        h->db.mv_count = 0;
         if (precision == ISIRA_MIXED) {
             alloc_inner(h, h->fb);
             float* Vt = internal_V<float>(h, d_V, c, s);
@@ -1011,6 +1270,29 @@ isira_status isira_inner_solve(isira_handle h, int precision, double sigma, int 
         sync(h);
         if (iters) *iters = its;
         if (relres) *relres = hst(h)->inner_relres;
+    } catch (CudaError& e) {
+        return map_cuda(e.e);
+    } catch (StatusError& e) {
+        return e.s;
+    }
+    return ISIRA_OK;
+}
+
+
+isira_status isira_precond_apply(isira_handle h, int precision, const void* d_x, void* d_y, int* levels,
+                                 int64_t* coarse_n) {
+    if (!h || !d_x || !d_y || (precision != ISIRA_FP64 && precision != ISIRA_MIXED)) return ISIRA_ERR_INVALID_ARG;
+    clear_dev_error(h);
+    try {
+        if (precision == ISIRA_MIXED) {
+            precond_apply_t<float>(h, h->fb, static_cast<const float*>(d_x), static_cast<float*>(d_y));
+            if (levels) *levels = h->fb.H.nlev;
+            if (coarse_n) *coarse_n = h->fb.H.n_coarse;
+        } else {
+            precond_apply_t<double>(h, h->db, static_cast<const double*>(d_x), static_cast<double*>(d_y));
+            if (levels) *levels = h->db.H.nlev;
+            if (coarse_n) *coarse_n = h->db.H.n_coarse;
+        }
     } catch (CudaError& e) {
         return map_cuda(e.e);
     } catch (StatusError& e) {
