@@ -103,13 +103,18 @@ typedef struct {
                              sliced ELL copy (slices of 32 rows, column-major, so every index load
                              of a warp is one 128-byte line); 0: from CSR tiles with spmv_lanes
                              lanes per row.  Sums differ only by rounding order. */
-    int precond;          /* preconditioner of the inner solve (Remark 3.2 with the deflation term of
-                             Eq. 3.6 by Sherman-Morrison-Woodbury in both cases):
-                             0 (default): the diagonal diag(max(deg - sigma, deg / 2));
-                             1: an aggregation multilevel preconditioner of the trimmed Laplacian
+    int precond;          /* preconditioner of the inner solve (Remark 3.2):
+                             0: the diagonal D = diag(max(deg - sigma, deg / 2)), with the deflation
+                             term by Sherman-Morrison-Woodbury (Eq. 3.6);
+                             1: an aggregation multilevel preconditioner M of the trimmed Laplacian
                              (greedy aggregation, Galerkin coarse Laplacians, one symmetric V-cycle
-                             with damped Jacobi smoothing), standing in for combinatorial multigrid */
-    double ml_alpha;      /* precond = 1: over-correction factor of the coarse-grid correction; <= 0: 1.5 */
+                             with damped Jacobi smoothing), standing in for combinatorial multigrid,
+                             deflated by projection: inv(P) = Pi inv(M) Pi + Vh diag(1/(lambda - sigma +
+                             delta)) Vh^T, Pi = I - Vh Vh^T;
+                             -1 (default): automatic: on graphs with n >= 100000 and maximum degree
+                             <= 64, one timed inner solve with each at create, the faster is kept;
+                             the diagonal elsewhere */
+    double ml_alpha;      /* multilevel: over-correction factor of the coarse-grid correction; <= 0: 1.5 */
 } isira_opts;
 
 typedef struct {
@@ -143,6 +148,10 @@ typedef struct {
     long long sell_entries;       /* stored entries (with padding) of the sliced ELL copy (0: none) */
     double max_diag;              /* largest diagonal entry of L (the maximum degree; the maximum
                                      weighted degree for isira_create_weighted) */
+    int precond;                  /* preconditioner in use: 0 diagonal, 1 multilevel */
+    int ml_levels;                /* levels of the multilevel hierarchy in use (0: none) */
+    double precond_probe_ms[2];   /* automatic choice: the timed inner solve with the diagonal and with
+                                     the multilevel preconditioner (0: not probed) */
 } isira_stats;
 
 /* Fills *opts with the defaults listed above (precision = ISIRA_MIXED). */

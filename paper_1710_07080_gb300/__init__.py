@@ -58,10 +58,15 @@ class isira_stats(C.Structure):
                 ("inner_phase1_csum", C.c_longlong), ("kernel_launches", C.c_longlong),
                 ("gather_block", C.c_int), ("hub_bytes", C.c_int), ("hub_timeouts", C.c_longlong),
                 ("inner_rows_ms", C.c_double), ("inner_phase2_ms", C.c_double), ("w_columns", C.c_longlong),
-                ("sell_entries", C.c_longlong), ("max_diag", C.c_double)]
+                ("sell_entries", C.c_longlong), ("max_diag", C.c_double), ("precond", C.c_int),
+                ("ml_levels", C.c_int), ("precond_probe_ms", C.c_double * 2)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        out = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            out[f] = list(v) if hasattr(v, "__len__") else v
+        return out
 
 
 def _load() -> C.CDLL:

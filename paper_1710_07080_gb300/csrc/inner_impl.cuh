@@ -727,25 +727,31 @@ __global__ void k_copy_vcol(const double* src, T* dst, int64_t n) {
 }
 
 // ------------------------------------------------------------------ multilevel-preconditioned MINRES
-// Preconditioner P = M + delta Vh Vh^T (Remark 3.2, Eq. 3.6) with M^{-1} one V-cycle of the
-// aggregation hierarchy (multilevel.cu); by Sherman-Morrison-Woodbury
-//   P^{-1} r = w - MV C^{-1} Vh^T w,  w = M^{-1} r,  MV = M^{-1} Vh,  C = delta^{-1} I + Vh^T MV.
-// P is not diagonal, so the unpreconditioned Lanczos vectors r_{k-1}, r_k are kept (buffers rp, rc,
-// shifted in place by phase 2a) instead of being rebuilt from z.  One iteration k:
+// Preconditioner (Remark 3.2; here with the multilevel M instead of a diagonal):
+//   P^{-1} r = Pi M^{-1} Pi r + Vh D Vh^T r,   Pi = I - Vh Vh^T,   D = diag(1 / (lambda_t - sigma + delta)),
+// with M^{-1} one V-cycle of the aggregation hierarchy (multilevel.cu) and lambda_t the locked
+// eigenvalues.  It is symmetric positive definite and, for Vh made of eigenvectors, it inverts
+// Lh + delta Vh Vh^T - sigma I on span Vh and approximates it on the complement.  It replaces the
+// Sherman-Morrison-Woodbury form of Eq. 3.6 (exact for M + delta Vh Vh^T) because M^{-1} is ~1/lambda_1
+// on the deflated directions: SMW subtracts two terms of that size to get one of size 1/delta,
+// which in FP32 loses more than the inner tolerance; the projections never form those terms.
+// P is not diagonal, so the unpreconditioned Lanczos vectors r_{k-1}, r_k are kept (buffers rprev,
+// rcur, shifted in place).  One iteration k:
 //   gather(z_k); ml_phase1: y' = ((deg - sigma) z_k - g + (sigma/n) s) / beta_k - (beta_k/beta_{k-1}) r_{k-1},
 //       the deferred w/x update, alpha' = v_k^T y', g_k = Vh^T z_k; last CTA: u1 = delta g_k / beta_k,
 //       alpha_k = alpha' + (g_k / beta_k)^T u1;
-//   ml_phase2a: r_{k+1} = y' + Vh u1 - (alpha_k / beta_k) r_k  (rp <- r_k, rc <- r_{k+1});
-//   V-cycle: w = M^{-1} r_{k+1};
-//   ml_phase2b: Vh^T w, r^T w, r^T MV, 1^T w; last CTA: t = C^{-1} Vh^T w, beta_{k+1}^2 = r^T w - (r^T MV) t,
-//       1^T z = 1^T w - (1^T MV) t, Givens step, stopping test;
-//   ml_phase2c: z_{k+1} = w - MV t.
+//   ml_phase2a: r_{k+1} = y' + Vh u1 - (alpha_k / beta_k) r_k and h = Vh^T r_{k+1};
+//   ml_project: rin = r_{k+1} - Vh h (= Pi r);   V-cycle: w = M^{-1} rin;
+//   ml_phase2b: Vh^T w, r^T w; last CTA: tv = D h - Vh^T w, beta_{k+1}^2 = r^T w + h^T tv, Givens step;
+//   ml_phase2c: z_{k+1} = w + Vh tv (= Pi w + Vh D h) and 1^T z_{k+1}.
 
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_ml_phase1(InnerArgs<T> a) {
     constexpr int VN = Vec<T>::N;
     constexpr int NE = Ncols<NC>::value;
     constexpr int NA = 1 + NE;
+    constexpr int TILE = kThreads * VN;
+    constexpr int QW = (NE + kWarps - 1) / kWarps;
     InnerState<T>* st = a.st;
     if (st->done) return;
     const int k = st->itn + 1;
@@ -764,59 +770,88 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase1(InnerArgs<T> a) {
     const T* __restrict__ wo1 = wbuf(a, j + 2);
     T* __restrict__ wn = wbuf(a, j);
     const T oldeps = st->w_oldeps, dlt = st->w_dlt, inv_gamma = st->w_inv_gamma, phi = st->w_phi;
-    T acc[NA];
+    __shared__ __align__(16) T sz[NE > 0 ? TILE : 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T acc0 = T(0);
+    T cg[QW > 0 ? QW : 1];
 #pragma unroll
-    for (int t = 0; t < NA; ++t) acc[t] = T(0);
+    for (int q = 0; q < (QW > 0 ? QW : 1); ++q) cg[q] = T(0);
     const int64_t n = a.rs.n, trim = a.trim;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
-    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
-        T g[VN], z[VN], y[VN], rpv[VN];
-        T dgv[VN];
-        bool ok[VN];
-        vld(a.gsum + r0, g);
-        vld(zc + r0, z);
-        vld_degree<T>(a, r0, dgv);
-        T zpv[VN], w2[VN], w1[VN], xv[VN], wv[VN];
-        if (has_prev) {
-            vld(a.rprev + r0, rpv);
-            vld(zp + r0, zpv);
-            vld(wo2 + r0, w2);
-            vld(wo1 + r0, w1);
-            vld_rw(a.x + r0, xv);
-        }
+    for (int64_t t0 = (int64_t)blockIdx.x * TILE; t0 < n; t0 += (int64_t)gridDim.x * TILE) {
+        const int64_t r0 = t0 + (int64_t)threadIdx.x * VN;
+        T z[VN];
 #pragma unroll
-        for (int e = 0; e < VN; ++e) {
-            const int64_t r = r0 + e;
-            ok[e] = r < n && r != trim;
-            const T degT = dgv[e];
-            T base = ((degT - sigma) * z[e] - g[e] + s_term) * inv_beta;
+        for (int e = 0; e < VN; ++e) z[e] = T(0);
+        if (r0 < n) {
+            T g[VN], y[VN], rpv[VN], dgv[VN];
+            vld(a.gsum + r0, g);
+            vld(zc + r0, z);
+            vld_degree<T>(a, r0, dgv);
+            T zpv[VN], w2[VN], w1[VN], xv[VN], wv[VN];
             if (has_prev) {
-                base -= cprev * rpv[e];
-                const T w = (zpv[e] * inv_oldb - oldeps * w2[e] - dlt * w1[e]) * inv_gamma;
-                wv[e] = ok[e] ? w : T(0);
-                xv[e] += ok[e] ? phi * w : T(0);
+                vld(a.rprev + r0, rpv);
+                vld(zp + r0, zpv);
+                vld(wo2 + r0, w2);
+                vld(wo1 + r0, w1);
+                vld_rw(a.x + r0, xv);
             }
-            y[e] = ok[e] ? base : T(0);
-            z[e] = ok[e] ? z[e] : T(0);
-            acc[0] += z[e] * inv_beta * y[e];
-        }
-        vst(a.Y + r0, y);
-        if (has_prev) {
-            vst(wn + r0, wv);
-            vst(a.x + r0, xv);
-        }
 #pragma unroll
-        for (int t = 0; t < NE; ++t) {
-            if (t < c) {
-                T v[VN];
-                vld(a.Vt + (int64_t)t * a.ldv + r0, v);
-#pragma unroll
-                for (int e = 0; e < VN; ++e) acc[1 + t] += (ok[e] ? v[e] : T(0)) * z[e];
+            for (int e = 0; e < VN; ++e) {
+                const int64_t r = r0 + e;
+                const bool ok = r < n && r != trim;
+                T base = ((dgv[e] - sigma) * z[e] - g[e] + s_term) * inv_beta;
+                if (has_prev) {
+                    base -= cprev * rpv[e];
+                    const T w = (zpv[e] * inv_oldb - oldeps * w2[e] - dlt * w1[e]) * inv_gamma;
+                    wv[e] = ok ? w : T(0);
+                    xv[e] += ok ? phi * w : T(0);
+                }
+                y[e] = ok ? base : T(0);
+                z[e] = ok ? z[e] : T(0);
+                acc0 += z[e] * inv_beta * y[e];
             }
+            vst(a.Y + r0, y);
+            if (has_prev) {
+                vst(wn + r0, wv);
+                vst(a.x + r0, xv);
+            }
+        }
+        if (NE > 0 && c > 0) {
+#pragma unroll
+            for (int e = 0; e < VN; ++e) sz[threadIdx.x * VN + e] = z[e];
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < QW; ++q) {
+                const int t = warp + q * kWarps;
+                if (t < c) {
+                    const T* col = a.Vt + (int64_t)t * a.ldv + t0;
+#pragma unroll
+                    for (int u = 0; u < TILE / (32 * VN); ++u) {
+                        const int rr = (u * 32 + lane) * VN;
+                        if (t0 + rr < n) {
+                            T v[VN];
+                            vld(col + rr, v);
+#pragma unroll
+                            for (int e = 0; e < VN; ++e) cg[q] += (t0 + rr + e < n ? v[e] : T(0)) * sz[rr + e];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
         }
     }
+    __shared__ T bv[NA];
+    const T a0 = block_sum0(acc0);
+    if (threadIdx.x == 0) bv[0] = a0;
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+        const int t = warp + q * kWarps;
+        const T sg = warp_sum(cg[q]);
+        if (lane == 0 && t < NE) bv[1 + t] = t < c ? sg : T(0);
+    }
+    __syncthreads();
     __shared__ T red[NA];
-    if (block_partials_arrive<T, NA>(acc, NE > 0 ? NA : 1, a.partial, a.pstride, a.counter)) {
+    if (block_values_arrive<T>(bv, NE > 0 ? NA : 1, a.partial, a.pstride, a.counter)) {
         last_block_sum(a.partial, a.pstride, gridDim.x, NE > 0 ? NA : 1, red, a.counter);
         if (threadIdx.x == 0) {
             const double bt = (double)beta, delta = (double)a.delta;
@@ -833,41 +868,129 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase1(InnerArgs<T> a) {
     }
 }
 
+// r_{k+1} = y' + Vh u1 - (alpha_k / beta_k) r_k (rprev <- r_k, rcur <- r_{k+1}) and h = Vh^T r_{k+1};
+// init: h = Vh^T r_1 only (r_1 = rcur from the prep kernel)
 template <typename T, int NC>
-__global__ void __launch_bounds__(kThreads) k_ml_phase2a(InnerArgs<T> a) {
+__global__ void __launch_bounds__(kThreads) k_ml_phase2a(InnerArgs<T> a, int init) {
+    constexpr int VN = Vec<T>::N;
+    constexpr int NE = Ncols<NC>::value;
+    constexpr int TILE = kThreads * VN;
+    constexpr int QW = (NE + kWarps - 1) / kWarps;
+    InnerState<T>* st = a.st;
+    if (!init && st->done) return;
+    const int c = st->p_c;
+    const T coef = init ? T(0) : st->alpha / st->beta;
+    __shared__ T us[NE > 0 ? NE : 1];
+    __shared__ __align__(16) T sr[NE > 0 ? TILE : 1];
+    for (int t = threadIdx.x; t < c; t += blockDim.x) us[t] = init ? T(0) : st->u1[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T ch[QW > 0 ? QW : 1];
+#pragma unroll
+    for (int q = 0; q < (QW > 0 ? QW : 1); ++q) ch[q] = T(0);
+    const int64_t n = a.rs.n, trim = a.trim;
+    for (int64_t t0 = (int64_t)blockIdx.x * TILE; t0 < n; t0 += (int64_t)gridDim.x * TILE) {
+        const int64_t r0 = t0 + (int64_t)threadIdx.x * VN;
+        T rn[VN];
+#pragma unroll
+        for (int e = 0; e < VN; ++e) rn[e] = T(0);
+        if (r0 < n) {
+            T rc[VN];
+            vld_rw(a.rcur + r0, rc);
+            if (init) {
+#pragma unroll
+                for (int e = 0; e < VN; ++e) rn[e] = (r0 + e < n && r0 + e != trim) ? rc[e] : T(0);
+            } else {
+                T y[VN], vu[VN];
+                vld(a.Y + r0, y);
+#pragma unroll
+                for (int e = 0; e < VN; ++e) vu[e] = T(0);
+#pragma unroll
+                for (int t = 0; t < NE; ++t) {
+                    if (t < c) {
+                        T v[VN];
+                        vld(a.Vt + (int64_t)t * a.ldv + r0, v);
+#pragma unroll
+                        for (int e = 0; e < VN; ++e) vu[e] += v[e] * us[t];
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < VN; ++e) {
+                    const int64_t r = r0 + e;
+                    rn[e] = (r < n && r != trim) ? y[e] + vu[e] - coef * rc[e] : T(0);
+                }
+                vst(a.rprev + r0, rc);
+                vst(a.rcur + r0, rn);
+            }
+        }
+        if (NE > 0 && c > 0) {
+#pragma unroll
+            for (int e = 0; e < VN; ++e) sr[threadIdx.x * VN + e] = rn[e];
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < QW; ++q) {
+                const int t = warp + q * kWarps;
+                if (t < c) {
+                    const T* col = a.Vt + (int64_t)t * a.ldv + t0;
+#pragma unroll
+                    for (int u = 0; u < TILE / (32 * VN); ++u) {
+                        const int rr = (u * 32 + lane) * VN;
+                        if (t0 + rr < n) {
+                            T v[VN];
+                            vld(col + rr, v);
+#pragma unroll
+                            for (int e = 0; e < VN; ++e) ch[q] += (t0 + rr + e < n ? v[e] : T(0)) * sr[rr + e];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (NE == 0) return;
+    __shared__ T bv[NE > 0 ? NE : 1];
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+        const int t = warp + q * kWarps;
+        const T sh = warp_sum(ch[q]);
+        if (lane == 0 && t < NE) bv[t] = t < c ? sh : T(0);
+    }
+    __syncthreads();
+    __shared__ T red[NE > 0 ? NE : 1];
+    if (block_values_arrive<T>(bv, NE, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, NE, red, a.counter);
+        for (int t = threadIdx.x; t < c; t += blockDim.x) st->hv[t] = red[t];
+    }
+}
+
+// rin = r_{k+1} - Vh h (Pi r); only for c > 0
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_ml_project(InnerArgs<T> a, int init) {
     constexpr int VN = Vec<T>::N;
     constexpr int NE = Ncols<NC>::value;
     InnerState<T>* st = a.st;
-    if (st->done) return;
+    if (!init && st->done) return;
     const int c = st->p_c;
-    const T coef = st->alpha / st->beta;
-    __shared__ T us[NE > 0 ? NE : 1];
-    for (int t = threadIdx.x; t < c; t += blockDim.x) us[t] = st->u1[t];
+    __shared__ T hs[NE > 0 ? NE : 1];
+    for (int t = threadIdx.x; t < c; t += blockDim.x) hs[t] = st->hv[t];
     __syncthreads();
     const int64_t n = a.rs.n, trim = a.trim;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
     for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
-        T y[VN], rc[VN], vu[VN], rn[VN];
-        vld(a.Y + r0, y);
-        vld_rw(a.rcur + r0, rc);
-#pragma unroll
-        for (int e = 0; e < VN; ++e) vu[e] = T(0);
+        T r[VN];
+        vld(a.rcur + r0, r);
 #pragma unroll
         for (int t = 0; t < NE; ++t) {
             if (t < c) {
                 T v[VN];
                 vld(a.Vt + (int64_t)t * a.ldv + r0, v);
 #pragma unroll
-                for (int e = 0; e < VN; ++e) vu[e] += v[e] * us[t];
+                for (int e = 0; e < VN; ++e) r[e] -= v[e] * hs[t];
             }
         }
 #pragma unroll
-        for (int e = 0; e < VN; ++e) {
-            const int64_t r = r0 + e;
-            rn[e] = (r < n && r != trim) ? y[e] + vu[e] - coef * rc[e] : T(0);
-        }
-        vst(a.rprev + r0, rc);
-        vst(a.rcur + r0, rn);
+        for (int e = 0; e < VN; ++e) r[e] = (r0 + e < n && r0 + e != trim) ? r[e] : T(0);
+        vst(a.rin + r0, r);
     }
 }
 
@@ -876,7 +999,7 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase2b(InnerArgs<T> a, int ini
                                                         int has_cond) {
     constexpr int VN = Vec<T>::N;
     constexpr int NE = Ncols<NC>::value;
-    constexpr int NA = 2 + 2 * NE;           // r^T w, 1^T w, Vh^T w, r^T MV
+    constexpr int NA = 1 + NE;               // r^T w, Vh^T w
     InnerState<T>* st = a.st;
     if (!init && st->done) {
         if (has_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
@@ -897,43 +1020,36 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase2b(InnerArgs<T> a, int ini
         for (int e = 0; e < VN; ++e) {
             const bool ok = r0 + e < n && r0 + e != trim;
             w[e] = ok ? w[e] : T(0);
-            r[e] = ok ? r[e] : T(0);
-            acc[0] += r[e] * w[e];
-            acc[1] += w[e];
+            acc[0] += (ok ? r[e] : T(0)) * w[e];
         }
 #pragma unroll
         for (int t = 0; t < NE; ++t) {
             if (t < c) {
-                T v[VN], m[VN];
+                T v[VN];
                 vld(a.Vt + (int64_t)t * a.ldv + r0, v);
-                vld(a.MV + (int64_t)t * a.ldv + r0, m);
 #pragma unroll
-                for (int e = 0; e < VN; ++e) {
-                    const bool ok = r0 + e < n && r0 + e != trim;
-                    acc[2 + t] += (ok ? v[e] : T(0)) * w[e];
-                    acc[2 + NE + t] += (ok ? m[e] : T(0)) * r[e];
-                }
+                for (int e = 0; e < VN; ++e) acc[1 + t] += (r0 + e < n && r0 + e != trim ? v[e] : T(0)) * w[e];
             }
         }
     }
     __shared__ T red[NA];
-    if (block_partials_arrive<T, NA>(acc, NE > 0 ? NA : 2, a.partial, a.pstride, a.counter)) {
-        last_block_sum(a.partial, a.pstride, gridDim.x, NE > 0 ? NA : 2, red, a.counter);
+    if (block_partials_arrive<T, NA>(acc, NE > 0 ? NA : 1, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, NE > 0 ? NA : 1, red, a.counter);
         if (threadIdx.x == 0) {
-            // t = C^{-1} Vh^T w, then the SMW-corrected r^T z and 1^T z
-            double bb = (double)red[0], ss = (double)red[1];
-            for (int p = 0; p < c; ++p) {
-                double tp = 0.0;
-                for (int q = 0; q < c; ++q) tp += a.Cinv[p + q * c] * (double)red[2 + q];
-                st->tv[p] = (T)tp;
-                bb -= (double)red[2 + NE + p] * tp;
-                ss -= a.mv1[p] * tp;
+            // z = Pi w + Vh D h = w + Vh tv,  tv = D h - Vh^T w,  r^T z = r^T w + h^T tv
+            double bb = (double)red[0];
+            for (int t = 0; t < c; ++t) {
+                const double h = (double)st->hv[t];
+                const double tv = a.dv[t] * h - (double)red[1 + t];
+                st->tv[t] = (T)tv;
+                bb += h * tv;
             }
-            minres_step(a, st, (T)bb, (T)ss, init, k, cond, has_cond);
+            minres_step(a, st, (T)bb, st->s_cur, init, k, cond, has_cond);
         }
     }
 }
 
+// z_{k+1} = w + Vh tv and its sum 1^T z_{k+1} (the next operator application's rank-one term)
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_ml_phase2c(InnerArgs<T> a, int init) {
     constexpr int VN = Vec<T>::N;
@@ -946,6 +1062,7 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase2c(InnerArgs<T> a, int ini
     __shared__ T ts[NE > 0 ? NE : 1];
     for (int t = threadIdx.x; t < c; t += blockDim.x) ts[t] = st->tv[t];
     __syncthreads();
+    T acc[1] = {T(0)};
     const int64_t n = a.rs.n, trim = a.trim;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
     for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
@@ -954,15 +1071,23 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase2c(InnerArgs<T> a, int ini
 #pragma unroll
         for (int t = 0; t < NE; ++t) {
             if (t < c) {
-                T m[VN];
-                vld(a.MV + (int64_t)t * a.ldv + r0, m);
+                T v[VN];
+                vld(a.Vt + (int64_t)t * a.ldv + r0, v);
 #pragma unroll
-                for (int e = 0; e < VN; ++e) w[e] -= m[e] * ts[t];
+                for (int e = 0; e < VN; ++e) w[e] += v[e] * ts[t];
             }
         }
 #pragma unroll
-        for (int e = 0; e < VN; ++e) w[e] = (r0 + e < n && r0 + e != trim) ? w[e] : T(0);
+        for (int e = 0; e < VN; ++e) {
+            w[e] = (r0 + e < n && r0 + e != trim) ? w[e] : T(0);
+            acc[0] += w[e];
+        }
         vst(zn + r0, w);
+    }
+    __shared__ T red[1];
+    if (block_partials_arrive<T, 1>(acc, 1, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, 1, red, a.counter);
+        if (threadIdx.x == 0) st->s_cur = red[0];
     }
 }
 
@@ -1002,80 +1127,6 @@ __global__ void __launch_bounds__(TPB, TPB == kThreads ? 4 : 1) k_gather_vec(Row
     if (done && *done) return;
     GatherStore<T> epi{g};
     for_each_row_gather<T, G>(rs, x, epi, skip);
-}
-
-// C = delta^{-1} I + Vh^T MV (symmetrised), its inverse (Cholesky, FP64), and 1^T MV, for the
-// multilevel SMW preconditioner.  One CTA per row tile; the last CTA factors.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_ml_gram(InnerArgs<T> a, double* Cinv, double* mv1, double* partial,
-                                                      int pstride) {
-    const int c = a.c;
-    const int ne = c * c + c;              // all entries of Vh^T MV, then 1^T MV
-    const int64_t n = a.rs.n;
-    constexpr int kPer = 4;                // (31 * 31 + 31) / 256 < 4
-    double acc[kPer];
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
-    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
-        if (r == a.trim) continue;
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int e = threadIdx.x + q * blockDim.x;
-            if (e < c * c) {
-                const int p = e % c, s2 = e / c;
-                acc[q] += (double)a.Vt[(int64_t)p * a.ldv + r] * (double)a.MV[(int64_t)s2 * a.ldv + r];
-            } else if (e < ne) {
-                acc[q] += (double)a.MV[(int64_t)(e - c * c) * a.ldv + r];
-            }
-        }
-    }
-    for (int q = 0; q < kPer; ++q) {
-        const int e = threadIdx.x + q * blockDim.x;
-        if (e < ne) partial[(size_t)e * pstride + blockIdx.x] = acc[q];
-    }
-    __threadfence();
-    __syncthreads();
-    __shared__ int last;
-    if (threadIdx.x == 0) last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!last) return;
-    __shared__ double Gs[kCMax * kCMax];
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (size_t)e * pstride + b);
-        if (e < c * c) Gs[e] = s; else mv1[e - c * c] = s;
-    }
-    if (threadIdx.x == 0) *a.counter = 0u;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double Lc[kCMax * kCMax];
-        const double dinv = 1.0 / (double)a.delta;
-        for (int s = 0; s < c; ++s) {
-            double d = 0.5 * (Gs[s + s * c] + Gs[s + s * c]) + dinv;
-            for (int t = 0; t < s; ++t) d -= Lc[s + t * c] * Lc[s + t * c];
-            d = sqrt(d > 0.0 ? d : 1e-300);
-            Lc[s + s * c] = d;
-            for (int p = s + 1; p < c; ++p) {
-                double v = 0.5 * (Gs[p + s * c] + Gs[s + p * c]);
-                for (int t = 0; t < s; ++t) v -= Lc[p + t * c] * Lc[s + t * c];
-                Lc[p + s * c] = v / d;
-            }
-        }
-        for (int col = 0; col < c; ++col) {
-            double y[kCMax];
-            for (int p = 0; p < c; ++p) {
-                double v = (p == col) ? 1.0 : 0.0;
-                for (int t = 0; t < p; ++t) v -= Lc[p + t * c] * y[t];
-                y[p] = v / Lc[p + p * c];
-            }
-            for (int p = c - 1; p >= 0; --p) {
-                double v = y[p];
-                for (int t = p + 1; t < c; ++t) v -= Lc[t + p * c] * y[t];
-                y[p] = v / Lc[p + p * c];
-            }
-            for (int p = 0; p < c; ++p) Cinv[p + col * c] = y[p];
-        }
-    }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -1162,6 +1213,7 @@ cudaError_t inner_gather_attrs(int bytes) {
         if (e == cudaSuccess) e = wave_register((const void*)k_ml_phase2a<T, NC>);                      \
         if (e == cudaSuccess) e = wave_register((const void*)k_ml_phase2b<T, NC>);                      \
         if (e == cudaSuccess) e = wave_register((const void*)k_ml_phase2c<T, NC>);                      \
+        if (e == cudaSuccess) e = wave_register((const void*)k_ml_project<T, NC>);                      \
     } while (0)
     for (int nc : {0, 8, 12, 16, 24, 32}) ISIRA_NC_DISPATCH(nc, LW);
 #undef LW
@@ -1230,10 +1282,18 @@ void ml_phase1(const InnerArgs<T>& a, cudaStream_t s) {
 }
 
 template <typename T>
-void ml_phase2a(const InnerArgs<T>& a, cudaStream_t s) {
-#define L2(NC) k_ml_phase2a<T, NC><<<wave_grid((const void*)k_ml_phase2a<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a)
+void ml_phase2a(const InnerArgs<T>& a, int init, cudaStream_t s) {
+#define L2(NC) k_ml_phase2a<T, NC><<<wave_grid((const void*)k_ml_phase2a<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a, init)
     ISIRA_NC_DISPATCH(a.c, L2);
 #undef L2
+}
+
+template <typename T>
+void ml_project(const InnerArgs<T>& a, int init, cudaStream_t s) {
+    if (a.c <= 0) return;
+#define LP(NC) k_ml_project<T, NC><<<wave_grid((const void*)k_ml_project<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a, init)
+    ISIRA_NC_DISPATCH(a.c, LP);
+#undef LP
 }
 
 template <typename T>
@@ -1250,14 +1310,6 @@ void ml_phase2c(const InnerArgs<T>& a, int init, cudaStream_t s) {
 #define L2(NC) k_ml_phase2c<T, NC><<<wave_grid((const void*)k_ml_phase2c<T, NC>, vec_blocks(a)), kThreads, 0, s>>>(a, init)
     ISIRA_NC_DISPATCH(a.c, L2);
 #undef L2
-}
-
-template <typename T>
-void ml_gram(const InnerArgs<T>& a, double* Cinv, double* mv1, cudaStream_t s) {
-    if (a.c <= 0) return;
-    const int ps = a.pstride / 2;                      // up to 1024 slots per block
-    const int grid = a.ew_blocks < ps ? a.ew_blocks : ps;
-    k_ml_gram<T><<<grid > 0 ? grid : 1, kThreads, 0, s>>>(a, Cinv, mv1, a.partial_d, ps);
 }
 
 template <typename T>
@@ -1302,10 +1354,10 @@ void copy_vcol(const double* src, T* dst, int64_t n, cudaStream_t s) {
     template void inner_gather_vec<T>(const InnerArgs<T>&, const T*, T*, int, const int*, cudaStream_t);   \
     template void ml_inner_prep<T>(const InnerArgs<T>&, const double*, const double*, cudaStream_t);      \
     template void ml_phase1<T>(const InnerArgs<T>&, cudaStream_t);                                       \
-    template void ml_phase2a<T>(const InnerArgs<T>&, cudaStream_t);                                      \
+    template void ml_phase2a<T>(const InnerArgs<T>&, int, cudaStream_t);                                 \
+    template void ml_project<T>(const InnerArgs<T>&, int, cudaStream_t);                                 \
     template void ml_phase2b<T>(const InnerArgs<T>&, int, cudaGraphConditionalHandle, int, cudaStream_t); \
     template void ml_phase2c<T>(const InnerArgs<T>&, int, cudaStream_t);                                 \
-    template void ml_gram<T>(const InnerArgs<T>&, double*, double*, cudaStream_t);                       \
     template void inner_gather<T>(const InnerArgs<T>&, int, cudaStream_t);                               \
     template void inner_rows<T>(const InnerArgs<T>&, cudaStream_t);                                      \
     template void inner_phase2<T>(const InnerArgs<T>&, int, cudaStream_t);                               \

@@ -72,6 +72,7 @@ struct InnerState {
     T s_cur;                                 // sum(z_k)
     T g_cur[kCMax], g_prev[kCMax];           // Vh^T z_k, Vh^T z_{k-1}
     T u1[kCMax];                             // phase-1 coefficient of Vh_r (see inner_impl.cuh)
+    T hv[kCMax];                             // multilevel path: Vh^T r_{k+1}
     T qv[kCMax];                             // phase-2: (alpha/beta) delta g_cur
     T tv[kCMax];                             // phase-2: SMW coefficient C^{-1} Vh^T D^{-1} y
     T p_sigma, p_sig_n;                      // shift and (sigma / n or 0) of the current solve
@@ -98,10 +99,10 @@ struct InnerArgs {
     HostStatus* hs;             // device alias of the mapped host status
     const double* Cinv;         // c-by-c inverse of C = delta^{-1} I + Vh^T D^{-1} Vh
     const double* Gm;           // c-by-c Vh^T D^{-1} Vh
-    // multilevel preconditioner: stored Lanczos vectors, the V-cycle output, M^{-1} Vh, 1^T M^{-1} Vh
-    T* rprev; T* rcur; T* wv;
-    const T* MV;
-    const double* mv1;
+    // multilevel preconditioner: stored Lanczos vectors, the projected V-cycle input, its output, and
+    // D = diag(1 / (lambda_t - sigma + delta)) of the deflated directions (device, c doubles)
+    T* rprev; T* rcur; T* rin; T* wv;
+    const double* dv;
     double* partial_d;          // the partial-sum buffer viewed as doubles (FP64 Gram sums)
     T tau; int max_it;
     int ew_blocks;              // grid of the row-elementwise kernels
@@ -132,11 +133,12 @@ template <typename T> void inner_gather_vec(const InnerArgs<T>& a, const T* x, T
 template <typename T> void ml_inner_prep(const InnerArgs<T>& a, const double* R, const double* rnorm_dev,
                                          cudaStream_t s);
 template <typename T> void ml_phase1(const InnerArgs<T>& a, cudaStream_t s);
-template <typename T> void ml_phase2a(const InnerArgs<T>& a, cudaStream_t s);
+template <typename T> void ml_phase2a(const InnerArgs<T>& a, int init, cudaStream_t s);
+template <typename T> void ml_project(const InnerArgs<T>& a, int init, cudaStream_t s);
 template <typename T> void ml_phase2b(const InnerArgs<T>& a, int init, cudaGraphConditionalHandle cond, int has_cond,
                                       cudaStream_t s);
 template <typename T> void ml_phase2c(const InnerArgs<T>& a, int init, cudaStream_t s);
-template <typename T> void ml_gram(const InnerArgs<T>& a, double* Cinv, double* mv1, cudaStream_t s);
+
 
 // ------------------------------------------------------------------ outer loop (FP64)
 struct OuterArgs {

@@ -210,35 +210,54 @@ __global__ void __launch_bounds__(kThreads) k_ml_scale(const T* __restrict__ b, 
         x[i] = i == skip ? T(0) : om * b[i] * dinv[i];
 }
 
-// coarse right-hand side: bc[I] = sum over the members i of I of the level's residual b - A x0 at
-// x0 = w D^{-1} b, i.e. (1 - w) b_i + (W x0)_i.  Level 0 takes (W x0)_i from the gather (wx0);
-// coarser levels compute it from their CSR.  One warp per cluster.
+// (W x)_r for the rows of a coarse level, G lanes per row (strided over the row's entries, then a
+// shuffle reduction); every warp runs the same number of passes so the shuffles stay converged
+template <typename T, int G>
+__device__ __forceinline__ T csr_row_sum(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                         const T* __restrict__ w, const T* __restrict__ x, int64_t row, bool valid) {
+    T s = T(0);
+    if (valid) {
+        const int j = threadIdx.x & (G - 1);
+        for (int32_t e = rp[row] + j; e < rp[row + 1]; e += G) s += w[e] * x[ci[e]];
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    return s;
+}
+
+// coarse level: r = b - A x0 at x0 = w D^{-1} b, i.e. (1 - w) b + W x0
+template <typename T, int G>
+__global__ void __launch_bounds__(kThreads) k_ml_resid(const T* __restrict__ b, const T* __restrict__ x0,
+                                                       const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                       const T* __restrict__ w, T om, int64_t n, T* __restrict__ r,
+                                                       const int* __restrict__ done) {
+    if (done && *done) return;
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t passes = (n + groups - 1) / groups;
+    for (int64_t p = 0; p < passes; ++p) {
+        const int64_t row = g0 + p * groups;
+        const T s = csr_row_sum<T, G>(rp, ci, w, x0, row, row < n);
+        if (row < n && (threadIdx.x & (G - 1)) == 0) r[row] = (T(1) - om) * b[row] + s;
+    }
+}
+
+// bc[I] = sum over the members i of cluster I of (ob * b_i + add_i): level 0 passes ob = 1 - w and
+// add = W x0 (the gather), so the summand is the residual (1 - w) b + W x0; coarser levels pass ob = 0
+// and add = their residual.  One thread per cluster.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_ml_restrict(const T* __restrict__ b, const T* __restrict__ wx0,
-                                                          const T* __restrict__ x0, const int32_t* __restrict__ rp,
-                                                          const int32_t* __restrict__ ci, const T* __restrict__ w,
+__global__ void __launch_bounds__(kThreads) k_ml_restrict(const T* __restrict__ b, const T* __restrict__ add, T ob,
                                                           const int64_t* __restrict__ mrp,
-                                                          const int32_t* __restrict__ mem, int64_t nc, T om,
+                                                          const int32_t* __restrict__ mem, int64_t nc,
                                                           T* __restrict__ bc, const int* __restrict__ done) {
     if (done && *done) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t I = w0; I < nc; I += nw) {
+    for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
         T s = T(0);
-        for (int64_t q = mrp[I] + lane; q < mrp[I + 1]; q += 32) {
+        for (int64_t q = mrp[I]; q < mrp[I + 1]; ++q) {
             const int32_t i = mem[q];
-            T wx;
-            if (wx0) {
-                wx = wx0[i];
-            } else {
-                wx = T(0);
-                for (int32_t e = rp[i]; e < rp[i + 1]; ++e) wx += w[e] * x0[ci[e]];
-            }
-            s += (T(1) - om) * b[i] + wx;
+            s += ob * b[i] + add[i];
         }
-        s = warp_sum(s);
-        if (lane == 0) bc[I] = s;
+        bc[I] = s;
     }
 }
 
@@ -255,28 +274,40 @@ __global__ void __launch_bounds__(kThreads) k_ml_prolong(const T* __restrict__ b
     }
 }
 
-// post-smoothing: out = x1 + w D^{-1} (b - d x1 + W x1), with (W x1) from the gather (level 0) or the CSR
+// post-smoothing: out = x1 + w D^{-1} (b - d x1 + W x1); level 0 takes (W x1) from the gather
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_ml_post(const T* __restrict__ b, const T* __restrict__ dinv,
-                                                      const T* __restrict__ x1, const T* __restrict__ wx1,
-                                                      const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                      const T* __restrict__ w, T om, int64_t n, int64_t skip,
-                                                      T* __restrict__ out, const int* __restrict__ done) {
+                                                      const T* __restrict__ x1, const T* __restrict__ wx1, T om,
+                                                      int64_t n, int64_t skip, T* __restrict__ out,
+                                                      const int* __restrict__ done) {
     if (done && *done) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (i == skip) {
             out[i] = T(0);
             continue;
         }
-        T wx;
-        if (wx1) {
-            wx = wx1[i];
-        } else {
-            wx = T(0);
-            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) wx += w[e] * x1[ci[e]];
-        }
         const T xi = x1[i], di = dinv[i];
-        out[i] = xi + om * (b[i] * di - xi + wx * di);
+        out[i] = xi + om * (b[i] * di - xi + wx1[i] * di);
+    }
+}
+
+// the same on a coarse level, (W x1) from its CSR with G lanes per row
+template <typename T, int G>
+__global__ void __launch_bounds__(kThreads) k_ml_post_csr(const T* __restrict__ b, const T* __restrict__ dinv,
+                                                          const T* __restrict__ x1, const int32_t* __restrict__ rp,
+                                                          const int32_t* __restrict__ ci, const T* __restrict__ w, T om,
+                                                          int64_t n, T* __restrict__ out, const int* __restrict__ done) {
+    if (done && *done) return;
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t passes = (n + groups - 1) / groups;
+    for (int64_t p = 0; p < passes; ++p) {
+        const int64_t row = g0 + p * groups;
+        const T s = csr_row_sum<T, G>(rp, ci, w, x1, row, row < n);
+        if (row < n && (threadIdx.x & (G - 1)) == 0) {
+            const T xi = x1[row], di = dinv[row];
+            out[row] = xi + om * (b[row] * di - xi + s * di);
+        }
     }
 }
 
@@ -424,6 +455,13 @@ static int ml_warp_grid(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 2432));
 }
 
+static int ml_group_grid(int64_t n, int G) {
+    const int64_t g = (n * G + kThreads - 1) / kThreads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 2432));
+}
+
+constexpr int kMlLanes = 4;          // lanes per coarse CSR row
+
 // out = M^{-1} b (b on level 0, n-space, the trimmed entry ignored; out may alias nothing else).
 // gather(x, g) must compute g = sum over neighbours of x for level 0 (the solver's gather).
 template <typename T>
@@ -438,11 +476,11 @@ void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather,
         k_ml_scale<T><<<ml_grid(D.n), kThreads, 0, s>>>(bl, D.dinv, omega, D.n, l == 0 ? H.skip : -1, D.x0, done);
         if (l == 0) {
             gather(D.x0, D.x, s);                                    // D.x <- W x0
-            k_ml_restrict<T><<<ml_warp_grid(C.n), kThreads, 0, s>>>(bl, D.x, nullptr, nullptr, nullptr, nullptr,
-                                                                     D.mrp, D.mem, C.n, omega, C.b, done);
+            k_ml_restrict<T><<<ml_grid(C.n), kThreads, 0, s>>>(bl, D.x, T(1) - omega, D.mrp, D.mem, C.n, C.b, done);
         } else {
-            k_ml_restrict<T><<<ml_warp_grid(C.n), kThreads, 0, s>>>(bl, nullptr, D.x0, D.rp, D.ci, D.w, D.mrp, D.mem,
-                                                                     C.n, omega, C.b, done);
+            k_ml_resid<T, kMlLanes><<<ml_group_grid(D.n, kMlLanes), kThreads, 0, s>>>(bl, D.x0, D.rp, D.ci, D.w,
+                                                                                        omega, D.n, D.x, done);
+            k_ml_restrict<T><<<ml_grid(C.n), kThreads, 0, s>>>(bl, D.x, T(0), D.mrp, D.mem, C.n, C.b, done);
         }
         bl = C.b;
     }
@@ -458,11 +496,10 @@ void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather,
         T* dst = l == 0 ? out : D.x;
         if (l == 0) {
             gather(D.x1, D.x0, s);                                   // D.x0 <- W x1 (x0 is free now)
-            k_ml_post<T><<<ml_grid(D.n), kThreads, 0, s>>>(bd, D.dinv, D.x1, D.x0, nullptr, nullptr, nullptr, omega,
-                                                           D.n, H.skip, dst, done);
+            k_ml_post<T><<<ml_grid(D.n), kThreads, 0, s>>>(bd, D.dinv, D.x1, D.x0, omega, D.n, H.skip, dst, done);
         } else {
-            k_ml_post<T><<<ml_grid(D.n), kThreads, 0, s>>>(bd, D.dinv, D.x1, nullptr, D.rp, D.ci, D.w, omega, D.n, -1,
-                                                           dst, done);
+            k_ml_post_csr<T, kMlLanes><<<ml_group_grid(D.n, kMlLanes), kThreads, 0, s>>>(bd, D.dinv, D.x1, D.rp, D.ci,
+                                                                                          D.w, omega, D.n, dst, done);
         }
         xc = dst;
     }
@@ -470,7 +507,7 @@ void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather,
 
 template <typename T>
 int ml_launches(const MlHierarchy<T>& H) {
-    return H.nlev <= 1 ? 1 : 6 + 4 * (H.nlev - 2) + 1;
+    return H.nlev <= 1 ? 1 : 6 + 5 * (H.nlev - 2) + 1;
 }
 
 #define ISIRA_INSTANTIATE_ML(T)                                                                              \

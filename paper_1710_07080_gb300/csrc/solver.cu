@@ -41,9 +41,8 @@ template <typename T>
 struct InnerBuffers {
     T* base = nullptr;
     InnerState<T>* st = nullptr;
-    // multilevel preconditioner: 3 n-vectors (r_{k-1}, r_k, V-cycle output) then kCMax columns M^{-1} Vh
+    // multilevel preconditioner: 4 n-vectors (r_{k-1}, r_k, projected V-cycle input, V-cycle output)
     T* ml = nullptr;
-    int mv_count = 0;                 // columns of M^{-1} Vh valid for the current deflation basis
     MlHierarchy<T> H;
 };
 
@@ -124,8 +123,8 @@ struct isira_handle_s {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t inner_graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaGraphExec_t ml_graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    double* ml_cinv = nullptr;        // kCMax x kCMax: C^{-1} of the multilevel SMW preconditioner
-    double* ml_mv1 = nullptr;         // kCMax: 1^T M^{-1} Vh
+    double* ml_dv = nullptr;          // kCMax: 1 / (lambda_t - sigma + delta) of the deflated directions
+    bool use_ml = false;              // inner solves with the multilevel preconditioner
     int pending_inner_stats = 0;
 };
 
@@ -166,15 +165,15 @@ InnerArgs<T> make_args(isira_handle h, InnerBuffers<T>& b, double sigma, int c, 
     a.counter = h->counter;
     a.st = b.st;
     a.hs = h->hs_dev;
-    a.Cinv = h->opts.precond == 1 ? h->ml_cinv : h->Cinv;
+    a.Cinv = h->Cinv;
     a.Gm = h->Gm;
     a.partial_d = h->partial;
     if (b.ml) {
         a.rprev = b.ml;
         a.rcur = b.ml + ld;
-        a.wv = b.ml + 2 * ld;
-        a.MV = b.ml + 3 * ld;
-        a.mv1 = h->ml_mv1;
+        a.rin = b.ml + 2 * ld;
+        a.wv = b.ml + 3 * ld;
+        a.dv = h->ml_dv;
     }
     a.tau = (T)tau;
     a.max_it = max_it;
@@ -248,13 +247,15 @@ cudaGraphExec_t build_inner_graph(isira_handle h, const InnerArgs<T>& a) {
 // iteration count; graph mode returns -1 (the count is read at the next synchronisation).
 template <typename T>
 int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* Vt, int64_t ldv, double tau,
-                 int max_it, bool gram_dirty, const double* R, const double* rnorm_dev, bool allow_graph);
+                 int max_it, bool gram_dirty, const double* R, const double* rnorm_dev, bool allow_graph,
+                 const double* lam);
 
 template <typename T>
 int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* Vt, int64_t ldv, double tau,
-              int max_it, bool gram_dirty, const double* R, const double* rnorm_dev, bool allow_graph = false) {
-    if (h->opts.precond == 1)
-        return run_inner_ml<T>(h, b, sigma, c, Vt, ldv, tau, max_it, gram_dirty, R, rnorm_dev, allow_graph);
+              int max_it, bool gram_dirty, const double* R, const double* rnorm_dev, bool allow_graph = false,
+              const double* lam = nullptr) {
+    if (h->use_ml)
+        return run_inner_ml<T>(h, b, sigma, c, Vt, ldv, tau, max_it, gram_dirty, R, rnorm_dev, allow_graph, lam);
     InnerArgs<T> a = make_args<T>(h, b, sigma, c, Vt, ldv, tau, max_it);
     cudaStream_t s = h->stream;
     if (gram_dirty && c > 0) {
@@ -323,15 +324,11 @@ constexpr double kMlOmega = 2.0 / 3.0;     // damping of the Jacobi smoother of 
 template <typename T>
 void ensure_ml(isira_handle h, InnerBuffers<T>& b) {
     if (!b.ml) {
-        const size_t elems = (size_t)h->ld * (3 + kCMax);
+        const size_t elems = (size_t)h->ld * 4;
         ck(cudaMalloc(&b.ml, sizeof(T) * elems));
         ck(cudaMemsetAsync(b.ml, 0, sizeof(T) * elems, h->stream));
-        b.mv_count = 0;
     }
-    if (!h->ml_cinv) {
-        ck(cudaMalloc(&h->ml_cinv, sizeof(double) * kCMax * kCMax));
-        ck(cudaMalloc(&h->ml_mv1, sizeof(double) * kCMax));
-    }
+    if (!h->ml_dv) ck(cudaMalloc(&h->ml_dv, sizeof(double) * kCMax));
     if (b.H.nlev == 0) ck(ml_build<T>(b.H, h->rs.rp, h->rs.ci, h->rs.wd, h->n, h->ld, h->trim, h->stream));
 }
 
@@ -346,8 +343,9 @@ void ml_iteration(isira_handle h, InnerBuffers<T>& b, const InnerArgs<T>& a, cud
     GatherFn<T> gather = [&](const T* x, T* g, cudaStream_t st) { inner_gather_vec<T>(a, x, g, h->lanes, done, st); };
     inner_gather<T>(a, h->lanes, s);
     ml_phase1<T>(a, s);
-    ml_phase2a<T>(a, s);
-    ml_vcycle<T>(b.H, a.rcur, a.wv, gather, (T)kMlOmega, ml_alpha<T>(h), done, s);
+    ml_phase2a<T>(a, 0, s);
+    ml_project<T>(a, 0, s);
+    ml_vcycle<T>(b.H, a.c > 0 ? a.rin : a.rcur, a.wv, gather, (T)kMlOmega, ml_alpha<T>(h), done, s);
     ml_phase2b<T>(a, 0, cond, has_cond, s);
     ml_phase2c<T>(a, 0, s);
 }
@@ -377,33 +375,32 @@ cudaGraphExec_t build_ml_graph(isira_handle h, InnerBuffers<T>& b, const InnerAr
 }
 
 template <typename T>
-int ml_launches_per_iteration(const InnerBuffers<T>& b) { return 5 + ml_launches(b.H) + 2; }
+int ml_launches_per_iteration(const InnerBuffers<T>& b, int c) { return 6 + (c > 0 ? 1 : 0) + ml_launches(b.H); }
 
-// One inner solve with the multilevel preconditioner; same contract as run_inner.
+// One inner solve with the multilevel preconditioner; same contract as run_inner.  lam: the
+// locked eigenvalues of the deflation columns (host, c values; null: taken as 0).
 template <typename T>
 int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* Vt, int64_t ldv, double tau,
-                 int max_it, bool gram_dirty, const double* R, const double* rnorm_dev, bool allow_graph) {
+                 int max_it, bool gram_dirty, const double* R, const double* rnorm_dev, bool allow_graph,
+                 const double* lam) {
     ensure_ml(h, b);
     InnerArgs<T> a = make_args<T>(h, b, sigma, c, Vt, ldv, tau, max_it);
     cudaStream_t s = h->stream;
     GatherFn<T> gather0 = [&](const T* x, T* g, cudaStream_t st) { inner_gather_vec<T>(a, x, g, h->lanes, nullptr, st); };
-    if (c > 0 && (gram_dirty || b.mv_count < c)) {
-        // M^{-1} Vh for the columns added since (M does not depend on sigma), then C^{-1}, 1^T M^{-1} Vh
-        if (b.mv_count > c) b.mv_count = 0;
-        for (int t = b.mv_count; t < c; ++t) {
-            ml_vcycle<T>(b.H, Vt + (size_t)t * ldv, b.ml + (size_t)(3 + t) * h->ld, gather0, (T)kMlOmega,
-                         ml_alpha<T>(h), nullptr, s);
-            h->stats.kernel_launches += ml_launches(b.H);
-        }
-        b.mv_count = c;
-        ml_gram<T>(a, h->ml_cinv, h->ml_mv1, s);
-        h->stats.kernel_launches += 1;
+    if (c > 0 && gram_dirty) {
+        // D = diag(1 / (lambda_t - sigma + delta)) for the deflated directions (pageable copy: synchronous)
+        double dv[kCMax];
+        for (int t = 0; t < c; ++t) dv[t] = 1.0 / ((lam ? lam[t] : 0.0) - sigma + h->delta);
+        ck(cudaMemcpyAsync(h->ml_dv, dv, sizeof(double) * c, cudaMemcpyHostToDevice, s));
     }
     ml_inner_prep<T>(a, R, rnorm_dev, s);
-    ml_vcycle<T>(b.H, a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), nullptr, s);
+    ml_phase2a<T>(a, 1, s);
+    ml_project<T>(a, 1, s);
+    ml_vcycle<T>(b.H, c > 0 ? a.rin : a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), nullptr, s);
     ml_phase2b<T>(a, 1, cudaGraphConditionalHandle{}, 0, s);
     ml_phase2c<T>(a, 1, s);
-    h->stats.kernel_launches += 3 + ml_launches(b.H);
+    const int per_it = ml_launches_per_iteration(b, c);
+    h->stats.kernel_launches += per_it - 1;
     if (allow_graph && h->opts.inner_graph && !h->profiling) {
         const int bkt = nc_bucket(c);
         if (!h->ml_graph[bkt]) h->ml_graph[bkt] = build_ml_graph<T>(h, b, a);
@@ -411,12 +408,11 @@ int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const 
         inner_finalize_to<T>(a, h->Z, s);
         h->stats.kernel_launches += 1;
         h->stats.inner_solves += 1;
-        h->pending_inner_stats = ml_launches_per_iteration(b);
+        h->pending_inner_stats = per_it;
         return -1;
     }
     const int chunk = h->opts.inner_chunk > 0 ? h->opts.inner_chunk : 16;
     int launched = 0;
-    const int per_it = ml_launches_per_iteration(b);
     while (true) {
         const bool prof = h->profiling != 0;
         for (int i = 0; i < chunk; ++i) {
@@ -425,8 +421,9 @@ int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const 
             if (prof) ck(cudaEventRecord(h->ev[4 * i + 1], s));
             ml_phase1<T>(a, s);
             if (prof) ck(cudaEventRecord(h->ev[4 * i + 2], s));
-            ml_phase2a<T>(a, s);
-            ml_vcycle<T>(b.H, a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), &a.st->done, s);
+            ml_phase2a<T>(a, 0, s);
+            ml_project<T>(a, 0, s);
+            ml_vcycle<T>(b.H, c > 0 ? a.rin : a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), &a.st->done, s);
             ml_phase2b<T>(a, 0, cudaGraphConditionalHandle{}, 0, s);
             ml_phase2c<T>(a, 0, s);
             if (prof) ck(cudaEventRecord(h->ev[4 * i + 3], s));
@@ -459,6 +456,60 @@ int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const 
     const int its = hst(h)->inner_iters;
     h->stats.inner_iters += its;
     return its;
+}
+
+// Preconditioner of the inner solve.  precond = 0 / 1 force the diagonal / the multilevel one.
+// precond = -1 (automatic): graphs with n >= 100000 and maximum degree <= 64 (mesh-like: the
+// multilevel hierarchy's coarse rows stay short, and its setup is amortised) get one timed inner
+// solve with each preconditioner (shift 0, no deflation, tau_inner, a seeded right-hand side) and
+// keep the faster; every other graph keeps the diagonal.
+template <typename T>
+float time_inner(isira_handle h, InnerBuffers<T>& b, cudaEvent_t e0, cudaEvent_t e1) {
+    cudaStream_t s = h->stream;
+    const double tau = h->opts.tau_inner > 0.0 ? h->opts.tau_inner : 1e-3;
+    const int max_it = h->opts.max_inner > 0 ? h->opts.max_inner : 5000;
+    ck(cudaEventRecord(e0, s));
+    run_inner<T>(h, b, 0.0, 0, nullptr, h->ld, tau, max_it, false, h->R, h->dscratch + 300, true);
+    ck(cudaEventRecord(e1, s));
+    sync(h);
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, e0, e1));
+    return ms;
+}
+
+void choose_preconditioner(isira_handle h) {
+    const int pc = h->opts.precond;
+    const bool mixed = h->opts.precision == ISIRA_MIXED;
+    auto build = [&]() {
+        if (mixed) ensure_ml(h, h->fb); else ensure_ml(h, h->db);
+        sync(h);
+    };
+    h->use_ml = false;
+    if (pc == 1) {
+        build();
+        h->use_ml = true;
+    }
+    if (pc != -1 || h->n < 100000 || h->max_degree > 64) return;
+    build();
+    OuterArgs oa = make_outer(h);
+    outer_random(oa, h->opts.seed, 7777, h->stream);            // right-hand side in Z, copied to R
+    ck(cudaMemcpyAsync(h->R, h->Z, sizeof(double) * (size_t)h->n, cudaMemcpyDeviceToDevice, h->stream));
+    const double one = 1.0;
+    ck(cudaMemcpyAsync(h->dscratch + 300, &one, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    cudaEvent_t e0, e1;
+    ck(cudaEventCreate(&e0));
+    ck(cudaEventCreate(&e1));
+    float t[2] = {0.f, 0.f};
+    for (int ml = 0; ml < 2; ++ml) {
+        h->use_ml = ml == 1;
+        for (int rep = 0; rep < 2; ++rep)                           // the first run builds the graph
+            t[ml] = mixed ? time_inner<float>(h, h->fb, e0, e1) : time_inner<double>(h, h->db, e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->use_ml = t[1] < t[0];
+    h->stats.precond_probe_ms[0] = t[0];
+    h->stats.precond_probe_ms[1] = t[1];
 }
 
 void ensure_outer(isira_handle h, int m, int d) {
@@ -641,7 +692,7 @@ void free_handle(isira_handle h) {
     void* ptrs[] = {h->own_w, h->wf, h->degwd, h->degwf, h->sell_wd, h->sell_wf, h->gsum, h->deg32, h->sell_off, h->sell_ci, h->own_rp, h->own_ci, h->perm, h->inv, h->item_row, h->item_k, h->item_partial,
                     h->item_count, h->warp_start, h->U, h->W, h->V, h->H, h->theta, h->S, h->R, h->Z, h->dscratch,
                     h->partial, h->counter, h->Gm, h->Cinv, h->lam_dev, h->tres_dev, h->fb.base, h->fb.st,
-                    h->db.base, h->db.st, h->Vt_f, h->fb.ml, h->db.ml, h->ml_cinv, h->ml_mv1};
+                    h->db.base, h->db.st, h->Vt_f, h->fb.ml, h->db.ml, h->ml_dv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ml_free(h->fb.H);
@@ -751,7 +802,7 @@ void isira_default_opts(isira_opts* o) {
     o->index_vec = 0;
     o->gather_chunk = 0;
     o->sell = 1;
-    o->precond = 0;
+    o->precond = -1;
     o->ml_alpha = 0.0;
 }
 
@@ -975,16 +1026,13 @@ isira_status isira_create_weighted(isira_handle* out, int64_t n, int64_t nnz, co
         ck(cudaHostGetDevicePointer((void**)&h->hs_dev, h->hs, 0));
         h->rs.err = &h->hs_dev->dev_error;
         if (h->opts.precision == ISIRA_MIXED) alloc_inner(h, h->fb); else alloc_inner(h, h->db);
-        if (h->opts.precond != 0 && h->opts.precond != 1) throw StatusError{ISIRA_ERR_INVALID_ARG};
+        if (h->opts.precond < -1 || h->opts.precond > 1) throw StatusError{ISIRA_ERR_INVALID_ARG};
         int chunk = h->opts.inner_chunk > 0 ? h->opts.inner_chunk : 16;
         h->ev.resize(4 * chunk);
         for (auto& e : h->ev) ck(cudaEventCreate(&e));
         sync(h);
         autotune_gather(h);
-        if (h->opts.precond == 1) {
-            if (h->opts.precision == ISIRA_MIXED) ensure_ml(h, h->fb); else ensure_ml(h, h->db);
-            sync(h);
-        }
+        choose_preconditioner(h);
         if (!rs.dyn) {   // static partition of the CSR work units for the chosen shape
             const int64_t n_units = rs.n_units();
             int64_t* cost = nullptr;
@@ -1010,6 +1058,12 @@ isira_status isira_create_weighted(isira_handle* out, int64_t n, int64_t nnz, co
         h->stats.hub_bytes = h->rs.hub_bytes;
         h->stats.sell_entries = h->sell_total;
         h->stats.max_diag = maxdiag;
+        h->stats.precond = h->use_ml ? 1 : 0;
+        h->stats.ml_levels = h->use_ml ? (h->opts.precision == ISIRA_MIXED ? h->fb.H.nlev : h->db.H.nlev) : 0;
+        h->stats.inner_iters = 0;
+        h->stats.inner_solves = 0;
+        h->stats.kernel_launches = 0;
+        h->pending_inner_stats = 0;
     } catch (CudaError& e) {
         isira_status st = map_cuda(e.e);
         free_handle(h);
@@ -1081,8 +1135,6 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         h->stats.kernel_launches = 0;
         (void)keep;
         h->lam.assign(d, 0.0);
-        h->fb.mv_count = 0;
-        h->db.mv_count = 0;
         OuterArgs oa = make_outer(h);
         ck(cudaMemsetAsync(h->H, 0, sizeof(double) * kMMax * kMMax, s));
         // start basis U_{k0}, k0 = 1 (Algorithm 2 REQUIRE): the given vector, or a SplitMix64 one
@@ -1151,10 +1203,10 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
             // inner solve of Eq. 2.14 and back-map Eq. 2.5 -> Z
             if (h->opts.precision == ISIRA_MIXED)
                 run_inner<float>(h, h->fb, sig, c, h->Vt_f, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch,
-                                 true);
+                                 true, h->lam.data());
             else
                 run_inner<double>(h, h->db, sig, c, h->V, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch,
-                                  true);
+                                  true, h->lam.data());
             gram_dirty = false;
             // orthonormalise against [U V 1] and expand U, W, H
             if (!expand_basis(h, k, c)) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
@@ -1247,8 +1299,6 @@ isira_status isira_inner_solve(isira_handle h, int precision, double sigma, int 
         const double one = 1.0;
         ck(cudaMemcpyAsync(h->dscratch + 300, &one, sizeof(double), cudaMemcpyHostToDevice, s));
         int its = 0;
-        h->fb.mv_count = 0;          // the deflation basis of this call is new
-        h->db.mv_count = 0;
         if (precision == ISIRA_MIXED) {
             alloc_inner(h, h->fb);
             float* Vt = internal_V<float>(h, d_V, c, s);

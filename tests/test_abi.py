@@ -41,7 +41,7 @@ def test_struct_layouts_match_header(isira):
     for struct, cls in [("isira_opts", isira.isira_opts), ("isira_stats", isira.isira_stats)]:
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + struct + ";", text).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-        fields = re.findall(r"(\w+)\s*[,;]", body)
+        fields = re.findall(r"(\w+)\s*(?:\[\s*\d+\s*\])?\s*[,;]", body)
         assert fields == [f for f, _ in cls._fields_], struct
 
 
