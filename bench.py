@@ -70,6 +70,8 @@ def parse(argv=None):
                    help="solver option key=value applied to every solver (e.g. reorder=1)")
     p.add_argument("--graph-cache", default=None,
                    help="directory to keep the generated graph in (.npz), reused by later runs")
+    p.add_argument("--batch-threads", type=int, default=0,
+                   help="host threads of the batched solve (0: the library default, min(G, 64))")
     return p.parse_args(argv)
 
 
@@ -501,7 +503,7 @@ def run_batch(args):
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = b.solve(k, rel_tol=rel)
+        st = b.solve(k, rel_tol=rel, n_threads=args.batch_threads)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
@@ -521,7 +523,7 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
             "config": {"workload": f"batch256 k={k} mixed", "graph": spec["desc"], "graphs": len(graphs),
                        "sum_n": int(sum(g.n for g in graphs)), "sum_nnz": int(sum(g.nnz for g in graphs)),
-                       "resid_rel": rel},
+                       "resid_rel": rel, "host_threads": args.batch_threads or min(len(graphs), 64)},
             "batch": {"status": st, "max_true_resid_rel": max_res, "inner_iters_max": int(iters_max),
                       "graphs_on_rank0": len(graphs), "sharding": "greedy by nnz + 10 n, no collective",
                       # the batch can finish no sooner than its slowest graph's own solve (a chain of

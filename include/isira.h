@@ -111,10 +111,16 @@ typedef struct {
                              with damped Jacobi smoothing), standing in for combinatorial multigrid,
                              deflated by projection: inv(P) = Pi inv(M) Pi + Vh diag(1/(lambda - sigma +
                              delta)) Vh^T, Pi = I - Vh Vh^T;
-                             -1 (default): automatic: on graphs with n >= 100000 and maximum degree
+                             -1 (default): automatic: on graphs with n >= 20000 and maximum degree
                              <= 64, one timed inner solve with each at create, the faster is kept;
                              the diagonal elsewhere */
     double ml_alpha;      /* multilevel: over-correction factor of the coarse-grid correction; <= 0: 1.5 */
+    int rr_arrow;         /* 1 (default): after one expansion of a diagonalised H, solve the
+                             Rayleigh-Ritz step as an arrowhead eigenproblem (secular equation,
+                             see isira_sym_eig_warm); 0: parallel Jacobi at every step */
+    int blocking_sync;    /* 1: the calling thread sleeps while it waits for the GPU (a blocking-sync
+                             event) instead of spinning, so many solver threads can share few cores
+                             (the batch calls set it); 0 (default): spin, the lowest wake-up latency */
 } isira_opts;
 
 typedef struct {
@@ -152,6 +158,10 @@ typedef struct {
     int ml_levels;                /* levels of the multilevel hierarchy in use (0: none) */
     double precond_probe_ms[2];   /* automatic choice: the timed inner solve with the diagonal and with
                                      the multilevel preconditioner (0: not probed) */
+    int rr_arrow;                 /* Rayleigh-Ritz steps of the last solve done by the arrowhead path */
+    int rr_jacobi;                /* ... done by parallel Jacobi (first steps, refusals, rr_arrow = 0) */
+    int rr_refused;               /* arrowhead attempts refused because Q0^T H Q0 was not diagonal to
+                                     rounding (each then ran Jacobi) */
 } isira_stats;
 
 /* Fills *opts with the defaults listed above (precision = ISIRA_MIXED). */
@@ -246,6 +256,27 @@ ISIRA_API isira_status isira_precond_apply(isira_handle h, int precision, const 
  * its largest-magnitude entry (first on ties) is positive.  stream as above. */
 ISIRA_API isira_status isira_sym_eig(int k, const double* d_H, double* d_theta, double* d_S, void* stream);
 
+/* Convergence history of the last isira_solve: ||r||_2 of the current Ritz pair at every outer step
+ * (Algorithm 2's residual, the quantity of the lock test), in step order.  Copies min(cap, steps)
+ * values to h_rnorm (host array) and the number of steps to *count (may be NULL).  The paper's
+ * Fig. 2 plots this kind of history. */
+ISIRA_API isira_status isira_residual_history(isira_handle h, double* h_rnorm, int cap, int* count);
+
+/* The Rayleigh-Ritz step of Algorithm 2 as isira_solve takes it after one expansion (opts.rr_arrow):
+ * H = [H0 h; h^T eta] (k-by-k, column-major, 2 <= k <= 64, not modified) where d_S's leading
+ * warm_w-by-warm_w block (ld k) holds orthonormal eigenvectors Q0 of H0 = H(0:warm_w, 0:warm_w);
+ * warm_w = k - 1 (one new row and column) or k (no new one).  Then diag(Q0, 1)^T H diag(Q0, 1) is an
+ * arrowhead matrix, whose eigenvalues are the roots of its secular equation; the eigenvectors are
+ * formed as Gu and Eisenstat (1995) do, from a z recomputed from the roots, so they are numerically
+ * orthogonal.  Poles with negligible z, and pairs of poles closer than 8 eps max|entry|, deflate.
+ * Output as isira_sym_eig (d_theta ascending, d_S overwritten by the k eigenvectors, sign rule).
+ * If Q0^T H0 Q0 is not diagonal to a few rounding errors the arrowhead path refuses and parallel
+ * Jacobi (isira_sym_eig, warm-started from Q0) produces the result instead; *path (may be NULL)
+ * receives 1 for the arrowhead path, 0 for Jacobi.  Allocates a small device scratch and
+ * synchronises the stream. */
+ISIRA_API isira_status isira_sym_eig_warm(int k, int warm_w, const double* d_H, double* d_theta, double* d_S,
+                                          int* path, void* stream);
+
 /* ---------------------------------------------------------------------------------
  * Batched solves: many independent graphs of uneven size (Algorithm 2 for each graph).
  * Every graph gets its own solver (as isira_create) and its own CUDA stream; a pool of host
@@ -257,14 +288,15 @@ ISIRA_API isira_status isira_sym_eig(int k, const double* d_H, double* d_theta, 
 typedef struct isira_batch_s* isira_batch;
 
 /* G >= 1 graphs; h_n, h_nnz: host arrays of G sizes; d_row_ptr, d_col_idx: host arrays of G
- * device pointers.  opts as in isira_create (NULL = defaults), applied to every graph. */
+ * device pointers.  opts as in isira_create (NULL = defaults), applied to every graph, with
+ * blocking_sync forced to 1 (the pool runs more threads than the host has cores). */
 ISIRA_API isira_status isira_batch_create(isira_batch* out, int G, const int64_t* h_n, const int64_t* h_nnz,
                                           const int64_t* const* d_row_ptr, const int32_t* const* d_col_idx,
                                           const isira_opts* opts);
 
 /* Solves every graph for its k smallest positive eigenpairs with initial shift sigma and the
  * absolute tolerance tol_rel * (2 * max degree of that graph).  n_threads host threads
- * (<= 0: min(G, 16)).  Returns ISIRA_OK if every graph succeeded, else the first failing
+ * (<= 0: min(G, 64)).  Returns ISIRA_OK if every graph succeeded, else the first failing
  * status; per-graph statuses via isira_batch_status. */
 ISIRA_API isira_status isira_batch_solve(isira_batch b, int k, double sigma, double tol_rel, int n_threads);
 

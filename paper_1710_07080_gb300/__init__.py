@@ -32,7 +32,7 @@ ISIRA_MIXED = 1
 EXPORTED = ["isira_default_opts", "isira_error_string", "isira_create", "isira_create_weighted", "isira_solve",
             "isira_eigpairs",
             "isira_get_stats", "isira_set_profiling", "isira_destroy", "isira_apply_operator",
-            "isira_inner_solve", "isira_sym_eig", "isira_apply_operator_noalloc", "isira_batch_create",
+            "isira_inner_solve", "isira_sym_eig", "isira_sym_eig_warm", "isira_residual_history", "isira_apply_operator_noalloc", "isira_batch_create",
             "isira_precond_apply",
             "isira_batch_solve", "isira_batch_status", "isira_batch_eigpairs", "isira_batch_get_stats",
             "isira_batch_destroy"]
@@ -45,7 +45,8 @@ class isira_opts(C.Structure):
                 ("spmv_lanes", C.c_int), ("inner_chunk", C.c_int), ("inner_graph", C.c_int),
                 ("reorder", C.c_int), ("gather_block", C.c_int), ("hub_kb", C.c_int),
                 ("gather_sched", C.c_int), ("index_vec", C.c_int), ("gather_chunk", C.c_int), ("sell", C.c_int),
-                ("precond", C.c_int), ("ml_alpha", C.c_double)]
+                ("precond", C.c_int), ("ml_alpha", C.c_double), ("rr_arrow", C.c_int),
+                ("blocking_sync", C.c_int)]
 
 
 class isira_stats(C.Structure):
@@ -59,7 +60,8 @@ class isira_stats(C.Structure):
                 ("gather_block", C.c_int), ("hub_bytes", C.c_int), ("hub_timeouts", C.c_longlong),
                 ("inner_rows_ms", C.c_double), ("inner_phase2_ms", C.c_double), ("w_columns", C.c_longlong),
                 ("sell_entries", C.c_longlong), ("max_diag", C.c_double), ("precond", C.c_int),
-                ("ml_levels", C.c_int), ("precond_probe_ms", C.c_double * 2)]
+                ("ml_levels", C.c_int), ("precond_probe_ms", C.c_double * 2), ("rr_arrow", C.c_int),
+                ("rr_jacobi", C.c_int), ("rr_refused", C.c_int)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -101,6 +103,10 @@ def _load() -> C.CDLL:
     lib.isira_precond_apply.restype = I
     lib.isira_sym_eig.argtypes = [I, P, P, P, P]
     lib.isira_sym_eig.restype = I
+    lib.isira_sym_eig_warm.argtypes = [I, I, P, P, P, C.POINTER(C.c_int), P]
+    lib.isira_sym_eig_warm.restype = I
+    lib.isira_residual_history.argtypes = [P, P, I, C.POINTER(C.c_int)]
+    lib.isira_residual_history.restype = I
     lib.isira_apply_operator_noalloc.argtypes = [I64, I64, P, P, I64, I, D, D, I, I, P, P, P, P]
     lib.isira_apply_operator_noalloc.restype = I
     lib.isira_batch_create.argtypes = [C.POINTER(P), I, P, P, P, P, C.POINTER(isira_opts)]
@@ -282,6 +288,14 @@ class Solver:
     def set_profiling(self, on: bool):
         check(lib.isira_set_profiling(self.h, int(bool(on))), "isira_set_profiling")
 
+    def residual_history(self) -> list:
+        """||r||_2 of the Ritz pair at every outer step of the last solve (isira_residual_history)."""
+        cnt = C.c_int(0)
+        check(lib.isira_residual_history(self.h, None, 0, C.byref(cnt)), "isira_residual_history")
+        buf = (C.c_double * max(1, cnt.value))()
+        check(lib.isira_residual_history(self.h, buf, cnt.value, C.byref(cnt)), "isira_residual_history")
+        return list(buf[:cnt.value])
+
     def solve(self, k: int, sigma: float = 0.0, tol: float | None = None, u0=None, rel_tol: float = 1e-8,
               raise_on_error: bool = True) -> int:
         """Algorithm 2.  tol: absolute bound on ||r||_2 (the paper's epsilon); default rel_tol * 2 max degree."""
@@ -362,6 +376,30 @@ def sym_eig(H):
     S = torch.empty((k, k), dtype=torch.float64, device=H.device)
     check(lib.isira_sym_eig(k, _ptr(Hc), _ptr(th), _ptr(S), _stream_ptr()), "isira_sym_eig")
     return th, S.t()                 # S was written column-major
+
+
+def sym_eig_warm(H, S0):
+    """Rayleigh-Ritz after one expansion (see isira_sym_eig_warm in include/isira.h): H is a symmetric
+    k-by-k CUDA float64 matrix (2 <= k <= 64) and S0 a w-by-w matrix (w = k - 1 or k) of orthonormal
+    eigenvectors of H[:w, :w].  Returns (theta, S, path), path 1 = arrowhead, 0 = Jacobi."""
+    import torch
+    if not isinstance(H, torch.Tensor) or H.dim() != 2 or H.shape[0] != H.shape[1] or not 2 <= H.shape[0] <= 64:
+        raise ValueError("H must be a square matrix of order 2..64")
+    k = H.shape[0]
+    _check_tensor(H.contiguous(), "H", (torch.float64,), (k, k))
+    if not isinstance(S0, torch.Tensor) or S0.dim() != 2 or S0.shape[0] != S0.shape[1] or S0.shape[0] not in (k - 1, k):
+        raise ValueError("S0 must be square of order k-1 or k")
+    _check_tensor(S0.contiguous(), "S0", (torch.float64,), tuple(S0.shape))
+    _check_cuda(H=H, S0=S0)
+    w = S0.shape[0]
+    Hc = H.t().contiguous()
+    S = torch.zeros((k, k), dtype=torch.float64, device=H.device)
+    S[:w, :w] = S0.t()                    # column-major, ld k
+    th = torch.empty(k, dtype=torch.float64, device=H.device)
+    path = C.c_int(-1)
+    check(lib.isira_sym_eig_warm(k, w, _ptr(Hc), _ptr(th), _ptr(S), C.byref(path), _stream_ptr()),
+          "isira_sym_eig_warm")
+    return th, S.t(), path.value
 
 
 def apply_operator_noalloc(row_ptr, col_idx, x, trim: int, sigma: float = 0.0, delta: float = 0.0, V=None,

@@ -10,6 +10,10 @@
 
 #include "../../include/isira.h"
 
+// default pool size: the threads mostly sleep on blocking-sync events, so the pool can be much
+// larger than the host's core count; it bounds how many graphs are in flight on the GPU at once
+constexpr int kBatchThreads = 64;
+
 struct isira_batch_s {
     int G = 0;
     int device = 0;
@@ -35,13 +39,17 @@ isira_status isira_batch_create(isira_batch* out, int G, const int64_t* h_n, con
     b->n.assign(h_n, h_n + G);
     b->nnz.assign(h_nnz, h_nnz + G);
     b->status.assign(G, ISIRA_ERR_NOT_SOLVED);
+    isira_opts o;
+    if (opts) o = *opts;
+    else isira_default_opts(&o);
+    o.blocking_sync = 1;
     isira_status st = ISIRA_OK;
     for (int g = 0; g < G && st == ISIRA_OK; ++g) {
         if (cudaStreamCreateWithFlags(&b->streams[g], cudaStreamNonBlocking) != cudaSuccess) {
             st = ISIRA_ERR_CUDA;
             break;
         }
-        st = isira_create(&b->h[g], h_n[g], h_nnz[g], d_row_ptr[g], d_col_idx[g], opts, b->streams[g]);
+        st = isira_create(&b->h[g], h_n[g], h_nnz[g], d_row_ptr[g], d_col_idx[g], &o, b->streams[g]);
     }
     if (st != ISIRA_OK) {
         isira_batch_destroy(b);
@@ -57,7 +65,7 @@ isira_status isira_batch_solve(isira_batch b, int k, double sigma, double tol_re
     std::vector<int> order(G);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->nnz[a] + b->n[a] > b->nnz[c] + b->n[c]; });
-    const int T = std::max(1, std::min(G, n_threads > 0 ? n_threads : 16));
+    const int T = std::max(1, std::min(G, n_threads > 0 ? n_threads : kBatchThreads));
     std::atomic<int> next(0);
     auto worker = [&]() {
         cudaSetDevice(b->device);

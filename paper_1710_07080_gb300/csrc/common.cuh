@@ -35,6 +35,7 @@ struct HostStatus {
     int inner_done;
     int inner_iters;
     int eig_sweeps;        // Jacobi sweeps used (-1: not converged)
+    int eig_path;          // Rayleigh-Ritz: 0 Jacobi, 1 arrowhead, -1 arrowhead refused (run Jacobi)
     int dev_error;         // bit 0: a gather CTA's staging copy missed its wait limit (set by the
                            // device, cleared by the host at the start of each entry point)
 };
@@ -647,6 +648,49 @@ __device__ __forceinline__ void for_each_row_gather(const RowSched& S, const T* 
     }
     if (my_row >= 0) epi(my_row, my_deg, my_sum);
 }
+
+// Gather for graphs without long rows (every row in the sliced copy, no work items): warp w walks
+// the slices w, w + W, ... (W warps in the grid), one lane per row, with the next slice's offsets
+// loaded ahead and eight independent index loads per pass.  Few registers, so a full SM of warps
+// keeps loads in flight.  A row's entries are added in slice order in two interleaved partial
+// sums, whatever the launch shape (the result does not depend on the grid).
+template <typename T, class Epi>
+__device__ __forceinline__ void slices_only_gather(const RowSched& S, const T* __restrict__ x, Epi& epi, int64_t skip) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (int)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (int)(blockDim.x >> 5);
+    const T* __restrict__ sw = S.swts<T>();
+    int64_t o0 = 0, o1 = 0;
+    if (gw < S.n_slices) { o0 = S.sell_off[gw]; o1 = S.sell_off[gw + 1]; }
+    for (int s = gw; s < S.n_slices; s += nw) {
+        const int64_t oa = o0;
+        const int wa = (int)((o1 - o0) >> 5);
+        if (s + nw < S.n_slices) { o0 = S.sell_off[s + nw]; o1 = S.sell_off[s + nw + 1]; }   // next slice
+        T s0 = 0, s1 = 0;
+        for (int q = 0; q < wa; q += 8) {
+            int32_t ia[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) ia[u] = q + u < wa ? __ldcs(S.sell_ci + oa + (int64_t)(q + u) * 32 + lane) : -1;
+            T va[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) va[u] = ia[u] >= 0 ? __ldg(x + ia[u]) : T(0);
+            if (sw) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) va[u] *= ia[u] >= 0 ? __ldcs(sw + oa + (int64_t)(q + u) * 32 + lane) : T(0);
+            }
+            s0 += (va[0] + va[1]) + (va[2] + va[3]);
+            s1 += (va[4] + va[5]) + (va[6] + va[7]);
+        }
+        const int64_t row = S.light0 + (int64_t)s * 32 + lane;
+        if (row < S.n) epi(row, 0, row == skip ? T(0) : s0 + s1);
+    }
+    if (skip >= 0 && skip < S.light0 && blockIdx.x == 0 && threadIdx.x == 0) epi(skip, 0, T(0));
+}
+
+// The slices-only kernels are used when every row is sliced: relabelling on, sliced copy on, no
+// work items.
+__host__ __device__ inline bool slices_only(const RowSched& S) { return S.sell && S.n_items == 0; }
+constexpr int kSliceBlocksPerSM = 8;
 
 // Epilogue of the plain gather: g[row] = sum over the row (0 for the skipped row).
 template <typename T>

@@ -991,6 +991,13 @@ __global__ void __launch_bounds__(kThreads) k_ml_project(InnerArgs<T> a, int ini
 #pragma unroll
         for (int e = 0; e < VN; ++e) r[e] = (r0 + e < n && r0 + e != trim) ? r[e] : T(0);
         vst(a.rin + r0, r);
+        if (a.ml_x0) {                        // the V-cycle's first smoothing step, x0 = w D^{-1} rin
+            T di[VN];
+            vld(a.ml_dinv0 + r0, di);
+#pragma unroll
+            for (int e = 0; e < VN; ++e) r[e] = a.ml_omega * r[e] * di[e];
+            vst(a.ml_x0 + r0, r);
+        }
     }
 }
 
@@ -1142,8 +1149,42 @@ __global__ void __launch_bounds__(TPB, TPB == kThreads ? 4 : 1) k_gather_vec(Row
         else { F(32); }         \
     } while (0)
 
+// slices-only gathers (every row in the sliced copy): z_k of the current iteration, or a given vector
+template <typename T>
+__global__ void __launch_bounds__(kThreads, kSliceBlocksPerSM) k_phase1_gather_s(InnerArgs<T> a) {
+    const InnerState<T>* st = a.st;
+    if (st->done) return;
+    const T* zc = (st->itn & 1) ? a.z1 : a.z0;
+    GatherStore<T> epi{a.gsum};
+    slices_only_gather<T>(a.rs, zc, epi, a.trim);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, kSliceBlocksPerSM) k_gather_vec_s(RowSched rs, const T* x, T* g,
+                                                                              int64_t skip, const int* done) {
+    if (done && *done) return;
+    GatherStore<T> epi{g};
+    slices_only_gather<T>(rs, x, epi, skip);
+}
+
+inline int slice_grid(const RowSched& rs) {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 152;
+    }
+    const int64_t want = ((int64_t)rs.n_slices + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)nsm * kSliceBlocksPerSM;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
 template <typename T>
 void inner_gather(const InnerArgs<T>& a, int lanes, cudaStream_t s) {
+    if (slices_only(a.rs)) {
+        k_phase1_gather_s<T><<<slice_grid(a.rs), kThreads, 0, s>>>(a);
+        return;
+    }
 #define LG(G, TPB) k_phase1_gather<T, G, TPB><<<a.rs.grid(), TPB, a.rs.hub_bytes, s>>>(a)
     ISIRA_GATHER_DISPATCH(lanes, a.rs.tpb, LG);
 #undef LG
@@ -1264,6 +1305,10 @@ void inner_phase2_cond(const InnerArgs<T>& a, cudaGraphConditionalHandle cond, c
 
 template <typename T>
 void inner_gather_vec(const InnerArgs<T>& a, const T* x, T* g, int lanes, const int* done, cudaStream_t s) {
+    if (slices_only(a.rs)) {
+        k_gather_vec_s<T><<<slice_grid(a.rs), kThreads, 0, s>>>(a.rs, x, g, a.trim, done);
+        return;
+    }
 #define LGV(G, TPB) k_gather_vec<T, G, TPB><<<a.rs.grid(), TPB, a.rs.hub_bytes, s>>>(a.rs, x, g, a.trim, done)
     ISIRA_GATHER_DISPATCH(lanes, a.rs.tpb, LGV);
 #undef LGV

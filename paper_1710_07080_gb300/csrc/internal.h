@@ -54,8 +54,8 @@ template <typename T> void ml_free(MlHierarchy<T>& H);
 // out = M^{-1} b, one V-cycle; kernels return at once while *done != 0 (done may be null)
 template <typename T>
 void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather, T omega, T alpha, const int* done,
-               cudaStream_t s);
-template <typename T> int ml_launches(const MlHierarchy<T>& H);
+               bool x0_ready, cudaStream_t s);
+template <typename T> int ml_launches(const MlHierarchy<T>& H, bool x0_ready);
 
 // ------------------------------------------------------------------ inner solve
 // State of one preconditioned MINRES solve (Paige & Saunders 1975) kept in device
@@ -102,6 +102,9 @@ struct InnerArgs {
     // multilevel preconditioner: stored Lanczos vectors, the projected V-cycle input, its output, and
     // D = diag(1 / (lambda_t - sigma + delta)) of the deflated directions (device, c doubles)
     T* rprev; T* rcur; T* rin; T* wv;
+    T* ml_x0;                   // level 0's x0 = w D^{-1} rin, written by the projection kernel (or null)
+    const T* ml_dinv0;          // level 0's 1 / diagonal
+    T ml_omega;
     const double* dv;
     double* partial_d;          // the partial-sum buffer viewed as doubles (FP64 Gram sums)
     T tau; int max_it;
@@ -162,6 +165,32 @@ void outer_residual(const OuterArgs& a, int k, cudaStream_t s);
 // warm_w > 0: S's leading warm_w x warm_w block holds eigenvectors of H's leading block (warm start)
 void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, int lds, HostStatus* hs, int warm_w,
                    cudaStream_t s);
+// Rayleigh-Ritz after one expansion (outer.cu): with Q0 = S(0:w, 0:w) (+) 1 diagonalising H's
+// leading w x w block, A = Q0^T H Q0 is an arrowhead matrix (diagonal D, last row and column z,
+// corner alpha); its eigenvalues are the roots of the secular equation.  Device scratch:
+struct ArrowWork {
+    double d[kMMax];            // diagonal of A's leading block (after the deflating rotations)
+    double z[kMMax];            // A's last column above the corner (zeroed where deflated)
+    double offb[kMMax];         // per column of Q0: max |off-diagonal| of Q0^T H Q0
+    double Q[kMMax * kMMax];    // Q0 with the deflating rotations applied (ld kMMax)
+    double mu[kMMax + 1];       // root j = d[org[j]] + mu[j] (org[j] < 0: root j = mu[j])
+    double zh[kMMax];           // z recomputed from the roots, per undeflated pole in ascending order
+    double alpha, znorm;
+    double rot_c[kMMax], rot_s[kMMax];
+    int rot_p[kMMax], rot_q[kMMax];
+    int pole[kMMax];            // undeflated indices in ascending order of d
+    int defl[kMMax];            // deflated indices
+    int org[kMMax + 1];
+    int m, nd, nrot;
+    int status;                 // 0 solved, 1 refused (Q0 does not diagonalise H's leading block)
+    unsigned counter;           // arrival counter of the setup kernel (returns to 0)
+};
+// k >= 2 and w in {k-1, k}.  theta, S as outer_sym_eig.  On refusal (status 1, hs->eig_path -1)
+// theta and S are left unspecified and the caller runs outer_sym_eig.
+// off_cap: the largest off-diagonal entry of Q0^T H Q0 that may be dropped (besides the relative
+// limit of a few rounding errors); launches returned in *launches.
+void outer_arrow_eig(const double* H, int ldh, int k, int w, double* theta, double* S, int lds, ArrowWork* aw,
+                     HostStatus* hs, double off_cap, int* launches, cudaStream_t s);
 // Z <- Z - Q(Q^T Z) - mean(Z) twice, then ||Z||, for Q = [U(:,0:k) V(:,0:c)]; Z already holds the
 // FP64 input.  Writes cgs_in / cgs_out to the host status.
 void outer_cgs2(const OuterArgs& a, int k, int c, cudaStream_t s);

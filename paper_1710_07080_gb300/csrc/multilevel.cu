@@ -20,9 +20,17 @@
 // Storage per level l >= 1: CSR (int32 row pointers) of the off-diagonal weights W (positive; the
 // matrix is diag(d) - W), 1/d, the cluster map of level l-1 (fine vertex -> cluster) and the member
 // lists of the clusters (CSR over the clusters).  Level 0 uses the solver's own gather for W x.
+//
+// Launches of one V-cycle: level 0 takes the gather twice (W x0 and W x1) with a restriction and a
+// prolongation / post-smoothing kernel around them (x0 itself usually comes from the caller's
+// projection kernel); each level l >= 1 takes one fused kernel down and one up, forming x0 and x1 of
+// the neighbours on the fly instead of storing them; the two coarsest levels, when small, run as
+// one CTA (k_ml_tail).  Five levels (the 128^3 grid: 2.1M, 264K, 15K, 690, 38 vertices) take 10
+// launches.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -210,38 +218,6 @@ __global__ void __launch_bounds__(kThreads) k_ml_scale(const T* __restrict__ b, 
         x[i] = i == skip ? T(0) : om * b[i] * dinv[i];
 }
 
-// (W x)_r for the rows of a coarse level, G lanes per row (strided over the row's entries, then a
-// shuffle reduction); every warp runs the same number of passes so the shuffles stay converged
-template <typename T, int G>
-__device__ __forceinline__ T csr_row_sum(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                         const T* __restrict__ w, const T* __restrict__ x, int64_t row, bool valid) {
-    T s = T(0);
-    if (valid) {
-        const int j = threadIdx.x & (G - 1);
-        for (int32_t e = rp[row] + j; e < rp[row + 1]; e += G) s += w[e] * x[ci[e]];
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    return s;
-}
-
-// coarse level: r = b - A x0 at x0 = w D^{-1} b, i.e. (1 - w) b + W x0
-template <typename T, int G>
-__global__ void __launch_bounds__(kThreads) k_ml_resid(const T* __restrict__ b, const T* __restrict__ x0,
-                                                       const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                       const T* __restrict__ w, T om, int64_t n, T* __restrict__ r,
-                                                       const int* __restrict__ done) {
-    if (done && *done) return;
-    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
-    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t passes = (n + groups - 1) / groups;
-    for (int64_t p = 0; p < passes; ++p) {
-        const int64_t row = g0 + p * groups;
-        const T s = csr_row_sum<T, G>(rp, ci, w, x0, row, row < n);
-        if (row < n && (threadIdx.x & (G - 1)) == 0) r[row] = (T(1) - om) * b[row] + s;
-    }
-}
-
 // bc[I] = sum over the members i of cluster I of (ob * b_i + add_i): level 0 passes ob = 1 - w and
 // add = W x0 (the gather), so the summand is the residual (1 - w) b + W x0; coarser levels pass ob = 0
 // and add = their residual.  One thread per cluster.
@@ -291,26 +267,6 @@ __global__ void __launch_bounds__(kThreads) k_ml_post(const T* __restrict__ b, c
     }
 }
 
-// the same on a coarse level, (W x1) from its CSR with G lanes per row
-template <typename T, int G>
-__global__ void __launch_bounds__(kThreads) k_ml_post_csr(const T* __restrict__ b, const T* __restrict__ dinv,
-                                                          const T* __restrict__ x1, const int32_t* __restrict__ rp,
-                                                          const int32_t* __restrict__ ci, const T* __restrict__ w, T om,
-                                                          int64_t n, T* __restrict__ out, const int* __restrict__ done) {
-    if (done && *done) return;
-    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
-    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t passes = (n + groups - 1) / groups;
-    for (int64_t p = 0; p < passes; ++p) {
-        const int64_t row = g0 + p * groups;
-        const T s = csr_row_sum<T, G>(rp, ci, w, x1, row, row < n);
-        if (row < n && (threadIdx.x & (G - 1)) == 0) {
-            const T xi = x1[row], di = dinv[row];
-            out[row] = xi + om * (b[row] * di - xi + s * di);
-        }
-    }
-}
-
 // coarsest level: x = A^{-1} b with the dense inverse, one warp per row (the inverse is symmetric,
 // so row i is column i: coalesced)
 template <typename T>
@@ -325,6 +281,122 @@ __global__ void __launch_bounds__(kThreads) k_ml_dense(const T* __restrict__ inv
         for (int64_t j = lane; j < n; j += 32) s += inv[j + i * n] * b[j];
         s = warp_sum(s);
         if (lane == 0) x[i] = s;
+    }
+}
+
+// Fused kernels of the levels l >= 1 (no excluded vertex there).  With x0 = w D^{-1} b formed on the
+// fly for every neighbour, the down sweep of a level is one kernel and so is the up sweep:
+//   down  bc[I] = sum_{i in I} ((1 - w) b_i + w sum_{c in N(i)} w_ic b_c / d_c)      (restricted residual)
+//   up    x1_i = w b_i / d_i + a xc[agg_i],  out_i = x1_i + w (b_i - d_i x1_i + sum_c w_ic x1_c) / d_i
+// One warp per cluster in the down sweep (a lane per member row), G lanes per row in the up sweep.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_ml_down(const T* __restrict__ b, const T* __restrict__ dinv,
+                                                      const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                      const T* __restrict__ w, const int64_t* __restrict__ mrp,
+                                                      const int32_t* __restrict__ mem, T om, int64_t nc,
+                                                      T* __restrict__ bc, const int* __restrict__ done) {
+    if (done && *done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t I = w0; I < nc; I += nw) {
+        T acc = T(0);
+        for (int64_t q = mrp[I] + lane; q < mrp[I + 1]; q += 32) {
+            const int32_t i = mem[q];
+            T s = T(0);
+            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+                const int32_t c = ci[e];
+                s += w[e] * (b[c] * dinv[c]);
+            }
+            acc += (T(1) - om) * b[i] + om * s;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) bc[I] = acc;
+    }
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kThreads) k_ml_up(const T* __restrict__ b, const T* __restrict__ dinv,
+                                                    const int32_t* __restrict__ agg, const T* __restrict__ xc,
+                                                    const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                    const T* __restrict__ w, T om, T alpha, int64_t n,
+                                                    T* __restrict__ out, const int* __restrict__ done) {
+    if (done && *done) return;
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t passes = (n + groups - 1) / groups;
+    const int j = threadIdx.x & (G - 1);
+    for (int64_t p = 0; p < passes; ++p) {
+        const int64_t row = g0 + p * groups;
+        const bool valid = row < n;
+        T s = T(0);
+        if (valid) {
+            for (int32_t e = rp[row] + j; e < rp[row + 1]; e += G) {
+                const int32_t c = ci[e];
+                s += w[e] * (om * b[c] * dinv[c] + alpha * xc[agg[c]]);
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (valid && j == 0) {
+            const T bi = b[row], di = dinv[row];
+            const T x1 = om * bi * di + alpha * xc[agg[row]];
+            out[row] = x1 + om * (bi * di - x1 + s * di);
+        }
+    }
+}
+
+// The two coarsest levels in one CTA: level t (n_t <= kMlTailMax rows, its CSR) and the dense
+// coarsest level t + 1.  Restricted residual of t, dense solve, prolongation and post-smoothing of t,
+// with the level-t vectors in shared memory; writes level t's output.
+constexpr int kMlTailMax = 4096;
+constexpr int kMlTailThreads = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kMlTailThreads) k_ml_tail(const T* __restrict__ b, const T* __restrict__ dinv,
+                                                            const int32_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ ci, const T* __restrict__ w,
+                                                            const int32_t* __restrict__ agg,
+                                                            const int64_t* __restrict__ mrp,
+                                                            const int32_t* __restrict__ mem,
+                                                            const T* __restrict__ inv, T om, T alpha, int nt, int nc,
+                                                            T* __restrict__ out, const int* __restrict__ done) {
+    if (done && *done) return;
+    extern __shared__ __align__(16) unsigned char tail_sm[];
+    T* r = reinterpret_cast<T*>(tail_sm);        // nt: residual, then x1
+    T* bc = r + nt;                              // nc
+    T* xc = bc + nc;                             // nc
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    for (int i = tid; i < nt; i += blockDim.x) {
+        T s = T(0);
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const int32_t c = ci[e];
+            s += w[e] * (b[c] * dinv[c]);
+        }
+        r[i] = (T(1) - om) * b[i] + om * s;
+    }
+    __syncthreads();
+    for (int I = wp; I < nc; I += blockDim.x / 32) {
+        T acc = T(0);
+        for (int64_t q = mrp[I] + lane; q < mrp[I + 1]; q += 32) acc += r[mem[q]];
+        acc = warp_sum(acc);
+        if (lane == 0) bc[I] = acc;
+    }
+    __syncthreads();
+    for (int I = wp; I < nc; I += blockDim.x / 32) {
+        T acc = T(0);
+        for (int J = lane; J < nc; J += 32) acc += inv[J + (int64_t)I * nc] * bc[J];
+        acc = warp_sum(acc);
+        if (lane == 0) xc[I] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < nt; i += blockDim.x) r[i] = om * b[i] * dinv[i] + alpha * xc[agg[i]];
+    __syncthreads();
+    for (int i = tid; i < nt; i += blockDim.x) {
+        T s = T(0);
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) s += w[e] * r[ci[e]];
+        const T x1 = r[i], di = dinv[i];
+        out[i] = x1 + om * (b[i] * di - x1 + s * di);
     }
 }
 
@@ -462,60 +534,79 @@ static int ml_group_grid(int64_t n, int G) {
 
 constexpr int kMlLanes = 4;          // lanes per coarse CSR row
 
+// Whether the two coarsest levels run as one k_ml_tail CTA.
+template <typename T>
+static bool ml_use_tail(const MlHierarchy<T>& H) {
+    return H.nlev >= 3 && H.lev[H.nlev - 2].n <= kMlTailMax && H.n_coarse <= kMlTailMax;
+}
+
 // out = M^{-1} b (b on level 0, n-space, the trimmed entry ignored; out may alias nothing else).
 // gather(x, g) must compute g = sum over neighbours of x for level 0 (the solver's gather).
+// x0_ready: level 0's x0 = w D^{-1} b is already in H.lev[0].x0 (written by the caller's kernel).
 template <typename T>
 void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather, T omega, T alpha, const int* done,
-               cudaStream_t s) {
+               bool x0_ready, cudaStream_t s) {
     const int L = H.nlev;
-    const T* bl = b;
-    // downward: x0 = w D^{-1} b, restrict the residual
-    for (int l = 0; l < L - 1; ++l) {
+    if (L == 1) {
+        k_ml_dense<T><<<ml_warp_grid(H.lev[0].n), kThreads, 0, s>>>(H.inv, b, H.lev[0].n, out, done);
+        return;
+    }
+    const bool tail = ml_use_tail(H);
+    const int nmid = tail ? L - 3 : L - 2;        // levels 1..nmid take the fused down / up kernels
+    MlLevel<T>& F = H.lev[0];
+    // level 0 down: x0 = w D^{-1} b, its neighbour sums by the solver's gather, restricted residual
+    if (!x0_ready)
+        k_ml_scale<T><<<ml_grid(F.n), kThreads, 0, s>>>(b, F.dinv, omega, F.n, H.skip, F.x0, done);
+    gather(F.x0, F.x, s);                                            // F.x <- W x0
+    k_ml_restrict<T><<<ml_grid(H.lev[1].n), kThreads, 0, s>>>(b, F.x, T(1) - omega, F.mrp, F.mem, H.lev[1].n,
+                                                              H.lev[1].b, done);
+    for (int l = 1; l <= nmid; ++l) {
         MlLevel<T>& D = H.lev[l];
         MlLevel<T>& C = H.lev[l + 1];
-        k_ml_scale<T><<<ml_grid(D.n), kThreads, 0, s>>>(bl, D.dinv, omega, D.n, l == 0 ? H.skip : -1, D.x0, done);
-        if (l == 0) {
-            gather(D.x0, D.x, s);                                    // D.x <- W x0
-            k_ml_restrict<T><<<ml_grid(C.n), kThreads, 0, s>>>(bl, D.x, T(1) - omega, D.mrp, D.mem, C.n, C.b, done);
-        } else {
-            k_ml_resid<T, kMlLanes><<<ml_group_grid(D.n, kMlLanes), kThreads, 0, s>>>(bl, D.x0, D.rp, D.ci, D.w,
-                                                                                        omega, D.n, D.x, done);
-            k_ml_restrict<T><<<ml_grid(C.n), kThreads, 0, s>>>(bl, D.x, T(0), D.mrp, D.mem, C.n, C.b, done);
-        }
-        bl = C.b;
+        k_ml_down<T><<<ml_warp_grid(C.n), kThreads, 0, s>>>(D.b, D.dinv, D.rp, D.ci, D.w, D.mrp, D.mem, omega, C.n,
+                                                            C.b, done);
     }
-    // coarsest
-    MlLevel<T>& Lc = H.lev[L - 1];
-    T* xc = L == 1 ? out : Lc.x;
-    k_ml_dense<T><<<ml_warp_grid(Lc.n), kThreads, 0, s>>>(H.inv, L == 1 ? b : Lc.b, Lc.n, xc, done);
-    // upward: prolong, post-smooth
-    for (int l = L - 2; l >= 0; --l) {
+    if (tail) {
+        static std::once_flag once;
+        std::call_once(once, [] {
+            cudaFuncSetAttribute(k_ml_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(T) * 3 * kMlTailMax));
+        });
+        MlLevel<T>& D = H.lev[L - 2];
+        const int nt = (int)D.n, nc = (int)H.n_coarse;
+        const int bytes = (int)(sizeof(T) * (nt + 2 * nc));
+        k_ml_tail<T><<<1, kMlTailThreads, bytes, s>>>(D.b, D.dinv, D.rp, D.ci, D.w, D.agg, D.mrp, D.mem, H.inv, omega,
+                                                      alpha, nt, nc, D.x, done);
+    } else {
+        MlLevel<T>& C = H.lev[L - 1];
+        k_ml_dense<T><<<ml_warp_grid(C.n), kThreads, 0, s>>>(H.inv, C.b, C.n, C.x, done);
+    }
+    for (int l = nmid; l >= 1; --l) {
         MlLevel<T>& D = H.lev[l];
-        const T* bd = l == 0 ? b : D.b;
-        k_ml_prolong<T><<<ml_grid(D.n), kThreads, 0, s>>>(bd, D.dinv, D.agg, xc, omega, alpha, D.n, D.x1, done);
-        T* dst = l == 0 ? out : D.x;
-        if (l == 0) {
-            gather(D.x1, D.x0, s);                                   // D.x0 <- W x1 (x0 is free now)
-            k_ml_post<T><<<ml_grid(D.n), kThreads, 0, s>>>(bd, D.dinv, D.x1, D.x0, omega, D.n, H.skip, dst, done);
-        } else {
-            k_ml_post_csr<T, kMlLanes><<<ml_group_grid(D.n, kMlLanes), kThreads, 0, s>>>(bd, D.dinv, D.x1, D.rp, D.ci,
-                                                                                          D.w, omega, D.n, dst, done);
-        }
-        xc = dst;
+        k_ml_up<T, kMlLanes><<<ml_group_grid(D.n, kMlLanes), kThreads, 0, s>>>(D.b, D.dinv, D.agg, H.lev[l + 1].x, D.rp,
+                                                                                D.ci, D.w, omega, alpha, D.n, D.x,
+                                                                                done);
     }
+    // level 0 up: prolong, neighbour sums of x1, post-smooth
+    k_ml_prolong<T><<<ml_grid(F.n), kThreads, 0, s>>>(b, F.dinv, F.agg, H.lev[1].x, omega, alpha, F.n, F.x1, done);
+    gather(F.x1, F.x0, s);                                           // F.x0 <- W x1 (x0 is free now)
+    k_ml_post<T><<<ml_grid(F.n), kThreads, 0, s>>>(b, F.dinv, F.x1, F.x0, omega, F.n, H.skip, out, done);
 }
 
 template <typename T>
-int ml_launches(const MlHierarchy<T>& H) {
-    return H.nlev <= 1 ? 1 : 6 + 5 * (H.nlev - 2) + 1;
+int ml_launches(const MlHierarchy<T>& H, bool x0_ready) {
+    if (H.nlev <= 1) return 1;
+    const int nmid = ml_use_tail(H) ? H.nlev - 3 : H.nlev - 2;
+    return (x0_ready ? 0 : 1) + 2 + 2 * nmid + 1 + 3;
 }
 
 #define ISIRA_INSTANTIATE_ML(T)                                                                              \
     template cudaError_t ml_build<T>(MlHierarchy<T>&, const int64_t*, const int32_t*, const double*, int64_t,  \
                                      int64_t, int64_t, cudaStream_t);                                        \
     template void ml_free<T>(MlHierarchy<T>&);                                                               \
-    template void ml_vcycle<T>(MlHierarchy<T>&, const T*, T*, const GatherFn<T>&, T, T, const int*, cudaStream_t); \
-    template int ml_launches<T>(const MlHierarchy<T>&);
+    template void ml_vcycle<T>(MlHierarchy<T>&, const T*, T*, const GatherFn<T>&, T, T, const int*, bool,     \
+                               cudaStream_t);                                                                \
+    template int ml_launches<T>(const MlHierarchy<T>&, bool);
 ISIRA_INSTANTIATE_ML(float)
 ISIRA_INSTANTIATE_ML(double)
 

@@ -2,6 +2,8 @@
 //
 //   residual      r = W s1 - theta1 U s1, ||r||                     (Algorithm 2, residual)
 //   sym_eig       all eigenpairs of H_k, one CTA, parallel Jacobi    (Rayleigh-Ritz)
+//   arrow_eig     the same after one expansion of a diagonalised H:   (Rayleigh-Ritz, warm start)
+//                 secular equation of the arrowhead matrix
 //   cgs2          classical Gram-Schmidt, two passes, against [U V 1] (orthonormalisation)
 //   expand        U(:,k) = u, W(:,k) = L u, H(:,k) = U^T W(:,k)      (expansion)
 //   rotate        X <- X S(:, a:b) in place, row tiles in shared memory (restart)
@@ -10,6 +12,7 @@
 // The tall-skinny kernels stage a tile of basis rows in shared memory once and use
 // it twice (row-wise update, column-wise dot products), so U and V are read once
 // per Gram-Schmidt pass.
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -271,7 +274,10 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* H, int ld
                 for (int j = best; j > i; --j) perm[j] = perm[j - 1];
                 perm[i] = t;
             }
-            if (hs) hs->eig_sweeps = (sweeps32 < 0 || sweeps64 < 0) ? -1 : sweeps32 + sweeps64;
+            if (hs) {
+                hs->eig_sweeps = (sweeps32 < 0 || sweeps64 < 0) ? -1 : sweeps32 + sweeps64;
+                hs->eig_path = 0;
+            }
         }
         __syncthreads();
         if (tid < k) {
@@ -289,7 +295,7 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* H, int ld
     if (tid == 0) {
         theta[0] = D0[0];
         S[0] = 1.0;
-        if (hs) hs->eig_sweeps = 0;
+        if (hs) { hs->eig_sweeps = 0; hs->eig_path = 0; }
     }
 }
 
@@ -299,6 +305,402 @@ void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, in
     static std::once_flag once;
     std::call_once(once, [bytes] { cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
     k_sym_eig<<<1, kEigThreads, bytes, s>>>(H, ldh, k, theta, S, lds, hs, warm_w);
+}
+
+// ------------------------------------------------------------------ Rayleigh-Ritz after one expansion
+// H = [H0 h; h^T eta] where the previous step left Q0 with Q0^T H0 Q0 diagonal.  Then
+// A = diag(Q0, 1)^T H diag(Q0, 1) = [D z; z^T alpha] (D = Q0^T H0 Q0, z = Q0^T h, alpha = eta) is an
+// arrowhead matrix, and by the Schur complement its eigenvalues are the roots of the secular equation
+//   f(lambda) = alpha - lambda - sum_i z_i^2 / (d_i - lambda),
+// one between each pair of consecutive poles d_i and one beyond each end (interlacing).  Two kinds
+// of deflation come first: a pole whose z_i is negligible is an eigenvalue with eigenvector e_i,
+// and of two poles closer than the tolerance a plane rotation zeroes one z (the other absorbs it)
+// so that one of them deflates.  The eigenvectors follow Gu and Eisenstat (SIAM J. Matrix Anal.
+// Appl. 16:172-191, 1995): a vector zhat is recomputed from the computed roots by Loewner's
+// formula, so the computed roots are the exact eigenvalues of the arrowhead with zhat, and the
+// vectors (zhat_i / (d_i - lambda), -1) are numerically orthogonal however close the roots lie.
+// The cost is O(k^2), against the O(k^3) per sweep of Jacobi; the work of each root and of each
+// zhat entry runs on its own SM, because one SM's FP64 pipe is narrow on this part.
+//   setup    one CTA per column i of Q0: one Newton-Schulz step q~_i = q_i (3/2) - Q0 Q0^T q_i / 2
+//            (keeps the warm-start basis orthonormal over many steps), d_i = q~_i^T H0 q~_i,
+//            z_i = q~_i^T h, and the largest |q_j^T H0 q~_i|, j != i; the last CTA deflates;
+//   roots    one warp per root: safeguarded Newton on (d_o - lambda) f(lambda) in coordinates
+//            centred on the nearer pole d_o, bisection when a step leaves the bracket;
+//   zhat     one warp per undeflated pole (Loewner's formula as a product of bounded ratios);
+//   vectors  one CTA per eigenpair: the vector in the arrowhead basis, its place in ascending
+//            order, S(:, place) = Q~ x with the sign rule of outer_sym_eig.
+// Q0 must diagonalise H0 to rounding: if the largest off-diagonal entry exceeds a few rounding
+// errors (or off_cap), the setup refuses (status 1) and the caller runs the Jacobi solver.
+
+constexpr double kEpsD = 2.220446049250313e-16;   // unit roundoff x 2 (machine epsilon, binary64)
+constexpr int kArrowThreads = 64;                 // >= kMMax: one thread per row of H
+constexpr int kArrowMaxIt = 200;                  // iteration limit of one root (bisection alone needs < 2100
+                                                  // halvings in the worst case; Newton ends in ~10)
+constexpr int kArrowLd = kMMax + 1;
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_prod(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Run by the last setup CTA: refusal test, ascending order, deflation, rotations of Q~.
+__device__ void arrow_deflate(int k, int w, ArrowWork* aw, HostStatus* hs, double off_cap) {
+    __shared__ double d[kMMax], z[kMMax];
+    __shared__ int ord[kMMax];
+    __shared__ double rm[3][kArrowThreads / 32];
+    __shared__ int refused, nrot_s;
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    const bool arrow = w < k;
+    double dv = 0.0, zv = 0.0, ov = 0.0;
+    if (tid < w) {
+        dv = __ldcg(aw->d + tid);
+        zv = arrow ? __ldcg(aw->z + tid) : 0.0;
+        ov = __ldcg(aw->offb + tid);
+        d[tid] = dv;
+        z[tid] = zv;
+    }
+    const double alpha = arrow ? __ldcg(&aw->alpha) : 0.0;
+    double a = warp_max(fmax(fabs(dv), fabs(zv)));
+    double o = warp_max(ov);
+    double zq = warp_sum(zv * zv);
+    if (lane == 0) { rm[0][wp] = a; rm[1][wp] = o; rm[2][wp] = zq; }
+    __syncthreads();
+    const double scale = fmax(fmax(rm[0][0], rm[0][1]), fabs(alpha));
+    const double offmax = fmax(rm[1][0], rm[1][1]);
+    if (tid == 0) {
+        aw->counter = 0u;
+        const double lim = fmin(4.0 * k * kEpsD * scale, off_cap);
+        refused = !(offmax <= lim);                       // NaN refuses too
+        aw->status = refused;
+        aw->znorm = sqrt(rm[2][0] + rm[2][1]);
+        if (hs) hs->eig_path = refused ? -1 : 1;
+    }
+    __syncthreads();
+    if (refused) return;
+    if (tid < w) {                                        // ascending order of d, ties by index
+        int r = 0;
+        for (int j = 0; j < w; ++j) r += (d[j] < dv) || (d[j] == dv && j < tid);
+        ord[r] = tid;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double tol = 8.0 * kEpsD * scale;
+        int m = 0, nd = 0, nrot = 0, last = -1;
+        for (int r = 0; r < w; ++r) {
+            const int i = ord[r];
+            if (!arrow || fabs(z[i]) <= tol) {            // z_i negligible: d_i is an eigenvalue
+                aw->defl[nd++] = i;
+                continue;
+            }
+            if (last >= 0 && d[i] - d[last] <= tol) {     // two poles within tol: rotate z_last away
+                const double zp = z[last], zi = z[i];
+                const double rr = hypot(zp, zi);
+                const double c = zi / rr, sn = -zp / rr;
+                const double dp = d[last], di = d[i];
+                d[last] = c * c * dp + sn * sn * di;
+                d[i] = sn * sn * dp + c * c * di;
+                z[last] = 0.0;
+                z[i] = rr;
+                aw->rot_p[nrot] = last;
+                aw->rot_q[nrot] = i;
+                aw->rot_c[nrot] = c;
+                aw->rot_s[nrot] = sn;
+                ++nrot;
+                aw->defl[nd++] = last;
+                aw->pole[m - 1] = i;
+            } else {
+                aw->pole[m++] = i;
+            }
+            last = i;
+        }
+        aw->m = m;
+        aw->nd = nd;
+        aw->nrot = nrot;
+        nrot_s = nrot;
+    }
+    __syncthreads();
+    if (tid < w) {
+        aw->d[tid] = d[tid];
+        aw->z[tid] = z[tid];
+        // columns p, q of Q~ <- (c q_p + s q_q, -s q_p + c q_q), in the order the rotations were made
+        for (int t = 0; t < nrot_s; ++t) {
+            const int p = aw->rot_p[t], q = aw->rot_q[t];
+            const double c = aw->rot_c[t], sn = aw->rot_s[t];
+            const double xp = __ldcg(aw->Q + tid + p * kMMax), xq = __ldcg(aw->Q + tid + q * kMMax);
+            aw->Q[tid + p * kMMax] = c * xp + sn * xq;
+            aw->Q[tid + q * kMMax] = -sn * xp + c * xq;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kArrowThreads) k_arrow_setup(const double* H, int ldh, int k, int w,
+                                                            const double* S, int lds, ArrowWork* aw,
+                                                            HostStatus* hs, double off_cap) {
+    extern __shared__ double arrow_sm[];
+    double* Qs = arrow_sm;                    // Q0, ld kArrowLd
+    double* Hs = arrow_sm + kMMax * kArrowLd; // H (symmetrised), ld kArrowLd
+    __shared__ double g[kMMax], qt[kMMax], t[kMMax];
+    __shared__ double red[3][kArrowThreads / 32];
+    __shared__ int is_last;
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5, i = blockIdx.x;
+    for (int idx = tid; idx < w * w; idx += blockDim.x) {
+        const int r = idx % w, c = idx / w;
+        Qs[r + c * kArrowLd] = S[r + (int64_t)c * lds];
+    }
+    for (int idx = tid; idx < k * k; idx += blockDim.x) {
+        const int r = idx % k, c = idx / k;
+        Hs[r + c * kArrowLd] = H[r + (int64_t)c * ldh];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < k * k; idx += blockDim.x) {
+        const int r = idx % k, c = idx / k;
+        if (r < c) {
+            const double v = 0.5 * (Hs[r + c * kArrowLd] + Hs[c + r * kArrowLd]);
+            Hs[r + c * kArrowLd] = v;
+            Hs[c + r * kArrowLd] = v;
+        }
+    }
+    if (tid < w) {                                        // g = Q0^T q_i
+        double acc = 0.0;
+        for (int r = 0; r < w; ++r) acc += Qs[r + tid * kArrowLd] * Qs[r + i * kArrowLd];
+        g[tid] = acc;
+    }
+    __syncthreads();
+    if (tid < w) {                                        // q~_i = (3/2) q_i - (1/2) Q0 g
+        double acc = 0.0;
+        for (int j = 0; j < w; ++j) acc += Qs[tid + j * kArrowLd] * g[j];
+        qt[tid] = 1.5 * Qs[tid + i * kArrowLd] - 0.5 * acc;
+    }
+    __syncthreads();
+    if (tid < w) {                                        // t = H0 q~_i
+        double acc = 0.0;
+        for (int c = 0; c < w; ++c) acc += Hs[tid + c * kArrowLd] * qt[c];
+        t[tid] = acc;
+    }
+    __syncthreads();
+    double dd = 0.0, zz = 0.0, off = 0.0;
+    if (tid < w) {
+        dd = qt[tid] * t[tid];
+        if (w < k) zz = qt[tid] * Hs[tid + w * kArrowLd];
+        if (tid != i) {
+            double acc = 0.0;
+            for (int r = 0; r < w; ++r) acc += Qs[r + tid * kArrowLd] * t[r];
+            off = fabs(acc);
+        }
+    }
+    dd = warp_sum(dd);
+    zz = warp_sum(zz);
+    off = warp_max(off);
+    if (lane == 0) { red[0][wp] = dd; red[1][wp] = zz; red[2][wp] = off; }
+    if (tid < k) aw->Q[tid + i * kMMax] = tid < w ? qt[tid] : 0.0;
+    if (i == 0 && w < k && tid < k) aw->Q[tid + w * kMMax] = tid == w ? 1.0 : 0.0;
+    __syncthreads();
+    if (tid == 0) {
+        aw->d[i] = red[0][0] + red[0][1];
+        aw->z[i] = red[1][0] + red[1][1];
+        aw->offb[i] = fmax(red[2][0], red[2][1]);
+        if (i == 0) aw->alpha = w < k ? Hs[w + w * kArrowLd] : 0.0;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(&aw->counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    arrow_deflate(k, w, aw, hs, off_cap);
+}
+
+// One warp per root j = blockIdx.x (0..m).  Root j lies between poles p_{j-1} and p_j (p_{-1} = -inf,
+// p_m = +inf).  With o the pole nearer to the root and mu = lambda - d_o:
+//   g(mu) = (alpha - d_o) - mu - S1(mu) + zeta_o / mu,   S1 = sum_{i != o} zeta_i / (delta_i - mu),
+//   h(mu) = -mu g(mu) (no pole at mu = 0), h'(mu) = -(alpha - d_o) + 2 mu + S1 + mu S2,
+// zeta_i = z_i^2, delta_i = d_i - d_o, S2 = sum_{i != o} zeta_i / (delta_i - mu)^2.  g decreases
+// through the root, so its sign keeps a bracket; Newton steps on h that leave it are replaced by
+// bisection.
+__global__ void __launch_bounds__(32) k_arrow_roots(ArrowWork* aw) {
+    if (aw->status) return;
+    const int m = aw->m, j = blockIdx.x, lane = threadIdx.x;
+    if (j > m) return;
+    const double alpha = aw->alpha;
+    if (m == 0) {
+        if (lane == 0) { aw->org[0] = -1; aw->mu[0] = alpha; }
+        return;
+    }
+    const int i0 = lane, i1 = lane + 32;
+    const double p0 = i0 < m ? aw->d[aw->pole[i0]] : 0.0, p1 = i1 < m ? aw->d[aw->pole[i1]] : 0.0;
+    const double z0 = i0 < m ? aw->z[aw->pole[i0]] : 0.0, z1 = i1 < m ? aw->z[aw->pole[i1]] : 0.0;
+    const double zeta0 = z0 * z0, zeta1 = z1 * z1;
+    auto pole_at = [&](int i) { return __shfl_sync(kFull, i < 32 ? p0 : p1, i & 31); };
+    auto zeta_at = [&](int i) { return __shfl_sync(kFull, i < 32 ? zeta0 : zeta1, i & 31); };
+    // S1, S2 over the poles other than o, centred on d_o
+    auto sums = [&](int o, double po, double mu, double& s1, double& s2) {
+        double a1 = 0.0, a2 = 0.0;
+        if (i0 < m && i0 != o) { const double den = (p0 - po) - mu, q = zeta0 / den; a1 += q; a2 += q / den; }
+        if (i1 < m && i1 != o) { const double den = (p1 - po) - mu, q = zeta1 / den; a1 += q; a2 += q / den; }
+        s1 = warp_sum(a1);
+        s2 = warp_sum(a2);
+    };
+    int o;
+    double a, b;                                          // bracket of mu (endpoint 0 = the pole itself)
+    if (j == 0) {
+        o = 0;
+        const double po = pole_at(0);
+        a = fmin(0.0, alpha - po) - 1.0625 * aw->znorm;
+        b = 0.0;
+    } else if (j == m) {
+        o = m - 1;
+        const double po = pole_at(m - 1);
+        a = 0.0;
+        b = fmax(0.0, alpha - po) + 1.0625 * aw->znorm;
+    } else {
+        const double pl = pole_at(j - 1), pr = pole_at(j);
+        const double half = 0.5 * (pr - pl);
+        double s1, s2;
+        sums(j - 1, pl, half, s1, s2);
+        const double gm = (alpha - pl) - half - s1 + zeta_at(j - 1) / half;
+        if (gm > 0.0) { o = j; a = -half; b = 0.0; }      // root in (midpoint, p_j): centre on p_j
+        else { o = j - 1; a = 0.0; b = half; }            // root in (p_{j-1}, midpoint]
+    }
+    const double po = pole_at(o), ao = alpha - po, zo = zeta_at(o);
+    double mu = 0.5 * (a + b);
+    for (int it = 0; it < kArrowMaxIt; ++it) {
+        double s1, s2;
+        sums(o, po, mu, s1, s2);
+        const double gv = ao - mu - s1 + zo / mu;
+        if (gv > 0.0) a = mu;
+        else if (gv < 0.0) b = mu;
+        else break;
+        const double h = -mu * ao + mu * mu + mu * s1 - zo;
+        const double hp = -ao + 2.0 * mu + s1 + mu * s2;
+        const double nw = mu - h / hp;
+        const double nxt = (nw > a && nw < b) ? nw : 0.5 * (a + b);
+        const bool done = fabs(nxt - mu) <= 2.0 * kEpsD * fabs(nxt) || (b - a) <= 2.0 * kEpsD * fmax(fabs(a), fabs(b));
+        mu = nxt;
+        if (done) break;
+    }
+    if (lane == 0) {
+        aw->org[j] = aw->pole[o];
+        aw->mu[j] = mu;
+    }
+}
+
+// zhat_i for undeflated pole i = blockIdx.x (ascending order), one warp:
+//   zhat_i^2 = -(lambda_i - p_i)(lambda_m - p_i) prod_{j < m, j != i} (lambda_j - p_i) / (p_j - p_i),
+// each ratio positive and bounded by interlacing; lambda_j - p_i = (d_{org j} - p_i) + mu_j.
+__global__ void __launch_bounds__(32) k_arrow_zhat(ArrowWork* aw) {
+    if (aw->status) return;
+    const int m = aw->m, i = blockIdx.x, lane = threadIdx.x;
+    if (i >= m) return;
+    const double pi = aw->d[aw->pole[i]];
+    double pr = 1.0;
+    for (int j = lane; j < m; j += 32) {
+        if (j == i) continue;
+        const double num = (aw->d[aw->org[j]] - pi) + aw->mu[j];
+        const double den = aw->d[aw->pole[j]] - pi;
+        pr *= num / den;
+    }
+    pr = warp_prod(pr);
+    if (lane == 0) {
+        const double li = (aw->d[aw->org[i]] - pi) + aw->mu[i];
+        const double lm = (aw->d[aw->org[m]] - pi) + aw->mu[m];
+        const double z2 = -li * lm * pr;
+        aw->zh[i] = copysign(sqrt(fmax(z2, 0.0)), aw->z[aw->pole[i]]);
+    }
+}
+
+// Eigenpair e = blockIdx.x: e < R = (arrow ? m + 1 : 0) is root e, else deflated index defl[e - R].
+__global__ void __launch_bounds__(kArrowThreads) k_arrow_vectors(int k, int w, ArrowWork* aw, double* theta,
+                                                              double* S, int lds, HostStatus* hs) {
+    if (aw->status) return;
+    __shared__ double lam[kMMax], x[kMMax];
+    __shared__ double red[kArrowThreads / 32];
+    __shared__ int cnt[kArrowThreads / 32], arg[kArrowThreads / 32];
+    __shared__ double amax[kArrowThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5, e = blockIdx.x;
+    const bool arrow = w < k;
+    const int m = aw->m, R = arrow ? m + 1 : 0;
+    if (tid < k) {
+        double v;
+        if (tid < R) { const int og = aw->org[tid]; v = og >= 0 ? aw->d[og] + aw->mu[tid] : aw->mu[tid]; }
+        else v = aw->d[aw->defl[tid - R]];
+        lam[tid] = v;
+        x[tid] = 0.0;
+    }
+    __syncthreads();
+    const double le = lam[e];
+    int c = 0;
+    if (tid < k) c = (lam[tid] < le) || (lam[tid] == le && tid < e);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if (lane == 0) cnt[wp] = c;
+    // the vector in the arrowhead basis
+    double xv = 0.0;
+    if (e >= R) {
+        if (tid == aw->defl[e - R]) xv = 1.0;
+    } else if (m == 0) {
+        if (tid == w) xv = 1.0;
+    } else {
+        const double de = aw->d[aw->org[e]], me = aw->mu[e];
+        if (tid < m) xv = aw->zh[tid] / ((aw->d[aw->pole[tid]] - de) - me);
+        else if (tid == m) xv = -1.0;
+    }
+    double ss = warp_sum(xv * xv);
+    if (lane == 0) red[wp] = ss;
+    __syncthreads();
+    const int pos = cnt[0] + cnt[1];
+    const double inv = 1.0 / sqrt(red[0] + red[1]);
+    if (e >= R || m == 0) {
+        if (xv != 0.0) x[tid] = xv;
+    } else {
+        if (tid < m) x[aw->pole[tid]] = xv * inv;
+        else if (tid == m) x[w] = -inv;
+    }
+    __syncthreads();
+    double y = 0.0;
+    if (tid < k)
+        for (int cc = 0; cc < k; ++cc) y += aw->Q[tid + cc * kMMax] * x[cc];
+    // sign: the largest-magnitude entry (first on ties) positive
+    double av = tid < k ? fabs(y) : -1.0;
+    int ai = tid;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(kFull, av, o);
+        const int oi = __shfl_xor_sync(kFull, ai, o);
+        if (ov > av || (ov == av && oi < ai)) { av = ov; ai = oi; }
+    }
+    if (lane == 0) { amax[wp] = av; arg[wp] = ai; }
+    __syncthreads();
+    const int im = (amax[1] > amax[0]) ? arg[1] : arg[0];
+    __shared__ double ysel;
+    if (tid == im) ysel = y;
+    __syncthreads();
+    const double sg = ysel < 0.0 ? -1.0 : 1.0;
+    if (tid < k) S[tid + (int64_t)pos * lds] = sg * y;
+    if (tid == 0) {
+        theta[pos] = le;
+        if (hs && e == 0) hs->eig_sweeps = 0;
+    }
+}
+
+void outer_arrow_eig(const double* H, int ldh, int k, int w, double* theta, double* S, int lds, ArrowWork* aw,
+                     HostStatus* hs, double off_cap, int* launches, cudaStream_t s) {
+    const int bytes = (int)(sizeof(double) * 2 * kMMax * kArrowLd);
+    static std::once_flag once;
+    std::call_once(once, [bytes] { cudaFuncSetAttribute(k_arrow_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
+    k_arrow_setup<<<w, kArrowThreads, bytes, s>>>(H, ldh, k, w, S, lds, aw, hs, off_cap);
+    int nl = 1;
+    if (w < k) {
+        k_arrow_roots<<<w + 1, 32, 0, s>>>(aw);
+        k_arrow_zhat<<<w, 32, 0, s>>>(aw);
+        nl += 2;
+    }
+    k_arrow_vectors<<<k, kArrowThreads, 0, s>>>(k, w, aw, theta, S, lds, hs);
+    if (launches) *launches = nl + 1;
 }
 
 // ------------------------------------------------------------------ tall-skinny passes (orthonormalisation, H column)
@@ -501,7 +903,25 @@ __global__ void __launch_bounds__(kThreads) k_laplacian_rows(OuterArgs a, const 
         y[r] = row_degree<double>(a.rs, r) * x[r] - a.gsum[r];
 }
 
+__global__ void __launch_bounds__(kThreads, kSliceBlocksPerSM) k_gather_plain_s(RowSched rs, const double* x, double* g) {
+    GatherStore<double> epi{g};
+    slices_only_gather<double>(rs, x, epi, -1);
+}
+
 static void outer_gather(const OuterArgs& a, const double* x, int lanes, cudaStream_t s) {
+    if (slices_only(a.rs)) {
+        static int nsm = 0;
+        if (nsm == 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                nsm = 152;
+        }
+        const int64_t want = ((int64_t)a.rs.n_slices + kWarps - 1) / kWarps;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * kSliceBlocksPerSM));
+        k_gather_plain_s<<<grid, kThreads, 0, s>>>(a.rs, x, a.gsum);
+        return;
+    }
 #define LG(G, TPB) k_gather_plain<G, TPB><<<a.rs.grid(), TPB, a.rs.hub_bytes, s>>>(a.rs, x, a.gsum)
     ISIRA_GATHER_DISPATCH(lanes, a.rs.tpb, LG);
 #undef LG

@@ -18,6 +18,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/isira.h"
 #include "internal.h"
 
@@ -47,6 +49,15 @@ struct InnerBuffers {
 };
 
 }  // namespace
+
+// NVTX range over one phase of Algorithm 2 (visible in Nsight Systems / Compute timelines; a
+// no-op without a tool attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct isira_handle_s {
     int64_t n = 0, nnz = 0, ld = 0;
@@ -98,6 +109,7 @@ struct isira_handle_s {
     double* R = nullptr;
     double* Z = nullptr;
     double* dscratch = nullptr;
+    ArrowWork* arrow = nullptr;   // scratch of the warm-start Rayleigh-Ritz path
     double* gsum = nullptr;       // gather output, n doubles (shared by both precisions)
     double* partial = nullptr;
     size_t partial_elems = 0;
@@ -114,11 +126,13 @@ struct isira_handle_s {
     float* Vt_f = nullptr;
     // results
     std::vector<double> lam;
+    std::vector<double> rhist;    // ||r|| of every outer step of the last solve
     int n_locked = 0;
     bool solved = false;
     isira_stats stats{};
     int profiling = 0;
     std::vector<cudaEvent_t> ev;
+    cudaEvent_t sync_ev = nullptr;   // blocking-sync event of sync() when opts.blocking_sync = 1
     // device-driven inner loop: one instantiated graph per deflation-rank bucket (c = 0, <=8, <=12, <=16, <=24, <=32)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t inner_graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -140,6 +154,8 @@ void alloc_inner(isira_handle h, InnerBuffers<T>& b) {
     ck(cudaMemsetAsync(b.base, 0, sizeof(T) * (size_t)h->ld * nvec, h->stream));
     ck(cudaMemsetAsync(b.st, 0, sizeof(InnerState<T>), h->stream));
 }
+
+constexpr double kMlOmega = 2.0 / 3.0;     // damping of the Jacobi smoother of the V-cycle
 
 template <typename T>
 InnerArgs<T> make_args(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* Vt, int64_t ldv, double tau,
@@ -174,6 +190,11 @@ InnerArgs<T> make_args(isira_handle h, InnerBuffers<T>& b, double sigma, int c, 
         a.rin = b.ml + 2 * ld;
         a.wv = b.ml + 3 * ld;
         a.dv = h->ml_dv;
+        if (b.H.nlev >= 2) {
+            a.ml_x0 = b.H.lev[0].x0;
+            a.ml_dinv0 = b.H.lev[0].dinv;
+        }
+        a.ml_omega = (T)kMlOmega;
     }
     a.tau = (T)tau;
     a.max_it = max_it;
@@ -201,7 +222,12 @@ OuterArgs make_outer(isira_handle h) {
 }
 
 void sync(isira_handle h) {
-    ck(cudaStreamSynchronize(h->stream));
+    if (h->sync_ev) {                     // the thread sleeps until the stream reaches the event
+        ck(cudaEventRecord(h->sync_ev, h->stream));
+        ck(cudaEventSynchronize(h->sync_ev));
+    } else {
+        ck(cudaStreamSynchronize(h->stream));
+    }
     ck(cudaGetLastError());
     if (h->hs && (static_cast<volatile HostStatus*>(h->hs)->dev_error & 1))
         throw StatusError{ISIRA_ERR_DEVICE_TIMEOUT};
@@ -319,7 +345,6 @@ int run_inner(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const T* 
 }
 
 // ------------------------------------------------------------------ multilevel-preconditioned inner solve
-constexpr double kMlOmega = 2.0 / 3.0;     // damping of the Jacobi smoother of the V-cycle
 
 template <typename T>
 void ensure_ml(isira_handle h, InnerBuffers<T>& b) {
@@ -345,7 +370,8 @@ void ml_iteration(isira_handle h, InnerBuffers<T>& b, const InnerArgs<T>& a, cud
     ml_phase1<T>(a, s);
     ml_phase2a<T>(a, 0, s);
     ml_project<T>(a, 0, s);
-    ml_vcycle<T>(b.H, a.c > 0 ? a.rin : a.rcur, a.wv, gather, (T)kMlOmega, ml_alpha<T>(h), done, s);
+    ml_vcycle<T>(b.H, a.c > 0 ? a.rin : a.rcur, a.wv, gather, (T)kMlOmega, ml_alpha<T>(h), done,
+                 a.c > 0 && a.ml_x0 != nullptr, s);
     ml_phase2b<T>(a, 0, cond, has_cond, s);
     ml_phase2c<T>(a, 0, s);
 }
@@ -375,7 +401,9 @@ cudaGraphExec_t build_ml_graph(isira_handle h, InnerBuffers<T>& b, const InnerAr
 }
 
 template <typename T>
-int ml_launches_per_iteration(const InnerBuffers<T>& b, int c) { return 6 + (c > 0 ? 1 : 0) + ml_launches(b.H); }
+int ml_launches_per_iteration(const InnerBuffers<T>& b, int c) {
+    return 6 + (c > 0 ? 1 : 0) + ml_launches(b.H, c > 0 && b.H.nlev >= 2);
+}
 
 // One inner solve with the multilevel preconditioner; same contract as run_inner.  lam: the
 // locked eigenvalues of the deflation columns (host, c values; null: taken as 0).
@@ -396,7 +424,8 @@ int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const 
     ml_inner_prep<T>(a, R, rnorm_dev, s);
     ml_phase2a<T>(a, 1, s);
     ml_project<T>(a, 1, s);
-    ml_vcycle<T>(b.H, c > 0 ? a.rin : a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), nullptr, s);
+    ml_vcycle<T>(b.H, c > 0 ? a.rin : a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), nullptr,
+                 c > 0 && a.ml_x0 != nullptr, s);
     ml_phase2b<T>(a, 1, cudaGraphConditionalHandle{}, 0, s);
     ml_phase2c<T>(a, 1, s);
     const int per_it = ml_launches_per_iteration(b, c);
@@ -423,7 +452,8 @@ int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const 
             if (prof) ck(cudaEventRecord(h->ev[4 * i + 2], s));
             ml_phase2a<T>(a, 0, s);
             ml_project<T>(a, 0, s);
-            ml_vcycle<T>(b.H, c > 0 ? a.rin : a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), &a.st->done, s);
+            ml_vcycle<T>(b.H, c > 0 ? a.rin : a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), &a.st->done,
+                         c > 0 && a.ml_x0 != nullptr, s);
             ml_phase2b<T>(a, 0, cudaGraphConditionalHandle{}, 0, s);
             ml_phase2c<T>(a, 0, s);
             if (prof) ck(cudaEventRecord(h->ev[4 * i + 3], s));
@@ -459,7 +489,7 @@ int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const 
 }
 
 // Preconditioner of the inner solve.  precond = 0 / 1 force the diagonal / the multilevel one.
-// precond = -1 (automatic): graphs with n >= 100000 and maximum degree <= 64 (mesh-like: the
+// precond = -1 (automatic): graphs with n >= 20000 and maximum degree <= 64 (mesh-like: the
 // multilevel hierarchy's coarse rows stay short, and its setup is amortised) get one timed inner
 // solve with each preconditioner (shift 0, no deflation, tau_inner, a seeded right-hand side) and
 // keep the faster; every other graph keeps the diagonal.
@@ -489,7 +519,7 @@ void choose_preconditioner(isira_handle h) {
         build();
         h->use_ml = true;
     }
-    if (pc != -1 || h->n < 100000 || h->max_degree > 64) return;
+    if (pc != -1 || h->n < 20000 || h->max_degree > 64) return;
     build();
     OuterArgs oa = make_outer(h);
     outer_random(oa, h->opts.seed, 7777, h->stream);            // right-hand side in Z, copied to R
@@ -644,7 +674,8 @@ void autotune_gather(isira_handle h) {
     // default (untimed) shape: the first candidate
     apply_gather_shape(h, shapes[0].first, shapes[0].second);
     h->lanes = lanes0;
-    if (h->n < 100000 || (shapes.size() == 1 && (lanes_fixed || rs.sell))) return;
+    // the slices-only kernels ignore the launch shape (their grid is one full wave of 256-thread CTAs)
+    if (h->n < 100000 || slices_only(rs) || (shapes.size() == 1 && (lanes_fixed || rs.sell))) return;
     int dev = 0;
     ck(cudaGetDevice(&dev));
     auto ilog2 = [](double v) { return (int)std::floor(std::log2(std::max(1.0, v))); };
@@ -691,7 +722,7 @@ void free_handle(isira_handle h) {
     if (!h) return;
     void* ptrs[] = {h->own_w, h->wf, h->degwd, h->degwf, h->sell_wd, h->sell_wf, h->gsum, h->deg32, h->sell_off, h->sell_ci, h->own_rp, h->own_ci, h->perm, h->inv, h->item_row, h->item_k, h->item_partial,
                     h->item_count, h->warp_start, h->U, h->W, h->V, h->H, h->theta, h->S, h->R, h->Z, h->dscratch,
-                    h->partial, h->counter, h->Gm, h->Cinv, h->lam_dev, h->tres_dev, h->fb.base, h->fb.st,
+                    h->arrow, h->partial, h->counter, h->Gm, h->Cinv, h->lam_dev, h->tres_dev, h->fb.base, h->fb.st,
                     h->db.base, h->db.st, h->Vt_f, h->fb.ml, h->db.ml, h->ml_dv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -701,6 +732,7 @@ void free_handle(isira_handle h) {
         if (g) cudaGraphExecDestroy(g);
     if (h->hs) cudaFreeHost(h->hs);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->sync_ev) cudaEventDestroy(h->sync_ev);
     for (cudaGraphExec_t g : h->inner_graph)
         if (g) cudaGraphExecDestroy(g);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -768,7 +800,7 @@ void precond_apply_t(isira_handle h, InnerBuffers<T>& b, const T* d_x, T* d_y) {
     if (h->perm) to_internal<T>(d_x, h->perm, h->n, xin, s);
     else ck(cudaMemcpyAsync(xin, d_x, sizeof(T) * h->n, cudaMemcpyDeviceToDevice, s));
     GatherFn<T> gather = [&](const T* x, T* g, cudaStream_t st) { inner_gather_vec<T>(a, x, g, h->lanes, nullptr, st); };
-    ml_vcycle<T>(b.H, xin, yout, gather, (T)kMlOmega, ml_alpha<T>(h), nullptr, s);
+    ml_vcycle<T>(b.H, xin, yout, gather, (T)kMlOmega, ml_alpha<T>(h), nullptr, false, s);
     if (h->perm) to_external<T>(yout, h->perm, h->n, d_y, s);
     else ck(cudaMemcpyAsync(d_y, yout, sizeof(T) * h->n, cudaMemcpyDeviceToDevice, s));
     sync(h);
@@ -804,6 +836,8 @@ void isira_default_opts(isira_opts* o) {
     o->sell = 1;
     o->precond = -1;
     o->ml_alpha = 0.0;
+    o->rr_arrow = 1;
+    o->blocking_sync = 0;
 }
 
 const char* isira_error_string(isira_status s) {
@@ -1010,6 +1044,8 @@ isira_status isira_create_weighted(isira_handle* out, int64_t n, int64_t nnz, co
         ck(cudaMalloc(&h->H, sizeof(double) * kMMax * kMMax));
         ck(cudaMalloc(&h->theta, sizeof(double) * kMMax));
         ck(cudaMalloc(&h->S, sizeof(double) * kMMax * kMMax));
+        ck(cudaMalloc(&h->arrow, sizeof(ArrowWork)));
+        ck(cudaMemsetAsync(h->arrow, 0, sizeof(ArrowWork), s));
         ck(cudaMalloc(&h->R, sizeof(double) * (size_t)h->ld));
         ck(cudaMalloc(&h->Z, sizeof(double) * (size_t)h->ld));
         ck(cudaMalloc(&h->gsum, sizeof(double) * (size_t)h->ld));
@@ -1030,6 +1066,8 @@ isira_status isira_create_weighted(isira_handle* out, int64_t n, int64_t nnz, co
         int chunk = h->opts.inner_chunk > 0 ? h->opts.inner_chunk : 16;
         h->ev.resize(4 * chunk);
         for (auto& e : h->ev) ck(cudaEventCreate(&e));
+        if (h->opts.blocking_sync)
+            ck(cudaEventCreateWithFlags(&h->sync_ev, cudaEventBlockingSync | cudaEventDisableTiming));
         sync(h);
         autotune_gather(h);
         choose_preconditioner(h);
@@ -1101,8 +1139,10 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
     if (!h) return ISIRA_ERR_INVALID_ARG;
     if (d < 1 || d > kCMax || d > h->n - 2 || !(tol >= 0.0) || !std::isfinite(sigma)) return ISIRA_ERR_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
+    NvtxRange range_solve("isira_solve");
     isira_status status = ISIRA_OK;
     h->solved = false;
+    h->rhist.clear();
     clear_dev_error(h);
     try {
         const isira_opts& o = h->opts;
@@ -1133,6 +1173,9 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         h->stats.inner_phase2_ms = 0.0;
         h->stats.w_columns = 0;
         h->stats.kernel_launches = 0;
+        h->stats.rr_arrow = 0;
+        h->stats.rr_jacobi = 0;
+        h->stats.rr_refused = 0;
         (void)keep;
         h->lam.assign(d, 0.0);
         OuterArgs oa = make_outer(h);
@@ -1147,18 +1190,51 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
         double sig = sigma;
         bool gram_dirty = true;
         int warm_w = 0;   // S's leading warm_w block diagonalises H's leading block (warm start)
+        // the arrowhead path may drop off-diagonal entries of Q0^T H Q0 up to 1% of tol in 2-norm
+        const double off_cap = 0.01 * tol / kMMax;
+        int arrow_skip = 0, arrow_backoff = 1;
         while (true) {
             if (h->stats.outer_steps >= max_outer) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
             h->stats.outer_steps += 1;
             h->stats.w_columns += k;
-            outer_sym_eig(h->H, kMMax, k, h->theta, h->S, kMMax, h->hs_dev, warm_w, s);   // Rayleigh-Ritz
-            warm_w = k;
+            // Rayleigh-Ritz: the arrowhead path after one expansion of a diagonalised H, else Jacobi
+            const bool try_arrow = o.rr_arrow != 0 && k >= 2 && warm_w >= k - 1 && warm_w >= 1 && arrow_skip == 0;
+            if (arrow_skip > 0) --arrow_skip;
+            nvtxRangePushA("rayleigh_ritz+residual");
+            if (try_arrow) {
+                int nl = 0;
+                outer_arrow_eig(h->H, kMMax, k, warm_w, h->theta, h->S, kMMax, h->arrow, h->hs_dev, off_cap, &nl, s);
+                h->stats.kernel_launches += nl;
+            } else {
+                outer_sym_eig(h->H, kMMax, k, h->theta, h->S, kMMax, h->hs_dev, warm_w, s);
+                h->stats.kernel_launches += 1;
+                h->stats.rr_jacobi += 1;
+            }
             outer_residual(oa, k, s);                                              // residual
-            h->stats.kernel_launches += 2;
+            h->stats.kernel_launches += 1;
             sync(h);
+            if (try_arrow) {
+                if (hst(h)->eig_path < 0) {        // Q0 no longer diagonalises H to rounding: Jacobi
+                    outer_sym_eig(h->H, kMMax, k, h->theta, h->S, kMMax, h->hs_dev, warm_w, s);
+                    outer_residual(oa, k, s);
+                    h->stats.kernel_launches += 2;
+                    h->stats.rr_jacobi += 1;
+                    h->stats.rr_refused += 1;
+                    arrow_skip = arrow_backoff;
+                    arrow_backoff = std::min(2 * arrow_backoff, 32);
+                    sync(h);
+                } else {
+                    h->stats.rr_arrow += 1;
+                    arrow_backoff = 1;
+                }
+            }
+            nvtxRangePop();
+            warm_w = k;
             const double rn = hst(h)->rnorm, th1 = hst(h)->theta[0], th2 = hst(h)->theta[1];
+            h->rhist.push_back(rn);
             const bool exhausted = (int64_t)(k + c) >= h->n - 1;
             if (rn < tol || exhausted) {                                           // lock
+                NvtxRange range_lock("lock+purge");
                 double* vcol = h->V + (size_t)c * h->ld;
                 const bool more = (c + 1 < d);
                 if (more && k >= 2) {
@@ -1192,6 +1268,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 continue;
             }
             if (k == m) {                                                          // restart
+                NvtxRange range_restart("restart");
                 outer_rotate(oa, h->U, k, 0, q, nullptr, s);
                 outer_rotate(oa, h->W, k, 0, q, nullptr, s);
                 outer_set_diag(oa, 0, q, s);
@@ -1201,6 +1278,7 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 h->stats.restarts += 1;
             }
             // inner solve of Eq. 2.14 and back-map Eq. 2.5 -> Z
+            nvtxRangePushA("inner_solve");
             if (h->opts.precision == ISIRA_MIXED)
                 run_inner<float>(h, h->fb, sig, c, h->Vt_f, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch,
                                  true, h->lam.data());
@@ -1208,7 +1286,9 @@ isira_status isira_solve(isira_handle h, int d, double sigma, double tol, const 
                 run_inner<double>(h, h->db, sig, c, h->V, h->ld, tau, max_inner, gram_dirty, h->R, h->dscratch,
                                   true, h->lam.data());
             gram_dirty = false;
+            nvtxRangePop();
             // orthonormalise against [U V 1] and expand U, W, H
+            NvtxRange range_expand("cgs2+expand");
             if (!expand_basis(h, k, c)) { status = ISIRA_ERR_NO_CONVERGENCE; break; }
             k += 1;
         }
@@ -1357,6 +1437,40 @@ isira_status isira_sym_eig(int k, const double* d_H, double* d_theta, double* d_
     outer_sym_eig(d_H, k, k, d_theta, d_S, k, nullptr, 0, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? ISIRA_OK : ISIRA_ERR_CUDA;
+}
+
+isira_status isira_residual_history(isira_handle h, double* h_rnorm, int cap, int* count) {
+    if (!h || cap < 0 || (cap > 0 && !h_rnorm)) return ISIRA_ERR_INVALID_ARG;
+    const int nh = (int)h->rhist.size();
+    for (int i = 0; i < std::min(cap, nh); ++i) h_rnorm[i] = h->rhist[i];
+    if (count) *count = nh;
+    return ISIRA_OK;
+}
+
+isira_status isira_sym_eig_warm(int k, int warm_w, const double* d_H, double* d_theta, double* d_S, int* path,
+                                void* stream) {
+    if (k < 2 || k > kMMax || warm_w < k - 1 || warm_w > k || !d_H || !d_theta || !d_S)
+        return ISIRA_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    ArrowWork* aw = nullptr;
+    cudaError_t e = cudaMalloc(&aw, sizeof(ArrowWork));
+    if (e != cudaSuccess) return ISIRA_ERR_OOM;
+    int st = 1;
+    e = cudaMemsetAsync(aw, 0, sizeof(ArrowWork), s);
+    if (e == cudaSuccess) {
+        outer_arrow_eig(d_H, k, k, warm_w, d_theta, d_S, k, aw, nullptr, HUGE_VAL, nullptr, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, &aw->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && st != 0) {
+        outer_sym_eig(d_H, k, k, d_theta, d_S, k, nullptr, warm_w, s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    cudaFree(aw);
+    if (path) *path = st == 0 ? 1 : 0;
     return e == cudaSuccess ? ISIRA_OK : ISIRA_ERR_CUDA;
 }
 

@@ -166,6 +166,63 @@ def test_sym_eig_degenerate_and_diagonal(isira):
     np.testing.assert_allclose(S.T @ S, np.eye(k), atol=1e-13 * k)
 
 
+def _warm_case(k, kind, rng):
+    """A symmetric k x k H and orthonormal eigenvectors Q0 of its leading w x w block (w = k - 1, or k
+    for kind 'diag'), shaped to exercise each deflation of the arrowhead path."""
+    w = k if kind == "diag" else k - 1
+    B = rng.standard_normal((k, k))
+    H = B + B.T
+    if kind == "repeated":            # H0 with eigenvalues of multiplicity > 1 (rotation deflation)
+        Q, _ = np.linalg.qr(rng.standard_normal((w, w)))
+        lam0 = np.round(rng.standard_normal(w) * 2.0) / 2.0
+        H0 = (Q * lam0) @ Q.T
+        H[:w, :w] = 0.5 * (H0 + H0.T)
+    th0, Q0, _ = oracle.sym_eig(H[:w, :w])
+    if kind == "orthogonal" and w >= 2:   # new column orthogonal to half of Q0 (z_i = 0 deflation)
+        col = Q0[:, : w // 2] @ rng.standard_normal(w // 2)
+        H[:w, w] = col
+        H[w, :w] = col
+    if kind == "zero":                # new column zero: alpha is an eigenvalue as it stands
+        H[:w, w] = 0.0
+        H[w, :w] = 0.0
+    return H, Q0
+
+
+@pytest.mark.parametrize("k", [2, 3, 7, 17, 30, 50, 64])
+@pytest.mark.parametrize("kind", ["plain", "repeated", "orthogonal", "zero", "diag"])
+def test_sym_eig_warm_arrowhead_matches_oracle(isira, k, kind):
+    """Rayleigh-Ritz after one expansion (secular equation of the arrowhead matrix, Gu-Eisenstat
+    vectors) against the oracle's Jacobi eigensolver and LAPACK."""
+    rng = np.random.default_rng(1000 * k + len(kind))
+    H, Q0 = _warm_case(k, kind, rng)
+    th, S, path = isira.sym_eig_warm(torch.from_numpy(H).cuda(), torch.from_numpy(Q0).cuda())
+    th, S = th.cpu().numpy(), S.cpu().numpy()
+    assert path == 1
+    th_or, S_or, _ = oracle.sym_eig(H)
+    scale = max(1.0, np.abs(th_or).max())
+    np.testing.assert_allclose(th, th_or, atol=1e-13 * scale * k)
+    np.testing.assert_allclose(th, np.linalg.eigvalsh(H), atol=1e-13 * scale * k)
+    np.testing.assert_allclose(H @ S, S * th[None, :], atol=1e-12 * scale * k)
+    np.testing.assert_allclose(S.T @ S, np.eye(k), atol=1e-13 * k)
+    gaps = np.diff(th_or)
+    if kind == "plain" and gaps.min() > 1e-6 * scale:    # simple spectrum: unique up to the sign rule
+        np.testing.assert_allclose(S, S_or, atol=1e-9 * k)
+
+
+def test_sym_eig_warm_refuses_a_basis_that_does_not_diagonalise(isira):
+    rng = np.random.default_rng(7)
+    k = 20
+    B = rng.standard_normal((k, k))
+    H = B + B.T
+    Q0, _ = np.linalg.qr(rng.standard_normal((k - 1, k - 1)))     # orthonormal, not eigenvectors
+    th, S, path = isira.sym_eig_warm(torch.from_numpy(H).cuda(), torch.from_numpy(Q0).cuda())
+    th, S = th.cpu().numpy(), S.cpu().numpy()
+    assert path == 0
+    th_or, _, _ = oracle.sym_eig(H)
+    np.testing.assert_allclose(th, th_or, atol=1e-13 * np.abs(th_or).max() * k)
+    np.testing.assert_allclose(S.T @ S, np.eye(k), atol=1e-13 * k)
+
+
 @pytest.mark.parametrize("name", ["grid31x33", "rmat12", "er3000"])
 @pytest.mark.parametrize("sigma,c,reorder", [(0.0, 0, 0), (0.15, 2, 0), (0.15, 2, 1)])
 def test_inner_solve_fp64_matches_oracle(isira, name, sigma, c, reorder):

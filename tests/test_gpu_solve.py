@@ -131,6 +131,7 @@ def test_rmat_vs_algorithm_oracle(isira, prec, scale, reorder):
     tol = 1e-12 * normL
     res = run(isira, g, 10, prec, tol=tol, reorder=reorder)
     assert res.status == isira.ISIRA_OK
+    assert res.stats["rr_arrow"] >= 1          # the warm-start Rayleigh-Ritz path took part
     lam, V = check_pairs(g, res, 10, rel_res=1e-11)
     lam_or, V_or, st = oracle.isira(g.row_ptr, g.col_idx, 10, sg.start_vector(g.n, 1), eps=tol, tau_inner=1e-3)
     assert st["status"] == 0
@@ -168,15 +169,33 @@ def test_options_trim_drop_rank1_restart(isira):
     ref = cf.grid2d(30, 29)[1:7]
     for kw in [dict(trim_index=0), dict(trim_index=g.n - 1), dict(drop_rank1=1), dict(m=12, q=7),
                dict(delta=100.0), dict(inner_chunk=3, inner_graph=0), dict(tau_inner=1e-2), dict(reorder=1),
-               dict(reorder=1, trim_index=5)]:
+               dict(reorder=1, trim_index=5), dict(rr_arrow=0), dict(rr_arrow=0, m=12, q=7)]:
         res = run(isira, g, 6, "mixed", tol=1e-10, **kw)
         assert res.status == isira.ISIRA_OK, kw
         if "trim_index" in kw:
             assert res.stats["trim_index"] == kw["trim_index"]
+        if kw.get("rr_arrow", 1) == 0:
+            assert res.stats["rr_arrow"] == 0 and res.stats["rr_jacobi"] == res.stats["outer_steps"]
+        else:
+            assert res.stats["rr_arrow"] + res.stats["rr_jacobi"] - res.stats["rr_refused"] == res.stats["outer_steps"]
         lam, _ = check_pairs(g, res, 6)
         np.testing.assert_allclose(lam, ref, rtol=1e-9, err_msg=str(kw))
     res = run(isira, g, 6, "mixed", tol=1e-10, m=12, q=7)
     assert res.stats["restarts"] > 0
+
+
+def test_residual_history_ends_below_tol(isira):
+    """One ||r|| per outer step; every lock happens at a step whose residual is below tol."""
+    g = sg.grid2d(30, 29)
+    rp, ci = dev_graph(g)
+    u0 = torch.from_numpy(sg.start_vector(g.n, 1)).cuda()
+    with isira.Solver(rp, ci, precision=isira.ISIRA_MIXED) as s:
+        s.solve(4, tol=1e-10, u0=u0)
+        h = s.residual_history()
+        st = s.stats()
+    assert len(h) == st["outer_steps"]
+    assert all(np.isfinite(h)) and h[-1] < 1e-10
+    assert sum(1 for x in h if x < 1e-10) == st["n_locked"]
 
 
 def test_default_start_vector(isira):
