@@ -282,7 +282,7 @@ def _isnum(s):
 
 # --------------------------------------------------------------------------------------------- roofline
 
-def kernel_bytes(kind, n, Z, c, word, n_long=None, n_slices=None):
+def kernel_bytes(kind, n, Z, c, word, n_long=None, n_slices=None, ml=None):
     """Algorithmic DRAM bytes of one launch of an inner-iteration kernel (word = 4 FP32, 8 FP64):
       gather  : column indices 4Z, the gathered vector once (w n), the row sums (w n), and the row
                 structure: row_ptr 8(n+1) for CSR rows, or with the sliced light rows 8(n_long+1)
@@ -294,6 +294,18 @@ def kernel_bytes(kind, n, Z, c, word, n_long=None, n_slices=None):
                 adds 8 n.
     c is the launch's deflation rank (averaged over the timed launches)."""
     extra = 8 * n if word == 8 else 0
+    if kind == "rows_ml":      # k_ml_phase1: as rows, plus r_{k-1}; no reciprocal diagonal
+        return 4 * n + (10 + c) * word * n
+    if kind == "phase2_ml":
+        # one application of the projected multilevel preconditioner with MINRES phase 2:
+        #   ml_phase2a (4 + c) w n, ml_project (4 + c) w n, ml_phase2b (2 + c) w n, ml_phase2c (2 + c) w n;
+        #   V-cycle level 0: two gathers, restriction (2 w n + 4 n), prolongation (3 w n + 4 n),
+        #   post-smoothing (5 w n); levels below: per level two CSR sweeps 2 (4 + w) nnz_l and
+        #   (16 + 5 w) n_l of vectors, cluster maps and member lists
+        n_c, nnz_c = ml
+        struct = 8 * (n + 1) if not n_slices else 8 * (n_long + 1) + 8 * (n_slices + 1)
+        return ((26 + 4 * c) * word * n + 8 * n + 2 * (struct + 4 * Z)
+                + 2 * (4 + word) * nnz_c + (16 + 5 * word) * n_c)
     if kind == "gather":
         struct = 8 * (n + 1) if not n_slices else 8 * (n_long + 1) + 8 * (n_slices + 1)
         return struct + 4 * Z + 2 * word * n
@@ -307,6 +319,10 @@ def kernel_bytes(kind, n, Z, c, word, n_long=None, n_slices=None):
 KERNEL_NAMES = {"gather": "k_phase1_gather (trimmed-operator SpMV gather)",
                 "rows": "k_phase1 (operator row epilogue + MINRES update)",
                 "phase2": "k_phase2 (SMW preconditioner + MINRES reductions)"}
+KERNEL_NAMES_ML = {"gather": "k_phase1_gather (trimmed-operator SpMV gather)",
+                   "rows": "k_ml_phase1 (operator row epilogue + MINRES update)",
+                   "phase2": "multilevel phase 2: ml_phase2a, ml_project, one V-cycle (10-25 launches incl. "
+                             "two level-0 gathers), ml_phase2b, ml_phase2c"}
 STAT_OF = {"gather": "inner_phase1_ms", "rows": "inner_rows_ms", "phase2": "inner_phase2_ms"}
 
 GATHER_SOURCES = ["paper_1710_07080_gb300/csrc/common.cuh", "paper_1710_07080_gb300/csrc/inner_impl.cuh"]
@@ -354,16 +370,20 @@ def kernel_rooflines(st, n, Z, word, workload, prec_tag):
     nl = st["inner_phase1_timed"]
     c_avg = st["inner_phase1_csum"] / max(1, nl)
     n_slices = (n - st["n_long_rows"] + 31) // 32 if st.get("sell_entries") else None
+    ml = st.get("precond") == 1
+    names = KERNEL_NAMES_ML if ml else KERNEL_NAMES
     out = {}
     for kind in ("gather", "rows", "phase2"):
         ms = st[STAT_OF[kind]]
         avg_s = ms / 1e3 / max(1, nl)
-        b = kernel_bytes(kind, n, Z, c_avg, word, st["n_long_rows"], n_slices)
+        bkind = kind + "_ml" if ml and kind != "gather" else kind
+        b = kernel_bytes(bkind, n, Z, c_avg, word, st["n_long_rows"], n_slices,
+                         (st.get("ml_coarse_n", 0), st.get("ml_coarse_nnz", 0)))
         ach = b / avg_s / 1e9 if avg_s > 0 else None
-        out[kind] = {"kernel": KERNEL_NAMES[kind], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+        out[kind] = {"kernel": names[kind], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak if ach else None, "bytes_per_launch": b, "avg_us": avg_s * 1e6,
                      "launches_timed": nl, "total_ms": ms, "avg_deflation_rank": c_avg,
-                     "traffic": ncu_traffic(f"{kind}_{prec_tag}_{workload}")}
+                     "traffic": ncu_traffic(f"{bkind}_{prec_tag}_{workload}")}
     dom = max(out, key=lambda q: out[q]["total_ms"])
     tot = sum(v["total_ms"] for v in out.values())
     for v in out.values():
@@ -514,6 +534,33 @@ def run_batch(args):
     solve_s = [p["solve_ms"] / 1e3 for p in per]
     res = [float(b.eigpairs(g)[2].max()) for g in range(len(graphs))]
     crit = max(range(len(graphs)), key=lambda q: solve_s[q])
+    # per family (graph index mod 3: ER / 2-D grid / WS): how much sequential work each carries
+    fams = {}
+    for q, p in enumerate(per):
+        f = ("er", "grid2d", "ws")[mine[q] % 3]
+        a = fams.setdefault(f, {"graphs": 0, "sum_n": 0, "inner_iters": 0, "outer_steps": 0, "multilevel": 0,
+                                "max_inner_iters": 0})
+        a["graphs"] += 1
+        a["sum_n"] += graphs[q].n
+        a["inner_iters"] += p["inner_iters"]
+        a["outer_steps"] += p["outer_steps"]
+        a["multilevel"] += 1 if p["precond"] == 1 else 0
+        a["max_inner_iters"] = max(a["max_inner_iters"], p["inner_iters"])
+    # the graph with the most inner iterations, solved alone afterwards (not in the timed region):
+    # the batch cannot finish before this chain of dependent iterations does
+    longest = max(range(len(graphs)), key=lambda q: iters[q])
+    alone = None
+    if rank == 0:
+        rp_l, ci_l = dg[longest]
+        with isira.Solver(rp_l, ci_l, precision=isira.ISIRA_MIXED, **solver_opts(args)) as s1:
+            tol_l = rel * s1.stats()["norm_L"]
+            s1.solve(k, tol=tol_l)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s1.solve(k, tol=tol_l)
+            torch.cuda.synchronize()
+            alone = {"index": mine[longest], "n": graphs[longest].n, "inner_iters": s1.stats()["inner_iters"],
+                     "precond": s1.stats()["precond"], "solve_alone_s": time.perf_counter() - t0}
     value = max_over_ranks(statistics.mean(times), dist, dev)
     max_res = max_over_ranks(max(res), dist, dev)
     iters_max = max_over_ranks(float(max(iters)), dist, dev)
@@ -531,6 +578,7 @@ def run_batch(args):
                       "critical_graph": {"index": mine[crit], "n": graphs[crit].n, "nnz": graphs[crit].nnz,
                                          "solve_s": solve_s[crit], "inner_iters": iters[crit]},
                       "sum_of_graph_solves_s": sum(solve_s),
+                      "families": fams, "longest_chain_alone": alone,
                       "wall_over_critical": (statistics.mean(times) / solve_s[crit]) if solve_s[crit] > 0 else None}}
     b.close()
     if rank == 0:

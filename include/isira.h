@@ -162,6 +162,8 @@ typedef struct {
     int rr_jacobi;                /* ... done by parallel Jacobi (first steps, refusals, rr_arrow = 0) */
     int rr_refused;               /* arrowhead attempts refused because Q0^T H Q0 was not diagonal to
                                      rounding (each then ran Jacobi) */
+    long long ml_coarse_n;        /* multilevel: vertices of the levels below the finest, summed */
+    long long ml_coarse_nnz;      /* multilevel: stored off-diagonal entries of those levels, summed */
 } isira_stats;
 
 /* Fills *opts with the defaults listed above (precision = ISIRA_MIXED). */

@@ -61,7 +61,8 @@ class isira_stats(C.Structure):
                 ("inner_rows_ms", C.c_double), ("inner_phase2_ms", C.c_double), ("w_columns", C.c_longlong),
                 ("sell_entries", C.c_longlong), ("max_diag", C.c_double), ("precond", C.c_int),
                 ("ml_levels", C.c_int), ("precond_probe_ms", C.c_double * 2), ("rr_arrow", C.c_int),
-                ("rr_jacobi", C.c_int), ("rr_refused", C.c_int)]
+                ("rr_jacobi", C.c_int), ("rr_refused", C.c_int), ("ml_coarse_n", C.c_longlong),
+                ("ml_coarse_nnz", C.c_longlong)]
 
     def as_dict(self) -> dict:
         out = {}

@@ -23,7 +23,7 @@ struct CudaFailure {
 // ------------------------------------------------------------------ multilevel preconditioner (multilevel.cu)
 template <typename T>
 struct MlLevel {
-    int64_t n = 0;
+    int64_t n = 0, nnz = 0;                   // rows; stored off-diagonal entries (levels >= 1)
     T* dinv = nullptr;                        // 1 / diagonal (0 at the trimmed vertex of level 0)
     int32_t* rp = nullptr;                    // level >= 1: CSR of the off-diagonal weights
     int32_t* ci = nullptr;

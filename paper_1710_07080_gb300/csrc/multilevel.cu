@@ -456,6 +456,7 @@ cudaError_t ml_build(MlHierarchy<T>& H, const int64_t* d_rp, const int32_t* d_ci
             MlLevel<T>& D = H.lev[l];
             const HostLevel& A = levels[l];
             D.n = A.n;
+            D.nnz = (int64_t)A.ci.size();
             std::vector<double> dinv(l == 0 ? ld : A.n, 0.0);
             for (int64_t i = 0; i < A.n; ++i) dinv[i] = (l == 0 && i == skip) ? 0.0 : 1.0 / A.d[i];
             upload<T>(&D.dinv, dinv);

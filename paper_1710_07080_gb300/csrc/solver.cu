@@ -1098,6 +1098,18 @@ isira_status isira_create_weighted(isira_handle* out, int64_t n, int64_t nnz, co
         h->stats.max_diag = maxdiag;
         h->stats.precond = h->use_ml ? 1 : 0;
         h->stats.ml_levels = h->use_ml ? (h->opts.precision == ISIRA_MIXED ? h->fb.H.nlev : h->db.H.nlev) : 0;
+        h->stats.ml_coarse_n = 0;
+        h->stats.ml_coarse_nnz = 0;
+        if (h->use_ml) {
+            auto add = [h](const auto& lev) {
+                for (size_t l = 1; l < lev.size(); ++l) {
+                    h->stats.ml_coarse_n += lev[l].n;
+                    h->stats.ml_coarse_nnz += lev[l].nnz;
+                }
+            };
+            if (h->opts.precision == ISIRA_MIXED) add(h->fb.H.lev);
+            else add(h->db.H.lev);
+        }
         h->stats.inner_iters = 0;
         h->stats.inner_solves = 0;
         h->stats.kernel_launches = 0;
