@@ -39,6 +39,10 @@ import sys
 import tempfile
 import time
 
+# Hardware work queues of this process's CUDA context (read when the context is created): the batched
+# workload keeps up to 64 streams busy at once, which the default of 8 queues would partly serialise.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 

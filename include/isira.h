@@ -291,7 +291,9 @@ typedef struct isira_batch_s* isira_batch;
 
 /* G >= 1 graphs; h_n, h_nnz: host arrays of G sizes; d_row_ptr, d_col_idx: host arrays of G
  * device pointers.  opts as in isira_create (NULL = defaults), applied to every graph, with
- * blocking_sync forced to 1 (the pool runs more threads than the host has cores). */
+ * blocking_sync forced to 1 (the pool runs more threads than the host has cores).  The graphs' streams
+ * run concurrently only as far as the context has hardware queues: set CUDA_DEVICE_MAX_CONNECTIONS
+ * (up to 32; default 8) in the environment before the process creates its CUDA context. */
 ISIRA_API isira_status isira_batch_create(isira_batch* out, int G, const int64_t* h_n, const int64_t* h_nnz,
                                           const int64_t* const* d_row_ptr, const int32_t* const* d_col_idx,
                                           const isira_opts* opts);

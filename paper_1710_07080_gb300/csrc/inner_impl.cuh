@@ -738,20 +738,16 @@ __global__ void k_copy_vcol(const double* src, T* dst, int64_t n) {
 // P is not diagonal, so the unpreconditioned Lanczos vectors r_{k-1}, r_k are kept (buffers rprev,
 // rcur, shifted in place).  One iteration k:
 //   gather(z_k); ml_phase1: y' = ((deg - sigma) z_k - g + (sigma/n) s) / beta_k - (beta_k/beta_{k-1}) r_{k-1},
-//       the deferred w/x update, alpha' = v_k^T y', g_k = Vh^T z_k; last CTA: u1 = delta g_k / beta_k,
-//       alpha_k = alpha' + (g_k / beta_k)^T u1;
+//       the deferred w/x update, alpha' = v_k^T y'; last CTA: u1 = delta g_k / beta_k,
+//       alpha_k = alpha' + (g_k / beta_k)^T u1 with g_k = Vh^T z_k from the phase-2c launch before;
 //   ml_phase2a: r_{k+1} = y' + Vh u1 - (alpha_k / beta_k) r_k and h = Vh^T r_{k+1};
 //   ml_project: rin = r_{k+1} - Vh h (= Pi r);   V-cycle: w = M^{-1} rin;
 //   ml_phase2b: Vh^T w, r^T w; last CTA: tv = D h - Vh^T w, beta_{k+1}^2 = r^T w + h^T tv, Givens step;
-//   ml_phase2c: z_{k+1} = w + Vh tv (= Pi w + Vh D h) and 1^T z_{k+1}.
+//   ml_phase2c: z_{k+1} = w + Vh tv (= Pi w + Vh D h), 1^T z_{k+1} and g_{k+1} = Vh^T z_{k+1}.
 
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_ml_phase1(InnerArgs<T> a) {
     constexpr int VN = Vec<T>::N;
-    constexpr int NE = Ncols<NC>::value;
-    constexpr int NA = 1 + NE;
-    constexpr int TILE = kThreads * VN;
-    constexpr int QW = (NE + kWarps - 1) / kWarps;
     InnerState<T>* st = a.st;
     if (st->done) return;
     const int k = st->itn + 1;
@@ -770,19 +766,14 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase1(InnerArgs<T> a) {
     const T* __restrict__ wo1 = wbuf(a, j + 2);
     T* __restrict__ wn = wbuf(a, j);
     const T oldeps = st->w_oldeps, dlt = st->w_dlt, inv_gamma = st->w_inv_gamma, phi = st->w_phi;
-    __shared__ __align__(16) T sz[NE > 0 ? TILE : 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T acc0 = T(0);
-    T cg[QW > 0 ? QW : 1];
-#pragma unroll
-    for (int q = 0; q < (QW > 0 ? QW : 1); ++q) cg[q] = T(0);
     const int64_t n = a.rs.n, trim = a.trim;
-    for (int64_t t0 = (int64_t)blockIdx.x * TILE; t0 < n; t0 += (int64_t)gridDim.x * TILE) {
-        const int64_t r0 = t0 + (int64_t)threadIdx.x * VN;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
+    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
         T z[VN];
 #pragma unroll
         for (int e = 0; e < VN; ++e) z[e] = T(0);
-        if (r0 < n) {
+        {
             T g[VN], y[VN], rpv[VN], dgv[VN];
             vld(a.gsum + r0, g);
             vld(zc + r0, z);
@@ -816,50 +807,18 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase1(InnerArgs<T> a) {
                 vst(a.x + r0, xv);
             }
         }
-        if (NE > 0 && c > 0) {
-#pragma unroll
-            for (int e = 0; e < VN; ++e) sz[threadIdx.x * VN + e] = z[e];
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < QW; ++q) {
-                const int t = warp + q * kWarps;
-                if (t < c) {
-                    const T* col = a.Vt + (int64_t)t * a.ldv + t0;
-#pragma unroll
-                    for (int u = 0; u < TILE / (32 * VN); ++u) {
-                        const int rr = (u * 32 + lane) * VN;
-                        if (t0 + rr < n) {
-                            T v[VN];
-                            vld(col + rr, v);
-#pragma unroll
-                            for (int e = 0; e < VN; ++e) cg[q] += (t0 + rr + e < n ? v[e] : T(0)) * sz[rr + e];
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
     }
-    __shared__ T bv[NA];
-    const T a0 = block_sum0(acc0);
-    if (threadIdx.x == 0) bv[0] = a0;
-#pragma unroll
-    for (int q = 0; q < QW; ++q) {
-        const int t = warp + q * kWarps;
-        const T sg = warp_sum(cg[q]);
-        if (lane == 0 && t < NE) bv[1 + t] = t < c ? sg : T(0);
-    }
-    __syncthreads();
-    __shared__ T red[NA];
-    if (block_values_arrive<T>(bv, NE > 0 ? NA : 1, a.partial, a.pstride, a.counter)) {
-        last_block_sum(a.partial, a.pstride, gridDim.x, NE > 0 ? NA : 1, red, a.counter);
+    __shared__ T red[1];
+    T accv[1] = {acc0};
+    if (block_partials_arrive<T, 1>(accv, 1, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, 1, red, a.counter);
         if (threadIdx.x == 0) {
+            // g_k = Vh^T z_k was reduced by the phase-2c launch that wrote z_k
             const double bt = (double)beta, delta = (double)a.delta;
             double al = (double)red[0];
             for (int t = 0; t < c; ++t) {
-                const double gn = (double)red[1 + t];
+                const double gn = (double)st->g_cur[t];
                 const double u = delta * gn / bt;
-                st->g_cur[t] = (T)gn;
                 st->u1[t] = (T)u;
                 al += gn / bt * u;
             }
@@ -1056,7 +1015,8 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase2b(InnerArgs<T> a, int ini
     }
 }
 
-// z_{k+1} = w + Vh tv and its sum 1^T z_{k+1} (the next operator application's rank-one term)
+// z_{k+1} = w + Vh tv, its sum 1^T z_{k+1} (the next operator application's rank-one term) and
+// g_{k+1} = Vh^T z_{k+1} (its deflation term)
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_ml_phase2c(InnerArgs<T> a, int init) {
     constexpr int VN = Vec<T>::N;
@@ -1069,7 +1029,10 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase2c(InnerArgs<T> a, int ini
     __shared__ T ts[NE > 0 ? NE : 1];
     for (int t = threadIdx.x; t < c; t += blockDim.x) ts[t] = st->tv[t];
     __syncthreads();
-    T acc[1] = {T(0)};
+    constexpr int NA = 1 + NE;                         // 1^T z_{k+1}, Vh^T z_{k+1}
+    T acc[NA];
+#pragma unroll
+    for (int t = 0; t < NA; ++t) acc[t] = T(0);
     const int64_t n = a.rs.n, trim = a.trim;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
     for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
@@ -1090,11 +1053,24 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase2c(InnerArgs<T> a, int ini
             acc[0] += w[e];
         }
         vst(zn + r0, w);
+        // Vh^T z_{k+1} for the next operator application (the columns are still in L1)
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {
+            if (t < c) {
+                T v[VN];
+                vld(a.Vt + (int64_t)t * a.ldv + r0, v);
+#pragma unroll
+                for (int e = 0; e < VN; ++e) acc[1 + t] += v[e] * w[e];
+            }
+        }
     }
-    __shared__ T red[1];
-    if (block_partials_arrive<T, 1>(acc, 1, a.partial, a.pstride, a.counter)) {
-        last_block_sum(a.partial, a.pstride, gridDim.x, 1, red, a.counter);
-        if (threadIdx.x == 0) st->s_cur = red[0];
+    __shared__ T red[NA];
+    if (block_partials_arrive<T, NA>(acc, NE > 0 ? NA : 1, a.partial, a.pstride, a.counter)) {
+        last_block_sum(a.partial, a.pstride, gridDim.x, NE > 0 ? NA : 1, red, a.counter);
+        if (threadIdx.x == 0) {
+            st->s_cur = red[0];
+            for (int t = 0; t < c; ++t) st->g_cur[t] = red[1 + t];
+        }
     }
 }
 

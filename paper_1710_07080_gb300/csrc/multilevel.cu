@@ -288,29 +288,28 @@ __global__ void __launch_bounds__(kThreads) k_ml_dense(const T* __restrict__ inv
 // fly for every neighbour, the down sweep of a level is one kernel and so is the up sweep:
 //   down  bc[I] = sum_{i in I} ((1 - w) b_i + w sum_{c in N(i)} w_ic b_c / d_c)      (restricted residual)
 //   up    x1_i = w b_i / d_i + a xc[agg_i],  out_i = x1_i + w (b_i - d_i x1_i + sum_c w_ic x1_c) / d_i
-// One warp per cluster in the down sweep (a lane per member row), G lanes per row in the up sweep.
+// On levels l >= 1 the rows are ordered by cluster (ml_build), so the members of cluster I are the
+// rows mrp[I] .. mrp[I+1]-1 and their entries one contiguous CSR range: one warp per cluster, lanes
+// striding over the rows and over the entries (coalesced), G lanes per row in the up sweep.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_ml_down(const T* __restrict__ b, const T* __restrict__ dinv,
                                                       const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                                       const T* __restrict__ w, const int64_t* __restrict__ mrp,
-                                                      const int32_t* __restrict__ mem, T om, int64_t nc,
-                                                      T* __restrict__ bc, const int* __restrict__ done) {
+                                                      T om, int64_t nc, T* __restrict__ bc,
+                                                      const int* __restrict__ done) {
     if (done && *done) return;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t I = w0; I < nc; I += nw) {
-        T acc = T(0);
-        for (int64_t q = mrp[I] + lane; q < mrp[I + 1]; q += 32) {
-            const int32_t i = mem[q];
-            T s = T(0);
-            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
-                const int32_t c = ci[e];
-                s += w[e] * (b[c] * dinv[c]);
-            }
-            acc += (T(1) - om) * b[i] + om * s;
+        const int64_t r_beg = mrp[I], r_end = mrp[I + 1];
+        T own = T(0), s = T(0);
+        for (int64_t i = r_beg + lane; i < r_end; i += 32) own += b[i];
+        for (int32_t e = rp[r_beg] + lane; e < rp[r_end]; e += 32) {
+            const int32_t c = ci[e];
+            s += w[e] * (b[c] * dinv[c]);
         }
-        acc = warp_sum(acc);
+        const T acc = warp_sum((T(1) - om) * own + om * s);
         if (lane == 0) bc[I] = acc;
     }
 }
@@ -449,6 +448,39 @@ cudaError_t ml_build(MlHierarchy<T>& H, const int64_t* d_rp, const int32_t* d_ci
             aggs.push_back(std::move(agg));
             levels.push_back(std::move(C));
         }
+        // Order the rows of every level l >= 1 that has a next level by cluster (stable), from the
+        // coarse end down, so that cluster ids are final when their members are sorted: the members
+        // of a cluster become consecutive rows in increasing cluster order, and the down sweep reads
+        // one contiguous range per cluster.
+        for (int l = (int)levels.size() - 2; l >= 1; --l) {
+            const HostLevel& A = levels[l];
+            std::vector<int32_t>& ag = aggs[l];
+            std::vector<int64_t> order(A.n), pos(A.n);
+            std::iota(order.begin(), order.end(), (int64_t)0);
+            std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return ag[x] < ag[y]; });
+            for (int64_t p = 0; p < A.n; ++p) pos[order[p]] = p;
+            HostLevel B;
+            B.n = A.n;
+            B.rp.assign(A.n + 1, 0);
+            B.d.resize(A.n);
+            B.ci.reserve(A.ci.size());
+            B.w.reserve(A.w.size());
+            std::vector<int32_t> ag2(A.n);
+            for (int64_t p = 0; p < A.n; ++p) {
+                const int64_t i = order[p];
+                B.d[p] = A.d[i];
+                for (int64_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+                    B.ci.push_back((int32_t)pos[A.ci[e]]);
+                    B.w.push_back(A.w[e]);
+                }
+                B.rp[p + 1] = (int64_t)B.ci.size();
+                ag2[p] = ag[i];
+            }
+            levels[l] = std::move(B);
+            ag = std::move(ag2);
+            for (int32_t& x : aggs[l - 1])
+                if (x >= 0) x = (int32_t)pos[x];
+        }
         const int L = (int)levels.size();
         H.nlev = L;
         H.lev.assign(L, MlLevel<T>{});
@@ -564,8 +596,8 @@ void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather,
     for (int l = 1; l <= nmid; ++l) {
         MlLevel<T>& D = H.lev[l];
         MlLevel<T>& C = H.lev[l + 1];
-        k_ml_down<T><<<ml_warp_grid(C.n), kThreads, 0, s>>>(D.b, D.dinv, D.rp, D.ci, D.w, D.mrp, D.mem, omega, C.n,
-                                                            C.b, done);
+        k_ml_down<T><<<ml_warp_grid(C.n), kThreads, 0, s>>>(D.b, D.dinv, D.rp, D.ci, D.w, D.mrp, omega, C.n, C.b,
+                                                            done);
     }
     if (tail) {
         static std::once_flag once;
