@@ -324,8 +324,9 @@ void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, in
 //   setup    one CTA per column i of Q0: one Newton-Schulz step q~_i = q_i (3/2) - Q0 Q0^T q_i / 2
 //            (keeps the warm-start basis orthonormal over many steps), d_i = q~_i^T H0 q~_i,
 //            z_i = q~_i^T h, and the largest |q_j^T H0 q~_i|, j != i; the last CTA deflates;
-//   roots    one warp per root: safeguarded Newton on (d_o - lambda) f(lambda) in coordinates
-//            centred on the nearer pole d_o, bisection when a step leaves the bracket;
+//   roots    one warp per root: safeguarded Newton, in coordinates centred on the nearer pole d_o,
+//            on f(lambda) times the interval's end poles, from the root of a one-pole model,
+//            bisection when a step leaves the bracket;
 //   zhat     one warp per undeflated pole (Loewner's formula as a product of bounded ratios);
 //   vectors  one CTA per eigenpair: the vector in the arrowhead basis, its place in ascending
 //            order, S(:, place) = Q~ x with the sign rule of outer_sym_eig.
@@ -334,8 +335,8 @@ void outer_sym_eig(const double* H, int ldh, int k, double* theta, double* S, in
 
 constexpr double kEpsD = 2.220446049250313e-16;   // unit roundoff x 2 (machine epsilon, binary64)
 constexpr int kArrowThreads = 64;                 // >= kMMax: one thread per row of H
-constexpr int kArrowMaxIt = 200;                  // iteration limit of one root (bisection alone needs < 2100
-                                                  // halvings in the worst case; Newton ends in ~10)
+constexpr int kArrowMaxIt = 200;                  // iteration limit of one root (Newton ends in 3-15; the
+                                                  // bracket test ends a run of bisection steps)
 constexpr int kArrowLd = kMMax + 1;
 
 __device__ __forceinline__ double warp_max(double v) {
@@ -518,11 +519,15 @@ __global__ void __launch_bounds__(kArrowThreads) k_arrow_setup(const double* H, 
 }
 
 // One warp per root j = blockIdx.x (0..m).  Root j lies between poles p_{j-1} and p_j (p_{-1} = -inf,
-// p_m = +inf).  With o the pole nearer to the root and mu = lambda - d_o:
-//   g(mu) = (alpha - d_o) - mu - S1(mu) + zeta_o / mu,   S1 = sum_{i != o} zeta_i / (delta_i - mu),
-//   h(mu) = -mu g(mu) (no pole at mu = 0), h'(mu) = -(alpha - d_o) + 2 mu + S1 + mu S2,
-// zeta_i = z_i^2, delta_i = d_i - d_o, S2 = sum_{i != o} zeta_i / (delta_i - mu)^2.  g decreases
-// through the root, so its sign keeps a bracket; Newton steps on h that leave it are replaced by
+// p_m = +inf).  With o the pole nearer to the root, f the interval's other end pole (none for the
+// two outer intervals) and mu = lambda - d_o:
+//   g(mu) = (alpha - d_o) - mu - S1(mu) + zeta_o / mu - zeta_f / (delta_f - mu),
+//   S1 = sum_{i != o, f} zeta_i / (delta_i - mu),  S2 = sum_{i != o, f} zeta_i / (delta_i - mu)^2,
+// zeta_i = z_i^2, delta_i = d_i - d_o.  Newton runs on F = (-mu)(delta_f - mu) g (h = -mu g without f),
+// which has no pole inside the interval:
+//   F = q r + zeta_o (mu - delta_f) + zeta_f mu,  q = mu^2 - delta_f mu,  r = (alpha - d_o) - mu - S1,
+//   F' = (2 mu - delta_f) r - q (1 + S2) + zeta_o + zeta_f.
+// g decreases through the root, so its sign keeps a bracket; steps that leave it are replaced by
 // bisection.
 __global__ void __launch_bounds__(32) k_arrow_roots(ArrowWork* aw) {
     if (aw->status) return;
@@ -539,11 +544,19 @@ __global__ void __launch_bounds__(32) k_arrow_roots(ArrowWork* aw) {
     const double zeta0 = z0 * z0, zeta1 = z1 * z1;
     auto pole_at = [&](int i) { return __shfl_sync(kFull, i < 32 ? p0 : p1, i & 31); };
     auto zeta_at = [&](int i) { return __shfl_sync(kFull, i < 32 ? zeta0 : zeta1, i & 31); };
-    // S1, S2 over the poles other than o, centred on d_o
-    auto sums = [&](int o, double po, double mu, double& s1, double& s2) {
+    // S1, S2 over the poles other than o and f, centred on d_o (one reciprocal per pole)
+    auto sums = [&](int o, int f, double po, double mu, double& s1, double& s2) {
         double a1 = 0.0, a2 = 0.0;
-        if (i0 < m && i0 != o) { const double den = (p0 - po) - mu, q = zeta0 / den; a1 += q; a2 += q / den; }
-        if (i1 < m && i1 != o) { const double den = (p1 - po) - mu, q = zeta1 / den; a1 += q; a2 += q / den; }
+        if (i0 < m && i0 != o && i0 != f) {
+            const double inv = 1.0 / ((p0 - po) - mu), q = zeta0 * inv;
+            a1 += q;
+            a2 += q * inv;
+        }
+        if (i1 < m && i1 != o && i1 != f) {
+            const double inv = 1.0 / ((p1 - po) - mu), q = zeta1 * inv;
+            a1 += q;
+            a2 += q * inv;
+        }
         s1 = warp_sum(a1);
         s2 = warp_sum(a2);
     };
@@ -563,27 +576,52 @@ __global__ void __launch_bounds__(32) k_arrow_roots(ArrowWork* aw) {
         const double pl = pole_at(j - 1), pr = pole_at(j);
         const double half = 0.5 * (pr - pl);
         double s1, s2;
-        sums(j - 1, pl, half, s1, s2);
+        sums(j - 1, -1, pl, half, s1, s2);
         const double gm = (alpha - pl) - half - s1 + zeta_at(j - 1) / half;
         if (gm > 0.0) { o = j; a = -half; b = 0.0; }      // root in (midpoint, p_j): centre on p_j
         else { o = j - 1; a = 0.0; b = half; }            // root in (p_{j-1}, midpoint]
     }
     const double po = pole_at(o), ao = alpha - po, zo = zeta_at(o);
-    double mu = 0.5 * (a + b);
+    // interior intervals: f is the other end pole; Newton runs on F = (-mu)(delta_f - mu) g(mu), which
+    // has neither pole of the interval; the outer intervals use h = -mu g(mu)
+    const int f = (j > 0 && j < m) ? (o == j - 1 ? j : j - 1) : -1;
+    const double df = f >= 0 ? pole_at(f) - po : 0.0, zf = f >= 0 ? zeta_at(f) : 0.0;
+    // start at the root of the model with the other poles' sum frozen at mu = 0:
+    // mu^2 - C mu - zeta_o = 0, C = (alpha - d_o) - S1(0) (- zeta_f / delta_f), taken on the bracket's side
+    double mu;
+    {
+        double s1, s2;
+        sums(o, f, po, 0.0, s1, s2);
+        const double cc = ao - s1 - (f >= 0 ? zf / df : 0.0), sq = sqrt(cc * cc + 4.0 * zo);
+        if (b == 0.0) mu = cc <= 0.0 ? 0.5 * (cc - sq) : -2.0 * zo / (cc + sq);
+        else mu = cc >= 0.0 ? 0.5 * (cc + sq) : 2.0 * zo / (sq - cc);
+        if (!(mu > a && mu < b)) mu = 0.5 * (a + b);
+    }
     for (int it = 0; it < kArrowMaxIt; ++it) {
         double s1, s2;
-        sums(o, po, mu, s1, s2);
-        const double gv = ao - mu - s1 + zo / mu;
+        sums(o, f, po, mu, s1, s2);
+        double gv, F, Fp;
+        if (f >= 0) {
+            gv = ao - mu - s1 + zo / mu - zf / (df - mu);
+            const double q = mu * mu - df * mu, r = ao - mu - s1;
+            F = q * r + zo * (mu - df) + zf * mu;
+            Fp = (2.0 * mu - df) * r - q * (1.0 + s2) + zo + zf;
+        } else {
+            gv = ao - mu - s1 + zo / mu;
+            F = -mu * ao + mu * mu + mu * s1 - zo;
+            Fp = -ao + 2.0 * mu + s1 + mu * s2;
+        }
         if (gv > 0.0) a = mu;
         else if (gv < 0.0) b = mu;
         else break;
-        const double h = -mu * ao + mu * mu + mu * s1 - zo;
-        const double hp = -ao + 2.0 * mu + s1 + mu * s2;
-        const double nw = mu - h / hp;
-        const double nxt = (nw > a && nw < b) ? nw : 0.5 * (a + b);
-        const bool done = fabs(nxt - mu) <= 2.0 * kEpsD * fabs(nxt) || (b - a) <= 2.0 * kEpsD * fmax(fabs(a), fabs(b));
+        const double nw = mu - F / Fp;
+        if (fabs(nw - mu) <= 4.0 * kEpsD * fabs(mu)) {      // Newton step of a few ulps: converged
+            if (nw >= a && nw <= b) mu = nw;
+            break;
+        }
+        const double nxt = (nw > a && nw < b) ? nw : 0.5 * (a + b);   // else bisection
         mu = nxt;
-        if (done) break;
+        if ((b - a) <= 4.0 * kEpsD * fmax(fabs(a), fabs(b))) break;
     }
     if (lane == 0) {
         aw->org[j] = aw->pole[o];
