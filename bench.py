@@ -302,13 +302,14 @@ def kernel_bytes(kind, n, Z, c, word, n_long=None, n_slices=None, ml=None):
         return 4 * n + (10 + c) * word * n
     if kind == "phase2_ml":
         # one application of the projected multilevel preconditioner with MINRES phase 2:
-        #   ml_phase2a (4 + c) w n, ml_project (4 + c) w n, ml_phase2b (2 + c) w n, ml_phase2c (2 + c) w n;
-        #   V-cycle level 0: two gathers, restriction (2 w n + 4 n), prolongation (3 w n + 4 n),
-        #   post-smoothing (5 w n); levels below: per level two CSR sweeps 2 (4 + w) nnz_l and
-        #   (16 + 5 w) n_l of vectors, cluster maps and member lists
+        #   ml_phase2a (4 + c) w n, ml_project (4 + c) w n, ml_phase2c (2 + c) w n;
+        #   V-cycle level 0: two gathers, restriction (2 w n + 4 n), prolongation (3 w n + 4 n);
+        #   ml_phase2b with level 0's post-smoothing: b, 1/D, x1, W x1, r_{k+1}, Vh read, w written
+        #   (6 + c) w n; levels below: per level two CSR sweeps 2 (4 + w) nnz_l and (16 + 5 w) n_l of
+        #   vectors, cluster maps and member lists
         n_c, nnz_c = ml
         struct = 8 * (n + 1) if not n_slices else 8 * (n_long + 1) + 8 * (n_slices + 1)
-        return ((26 + 4 * c) * word * n + 8 * n + 2 * (struct + 4 * Z)
+        return ((25 + 4 * c) * word * n + 8 * n + 2 * (struct + 4 * Z)
                 + 2 * (4 + word) * nnz_c + (16 + 5 * word) * n_c)
     if kind == "gather":
         struct = 8 * (n + 1) if not n_slices else 8 * (n_long + 1) + 8 * (n_slices + 1)

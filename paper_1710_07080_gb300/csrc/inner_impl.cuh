@@ -742,7 +742,8 @@ __global__ void k_copy_vcol(const double* src, T* dst, int64_t n) {
 //       alpha_k = alpha' + (g_k / beta_k)^T u1 with g_k = Vh^T z_k from the phase-2c launch before;
 //   ml_phase2a: r_{k+1} = y' + Vh u1 - (alpha_k / beta_k) r_k and h = Vh^T r_{k+1};
 //   ml_project: rin = r_{k+1} - Vh h (= Pi r);   V-cycle: w = M^{-1} rin;
-//   ml_phase2b: Vh^T w, r^T w; last CTA: tv = D h - Vh^T w, beta_{k+1}^2 = r^T w + h^T tv, Givens step;
+//   ml_phase2b: the V-cycle's last level-0 step (w), Vh^T w, r^T w; last CTA: tv = D h - Vh^T w,
+//       beta_{k+1}^2 = r^T w + h^T tv, Givens step;
 //   ml_phase2c: z_{k+1} = w + Vh tv (= Pi w + Vh D h), 1^T z_{k+1} and g_{k+1} = Vh^T z_{k+1}.
 
 template <typename T, int NC>
@@ -980,7 +981,18 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase2b(InnerArgs<T> a, int ini
     const int64_t step = (int64_t)gridDim.x * blockDim.x * VN;
     for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r0 < n; r0 += step) {
         T w[VN], r[VN];
-        vld(a.wv + r0, w);
+        if (a.ml_fuse_post) {
+            // the V-cycle's last step on level 0: w = x1 + w D^{-1} (b - D x1 + W x1), stored for phase 2c
+            T bb[VN], di[VN], x1[VN], wx[VN];
+            vld(a.ml_b0 + r0, bb);
+            vld(a.ml_dinv0 + r0, di);
+            vld(a.ml_x1 + r0, x1);
+            vld(a.ml_wx1 + r0, wx);
+#pragma unroll
+            for (int e = 0; e < VN; ++e) w[e] = x1[e] + a.ml_omega * (bb[e] * di[e] - x1[e] + wx[e] * di[e]);
+        } else {
+            vld(a.wv + r0, w);
+        }
         vld(a.rcur + r0, r);
 #pragma unroll
         for (int e = 0; e < VN; ++e) {
@@ -988,6 +1000,7 @@ __global__ void __launch_bounds__(kThreads) k_ml_phase2b(InnerArgs<T> a, int ini
             w[e] = ok ? w[e] : T(0);
             acc[0] += (ok ? r[e] : T(0)) * w[e];
         }
+        if (a.ml_fuse_post) vst(a.wv + r0, w);
 #pragma unroll
         for (int t = 0; t < NE; ++t) {
             if (t < c) {

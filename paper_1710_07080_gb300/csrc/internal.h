@@ -54,8 +54,8 @@ template <typename T> void ml_free(MlHierarchy<T>& H);
 // out = M^{-1} b, one V-cycle; kernels return at once while *done != 0 (done may be null)
 template <typename T>
 void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather, T omega, T alpha, const int* done,
-               bool x0_ready, cudaStream_t s);
-template <typename T> int ml_launches(const MlHierarchy<T>& H, bool x0_ready);
+               bool x0_ready, bool skip_post0, cudaStream_t s);
+template <typename T> int ml_launches(const MlHierarchy<T>& H, bool x0_ready, bool skip_post0);
 
 // ------------------------------------------------------------------ inner solve
 // State of one preconditioned MINRES solve (Paige & Saunders 1975) kept in device
@@ -105,6 +105,10 @@ struct InnerArgs {
     T* ml_x0;                   // level 0's x0 = w D^{-1} rin, written by the projection kernel (or null)
     const T* ml_dinv0;          // level 0's 1 / diagonal
     T ml_omega;
+    // level 0's post-smoothing done by phase 2b (ml_fuse_post): w = x1 + w D^{-1} (b - D x1 + W x1)
+    // from the V-cycle input b, x1 and W x1
+    int ml_fuse_post;
+    const T* ml_b0; const T* ml_x1; const T* ml_wx1;
     const double* dv;
     double* partial_d;          // the partial-sum buffer viewed as doubles (FP64 Gram sums)
     T tau; int max_it;

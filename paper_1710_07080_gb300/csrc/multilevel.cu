@@ -576,9 +576,11 @@ static bool ml_use_tail(const MlHierarchy<T>& H) {
 // out = M^{-1} b (b on level 0, n-space, the trimmed entry ignored; out may alias nothing else).
 // gather(x, g) must compute g = sum over neighbours of x for level 0 (the solver's gather).
 // x0_ready: level 0's x0 = w D^{-1} b is already in H.lev[0].x0 (written by the caller's kernel).
+// skip_post0 (nlev >= 2): stop after the gather of x1 (W x1 in H.lev[0].x0); the caller's next kernel
+// does level 0's post-smoothing (out is then not written).
 template <typename T>
 void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather, T omega, T alpha, const int* done,
-               bool x0_ready, cudaStream_t s) {
+               bool x0_ready, bool skip_post0, cudaStream_t s) {
     const int L = H.nlev;
     if (L == 1) {
         k_ml_dense<T><<<ml_warp_grid(H.lev[0].n), kThreads, 0, s>>>(H.inv, b, H.lev[0].n, out, done);
@@ -623,14 +625,15 @@ void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather,
     // level 0 up: prolong, neighbour sums of x1, post-smooth
     k_ml_prolong<T><<<ml_grid(F.n), kThreads, 0, s>>>(b, F.dinv, F.agg, H.lev[1].x, omega, alpha, F.n, F.x1, done);
     gather(F.x1, F.x0, s);                                           // F.x0 <- W x1 (x0 is free now)
-    k_ml_post<T><<<ml_grid(F.n), kThreads, 0, s>>>(b, F.dinv, F.x1, F.x0, omega, F.n, H.skip, out, done);
+    if (!skip_post0)
+        k_ml_post<T><<<ml_grid(F.n), kThreads, 0, s>>>(b, F.dinv, F.x1, F.x0, omega, F.n, H.skip, out, done);
 }
 
 template <typename T>
-int ml_launches(const MlHierarchy<T>& H, bool x0_ready) {
+int ml_launches(const MlHierarchy<T>& H, bool x0_ready, bool skip_post0) {
     if (H.nlev <= 1) return 1;
     const int nmid = ml_use_tail(H) ? H.nlev - 3 : H.nlev - 2;
-    return (x0_ready ? 0 : 1) + 2 + 2 * nmid + 1 + 3;
+    return (x0_ready ? 0 : 1) + 2 + 2 * nmid + 1 + (skip_post0 ? 2 : 3);
 }
 
 #define ISIRA_INSTANTIATE_ML(T)                                                                              \
@@ -638,8 +641,8 @@ int ml_launches(const MlHierarchy<T>& H, bool x0_ready) {
                                      int64_t, int64_t, cudaStream_t);                                        \
     template void ml_free<T>(MlHierarchy<T>&);                                                               \
     template void ml_vcycle<T>(MlHierarchy<T>&, const T*, T*, const GatherFn<T>&, T, T, const int*, bool,     \
-                               cudaStream_t);                                                                \
-    template int ml_launches<T>(const MlHierarchy<T>&, bool);
+                               bool, cudaStream_t);                                                          \
+    template int ml_launches<T>(const MlHierarchy<T>&, bool, bool);
 ISIRA_INSTANTIATE_ML(float)
 ISIRA_INSTANTIATE_ML(double)
 

@@ -193,6 +193,10 @@ InnerArgs<T> make_args(isira_handle h, InnerBuffers<T>& b, double sigma, int c, 
         if (b.H.nlev >= 2) {
             a.ml_x0 = b.H.lev[0].x0;
             a.ml_dinv0 = b.H.lev[0].dinv;
+            a.ml_fuse_post = 1;
+            a.ml_b0 = c > 0 ? a.rin : a.rcur;
+            a.ml_x1 = b.H.lev[0].x1;
+            a.ml_wx1 = b.H.lev[0].x0;
         }
         a.ml_omega = (T)kMlOmega;
     }
@@ -371,7 +375,7 @@ void ml_iteration(isira_handle h, InnerBuffers<T>& b, const InnerArgs<T>& a, cud
     ml_phase2a<T>(a, 0, s);
     ml_project<T>(a, 0, s);
     ml_vcycle<T>(b.H, a.c > 0 ? a.rin : a.rcur, a.wv, gather, (T)kMlOmega, ml_alpha<T>(h), done,
-                 a.c > 0 && a.ml_x0 != nullptr, s);
+                 a.c > 0 && a.ml_x0 != nullptr, a.ml_fuse_post != 0, s);
     ml_phase2b<T>(a, 0, cond, has_cond, s);
     ml_phase2c<T>(a, 0, s);
 }
@@ -402,7 +406,7 @@ cudaGraphExec_t build_ml_graph(isira_handle h, InnerBuffers<T>& b, const InnerAr
 
 template <typename T>
 int ml_launches_per_iteration(const InnerBuffers<T>& b, int c) {
-    return 6 + (c > 0 ? 1 : 0) + ml_launches(b.H, c > 0 && b.H.nlev >= 2);
+    return 6 + (c > 0 ? 1 : 0) + ml_launches(b.H, c > 0 && b.H.nlev >= 2, b.H.nlev >= 2);
 }
 
 // One inner solve with the multilevel preconditioner; same contract as run_inner.  lam: the
@@ -425,7 +429,7 @@ int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const 
     ml_phase2a<T>(a, 1, s);
     ml_project<T>(a, 1, s);
     ml_vcycle<T>(b.H, c > 0 ? a.rin : a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), nullptr,
-                 c > 0 && a.ml_x0 != nullptr, s);
+                 c > 0 && a.ml_x0 != nullptr, a.ml_fuse_post != 0, s);
     ml_phase2b<T>(a, 1, cudaGraphConditionalHandle{}, 0, s);
     ml_phase2c<T>(a, 1, s);
     const int per_it = ml_launches_per_iteration(b, c);
@@ -453,7 +457,7 @@ int run_inner_ml(isira_handle h, InnerBuffers<T>& b, double sigma, int c, const 
             ml_phase2a<T>(a, 0, s);
             ml_project<T>(a, 0, s);
             ml_vcycle<T>(b.H, c > 0 ? a.rin : a.rcur, a.wv, gather0, (T)kMlOmega, ml_alpha<T>(h), &a.st->done,
-                         c > 0 && a.ml_x0 != nullptr, s);
+                         c > 0 && a.ml_x0 != nullptr, a.ml_fuse_post != 0, s);
             ml_phase2b<T>(a, 0, cudaGraphConditionalHandle{}, 0, s);
             ml_phase2c<T>(a, 0, s);
             if (prof) ck(cudaEventRecord(h->ev[4 * i + 3], s));
@@ -800,7 +804,7 @@ void precond_apply_t(isira_handle h, InnerBuffers<T>& b, const T* d_x, T* d_y) {
     if (h->perm) to_internal<T>(d_x, h->perm, h->n, xin, s);
     else ck(cudaMemcpyAsync(xin, d_x, sizeof(T) * h->n, cudaMemcpyDeviceToDevice, s));
     GatherFn<T> gather = [&](const T* x, T* g, cudaStream_t st) { inner_gather_vec<T>(a, x, g, h->lanes, nullptr, st); };
-    ml_vcycle<T>(b.H, xin, yout, gather, (T)kMlOmega, ml_alpha<T>(h), nullptr, false, s);
+    ml_vcycle<T>(b.H, xin, yout, gather, (T)kMlOmega, ml_alpha<T>(h), nullptr, false, false, s);
     if (h->perm) to_external<T>(yout, h->perm, h->n, d_y, s);
     else ck(cudaMemcpyAsync(d_y, yout, sizeof(T) * h->n, cudaMemcpyDeviceToDevice, s));
     sync(h);
