@@ -416,23 +416,49 @@ SAMPLE_CAPS = {"grid128^3": (2, 150), "rmat20": (3, 5000), "grid100x100": (10000
                "rgg4M": (1, 60), "rmat24": (1, 20)}
 
 
-def oracle_sample(g, k, eps, u0, workload):
+# inner iterations of the oracle timed at the workload's average deflation rank
+INNER_RATE_ITERS = {"grid128^3": 40, "rmat20": 60, "grid100x100": 400, "rgg4M": 20, "rmat24": 8}
+
+
+def oracle_inner_rate(g, c, iters):
+    """Seconds per inner MINRES iteration of the oracle (trimmed operator, preconditioner, MINRES
+    update) with a deflation basis of c orthonormal columns: the capped run below only reaches the
+    first eigenpair (c = 0), while the cost of an iteration grows with c."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(7)
+    V = np.linalg.qr(rng.standard_normal((g.n, c)))[0] if c > 0 else None
+    r = rng.standard_normal(g.n)
+    r -= r.mean()
+    trim = int(np.argmax(g.degrees))
+    t0 = time.perf_counter()
+    _, it, _ = oracle.inner_solve(g.row_ptr, g.col_idx, trim, 0.0, 2.0 * float(g.degrees.max()), V, r,
+                                  tau=1e-300, max_it=iters)
+    return (time.perf_counter() - t0) / max(1, it), it
+
+
+def oracle_sample(g, k, eps, u0, workload, c_avg):
     """Runs the oracle on the workload with outer steps and inner iterations capped (a bounded
-    sample); returns its wall seconds and its stats (per-phase seconds and unit counts)."""
+    sample), then times inner iterations at deflation rank round(c_avg); returns the wall seconds
+    and the stats (per-phase seconds and unit counts, plus the per-iteration rate at that rank)."""
     import oracle
     max_outer, max_inner = SAMPLE_CAPS.get(workload, (2, 100))
     t0 = time.perf_counter()
     _, _, st = oracle.isira(g.row_ptr, g.col_idx, k, u0, eps=eps, tau_inner=1e-3, max_outer=max_outer,
                             max_inner=max_inner)
+    c = int(round(c_avg))
+    st["rate_c"] = c
+    st["rate_sec_per_it"], st["rate_iters"] = oracle_inner_rate(g, c, INNER_RATE_ITERS.get(workload, 50))
     return time.perf_counter() - t0, st
 
 
 def project(st_sample, counts):
     """Seconds of a full run from the sample's per-unit costs: seconds per recomputed W column (the
-    W_k, H_k step of Algorithm 2), per inner MINRES iteration (its inner solve) and per outer step
-    (the rest), times the full run's counts of those units."""
+    W_k, H_k step of Algorithm 2), per inner MINRES iteration (its inner solve, at the average
+    deflation rank) and per outer step (the rest), times the full run's counts of those units."""
     per_col = st_sample["sec_w"] / max(1, st_sample["w_columns"])
-    per_it = st_sample["sec_inner"] / max(1, st_sample["inner_iters"])
+    per_it = st_sample.get("rate_sec_per_it") or st_sample["sec_inner"] / max(1, st_sample["inner_iters"])
     rest = st_sample["sec_total"] - st_sample["sec_w"] - st_sample["sec_inner"]
     per_step = rest / max(1, st_sample["outer_steps"])
     return per_col * counts["w_columns"] + per_it * counts["inner_iters"] + per_step * counts["outer_steps"]
@@ -454,7 +480,9 @@ def sample_text(st, counts, src):
     return (f"Algorithm 2 by the FP64 oracle (tau_inner 1e-3, 1 thread) on the same graph at the same eps, "
             f"capped at {st['outer_steps']} outer steps and {st['inner_iters']} inner iterations (measured "
             f"{st['sec_total']:.1f} s: {st['sec_inner'] / max(1, st['inner_iters']) * 1e3:.2f} ms per inner "
-            f"iteration, {st['sec_w'] / max(1, st['w_columns']) * 1e3:.2f} ms per recomputed W column); scaled to "
+            f"iteration at deflation rank 0, {st['sec_w'] / max(1, st['w_columns']) * 1e3:.2f} ms per recomputed "
+            f"W column), then {st['rate_iters']} oracle inner iterations at deflation rank {st['rate_c']} (the "
+            f"solve's average; {st['rate_sec_per_it'] * 1e3:.2f} ms each); scaled to "
             f"one full solve with the unit counts {counts['inner_iters']} inner iterations, {counts['w_columns']} W "
             f"columns, {counts['outer_steps']} outer steps ({src})")
 
@@ -481,7 +509,8 @@ def run_reference(args):
     values, walls, st = [], [], None
     t_all = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        dt, st = oracle_sample(g, k, eps, u0, args.workload)
+        # average deflation rank over the inner iterations, taken as (k - 1) / 2 (no GPU run here)
+        dt, st = oracle_sample(g, k, eps, u0, args.workload, (k - 1) / 2.0)
         if i >= args.warmup:
             values.append(project(st, counts))
             walls.append(dt)
@@ -794,7 +823,8 @@ def main():
             counts = {"inner_iters": s64["inner_iters"], "w_columns": s64["w_columns"],
                       "outer_steps": s64["outer_steps"]}
             src = {"file": "unit counts of the GPU FP64 solve of this run (same algorithm, same eps)"}
-        dt, st = oracle_sample(g, k, eps, u0_h.numpy(), args.workload)
+        c_avg = line.get("roofline", {}).get("avg_deflation_rank") or (k - 1) / 2.0
+        dt, st = oracle_sample(g, k, eps, u0_h.numpy(), args.workload, c_avg)
         line["cpu_baseline"] = {"value": project(st, counts), "unit": "s", "cores": 1, "kind": "oracle",
                                 "sample": sample_text(st, counts, src["file"]), "sample_seconds": dt,
                                 "host": host_cpu()}
