@@ -25,8 +25,8 @@
 // prolongation / post-smoothing kernel around them (x0 itself usually comes from the caller's
 // projection kernel); each level l >= 1 takes one fused kernel down and one up, forming x0 and x1 of
 // the neighbours on the fly instead of storing them; the two coarsest levels, when small, run as
-// one CTA (k_ml_tail).  Five levels (the 128^3 grid: 2.1M, 264K, 15K, 690, 38 vertices) take 10
-// launches.
+// one CTA (k_ml_tail).  Five levels (the 128^3 grid: 2.1M, 264K, 15K, 690, 38 vertices) take 9
+// launches when the caller forms x0 and does level 0's post-smoothing in its own kernels.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
