@@ -298,8 +298,8 @@ def kernel_bytes(kind, n, Z, c, word, n_long=None, n_slices=None, ml=None):
                 adds 8 n.
     c is the launch's deflation rank (averaged over the timed launches)."""
     extra = 8 * n if word == 8 else 0
-    if kind == "rows_ml":      # k_ml_phase1: as rows, plus r_{k-1}; no reciprocal diagonal
-        return 4 * n + (10 + c) * word * n
+    if kind == "rows_ml":      # k_ml_phase1: degrees 4n, 7 vectors read (row sums, z_k, z_{k-1}, r_{k-1},
+        return 4 * n + 10 * word * n   # two w buffers, x), 3 written; Vh^T z_k comes from phase 2c
     if kind == "phase2_ml":
         # one application of the projected multilevel preconditioner with MINRES phase 2:
         #   ml_phase2a (4 + c) w n, ml_project (4 + c) w n, ml_phase2c (2 + c) w n;

@@ -291,12 +291,15 @@ __global__ void __launch_bounds__(kThreads) k_ml_dense(const T* __restrict__ inv
 // On levels l >= 1 the rows are ordered by cluster (ml_build), so the members of cluster I are the
 // rows mrp[I] .. mrp[I+1]-1 and their entries one contiguous CSR range: one warp per cluster, lanes
 // striding over the rows and over the entries (coalesced), G lanes per row in the up sweep.
+// x0 / x1 (FP64 only, else null): the level's x0 = w D^{-1} b / x1 stored by a separate kernel, read
+// instead of formed per entry: on this part an FP64 multiply costs as much as a load, so the FP64
+// path stores the vectors and the FP32 path forms them on the fly.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_ml_down(const T* __restrict__ b, const T* __restrict__ dinv,
                                                       const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                                       const T* __restrict__ w, const int64_t* __restrict__ mrp,
                                                       T om, int64_t nc, T* __restrict__ bc,
-                                                      const int* __restrict__ done) {
+                                                      const T* __restrict__ x0, const int* __restrict__ done) {
     if (done && *done) return;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -305,11 +308,16 @@ __global__ void __launch_bounds__(kThreads) k_ml_down(const T* __restrict__ b, c
         const int64_t r_beg = mrp[I], r_end = mrp[I + 1];
         T own = T(0), s = T(0);
         for (int64_t i = r_beg + lane; i < r_end; i += 32) own += b[i];
-        for (int32_t e = rp[r_beg] + lane; e < rp[r_end]; e += 32) {
-            const int32_t c = ci[e];
-            s += w[e] * (b[c] * dinv[c]);
+        if (x0) {
+            for (int32_t e = rp[r_beg] + lane; e < rp[r_end]; e += 32) s += w[e] * x0[ci[e]];
+        } else {
+            for (int32_t e = rp[r_beg] + lane; e < rp[r_end]; e += 32) {
+                const int32_t c = ci[e];
+                s += w[e] * (b[c] * dinv[c]);
+            }
+            s *= om;
         }
-        const T acc = warp_sum((T(1) - om) * own + om * s);
+        const T acc = warp_sum((T(1) - om) * own + s);
         if (lane == 0) bc[I] = acc;
     }
 }
@@ -319,7 +327,8 @@ __global__ void __launch_bounds__(kThreads) k_ml_up(const T* __restrict__ b, con
                                                     const int32_t* __restrict__ agg, const T* __restrict__ xc,
                                                     const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                                     const T* __restrict__ w, T om, T alpha, int64_t n,
-                                                    T* __restrict__ out, const int* __restrict__ done) {
+                                                    T* __restrict__ out, const T* __restrict__ x1v,
+                                                    const int* __restrict__ done) {
     if (done && *done) return;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -330,16 +339,20 @@ __global__ void __launch_bounds__(kThreads) k_ml_up(const T* __restrict__ b, con
         const bool valid = row < n;
         T s = T(0);
         if (valid) {
-            for (int32_t e = rp[row] + j; e < rp[row + 1]; e += G) {
-                const int32_t c = ci[e];
-                s += w[e] * (om * b[c] * dinv[c] + alpha * xc[agg[c]]);
+            if (x1v) {
+                for (int32_t e = rp[row] + j; e < rp[row + 1]; e += G) s += w[e] * x1v[ci[e]];
+            } else {
+                for (int32_t e = rp[row] + j; e < rp[row + 1]; e += G) {
+                    const int32_t c = ci[e];
+                    s += w[e] * (om * b[c] * dinv[c] + alpha * xc[agg[c]]);
+                }
             }
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (valid && j == 0) {
             const T bi = b[row], di = dinv[row];
-            const T x1 = om * bi * di + alpha * xc[agg[row]];
+            const T x1 = x1v ? x1v[row] : om * bi * di + alpha * xc[agg[row]];
             out[row] = x1 + om * (bi * di - x1 + s * di);
         }
     }
@@ -595,11 +608,13 @@ void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather,
     gather(F.x0, F.x, s);                                            // F.x <- W x0
     k_ml_restrict<T><<<ml_grid(H.lev[1].n), kThreads, 0, s>>>(b, F.x, T(1) - omega, F.mrp, F.mem, H.lev[1].n,
                                                               H.lev[1].b, done);
+    constexpr bool store = sizeof(T) == 8;          // FP64: x0 and x1 stored, not formed per entry
     for (int l = 1; l <= nmid; ++l) {
         MlLevel<T>& D = H.lev[l];
         MlLevel<T>& C = H.lev[l + 1];
+        if (store) k_ml_scale<T><<<ml_grid(D.n), kThreads, 0, s>>>(D.b, D.dinv, omega, D.n, -1, D.x0, done);
         k_ml_down<T><<<ml_warp_grid(C.n), kThreads, 0, s>>>(D.b, D.dinv, D.rp, D.ci, D.w, D.mrp, omega, C.n, C.b,
-                                                            done);
+                                                            store ? D.x0 : nullptr, done);
     }
     if (tail) {
         static std::once_flag once;
@@ -618,9 +633,12 @@ void ml_vcycle(MlHierarchy<T>& H, const T* b, T* out, const GatherFn<T>& gather,
     }
     for (int l = nmid; l >= 1; --l) {
         MlLevel<T>& D = H.lev[l];
+        if (store)
+            k_ml_prolong<T><<<ml_grid(D.n), kThreads, 0, s>>>(D.b, D.dinv, D.agg, H.lev[l + 1].x, omega, alpha, D.n,
+                                                              D.x1, done);
         k_ml_up<T, kMlLanes><<<ml_group_grid(D.n, kMlLanes), kThreads, 0, s>>>(D.b, D.dinv, D.agg, H.lev[l + 1].x, D.rp,
                                                                                 D.ci, D.w, omega, alpha, D.n, D.x,
-                                                                                done);
+                                                                                store ? D.x1 : nullptr, done);
     }
     // level 0 up: prolong, neighbour sums of x1, post-smooth
     k_ml_prolong<T><<<ml_grid(F.n), kThreads, 0, s>>>(b, F.dinv, F.agg, H.lev[1].x, omega, alpha, F.n, F.x1, done);
@@ -633,7 +651,7 @@ template <typename T>
 int ml_launches(const MlHierarchy<T>& H, bool x0_ready, bool skip_post0) {
     if (H.nlev <= 1) return 1;
     const int nmid = ml_use_tail(H) ? H.nlev - 3 : H.nlev - 2;
-    return (x0_ready ? 0 : 1) + 2 + 2 * nmid + 1 + (skip_post0 ? 2 : 3);
+    return (x0_ready ? 0 : 1) + 2 + (sizeof(T) == 8 ? 4 : 2) * nmid + 1 + (skip_post0 ? 2 : 3);
 }
 
 #define ISIRA_INSTANTIATE_ML(T)                                                                              \
