@@ -387,9 +387,9 @@ def sym_eig_warm(H, S0):
     if not isinstance(H, torch.Tensor) or H.dim() != 2 or H.shape[0] != H.shape[1] or not 2 <= H.shape[0] <= 64:
         raise ValueError("H must be a square matrix of order 2..64")
     k = H.shape[0]
-    _check_tensor(H.contiguous(), "H", (torch.float64,), (k, k))
     if not isinstance(S0, torch.Tensor) or S0.dim() != 2 or S0.shape[0] != S0.shape[1] or S0.shape[0] not in (k - 1, k):
         raise ValueError("S0 must be square of order k-1 or k")
+    _check_tensor(H.contiguous(), "H", (torch.float64,), (k, k))
     _check_tensor(S0.contiguous(), "S0", (torch.float64,), tuple(S0.shape))
     _check_cuda(H=H, S0=S0)
     w = S0.shape[0]

@@ -73,3 +73,23 @@ def test_vector_checks(isira):
     with pytest.raises(ValueError, match="dtype"):
         isira._check_x(x.int(), 4)
     assert isira._check_V(None, 4) == 0
+
+
+def test_sym_eig_warm_rejections(isira):
+    H = torch.eye(4, dtype=torch.float64)
+    with pytest.raises(ValueError, match="order 2..64"):
+        isira.sym_eig_warm(torch.eye(1, dtype=torch.float64), torch.eye(1, dtype=torch.float64))
+    with pytest.raises(ValueError, match="order k-1 or k"):
+        isira.sym_eig_warm(H, torch.eye(2, dtype=torch.float64))
+    with pytest.raises(ValueError, match="must have dtype"):
+        isira.sym_eig_warm(H.float(), torch.eye(3, dtype=torch.float64))
+    with pytest.raises(ValueError, match="must be a CUDA tensor"):
+        isira.sym_eig_warm(H, torch.eye(3, dtype=torch.float64))
+
+
+def test_abi_rejects_bad_warm_start_sizes(isira):
+    lib = isira.lib
+    assert lib.isira_sym_eig_warm(1, 0, None, None, None, None, None) == isira.ISIRA_ERR_INVALID_ARG
+    assert lib.isira_sym_eig_warm(8, 5, 8, 8, 8, None, None) == isira.ISIRA_ERR_INVALID_ARG     # warm_w < k - 1
+    assert lib.isira_sym_eig_warm(65, 64, 8, 8, 8, None, None) == isira.ISIRA_ERR_INVALID_ARG   # k > 64
+    assert lib.isira_residual_history(None, None, 0, None) == isira.ISIRA_ERR_INVALID_ARG
