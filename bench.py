@@ -326,8 +326,9 @@ KERNEL_NAMES = {"gather": "k_phase1_gather (trimmed-operator SpMV gather)",
                 "phase2": "k_phase2 (SMW preconditioner + MINRES reductions)"}
 KERNEL_NAMES_ML = {"gather": "k_phase1_gather (trimmed-operator SpMV gather)",
                    "rows": "k_ml_phase1 (operator row epilogue + MINRES update)",
-                   "phase2": "multilevel phase 2: ml_phase2a, ml_project, one V-cycle (10-25 launches incl. "
-                             "two level-0 gathers), ml_phase2b, ml_phase2c"}
+                   "phase2": "multilevel phase 2 (13 launches on the 128^3 grid in FP32): ml_phase2a, ml_project, "
+                             "one V-cycle (two level-0 gathers, restriction, prolongation, fused coarse-level "
+                             "sweeps), ml_phase2b with the level-0 post-smoothing, ml_phase2c"}
 STAT_OF = {"gather": "inner_phase1_ms", "rows": "inner_rows_ms", "phase2": "inner_phase2_ms"}
 
 GATHER_SOURCES = ["paper_1710_07080_gb300/csrc/common.cuh", "paper_1710_07080_gb300/csrc/inner_impl.cuh"]
