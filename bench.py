@@ -413,12 +413,12 @@ def oracle_counts(workload):
                                "oracle_seconds_on_build_host": g.get("oracle_seconds")}
 
 
-SAMPLE_CAPS = {"grid128^3": (2, 150), "rmat20": (3, 5000), "grid100x100": (100000, 20000),
+SAMPLE_CAPS = {"grid128^3": (2, 100), "rmat20": (3, 5000), "grid100x100": (100000, 20000),
                "rgg4M": (1, 60), "rmat24": (1, 20)}
 
 
 # inner iterations of the oracle timed at the workload's average deflation rank
-INNER_RATE_ITERS = {"grid128^3": 40, "rmat20": 60, "grid100x100": 400, "rgg4M": 20, "rmat24": 8}
+INNER_RATE_ITERS = {"grid128^3": 24, "rmat20": 60, "grid100x100": 400, "rgg4M": 20, "rmat24": 8}
 
 
 def oracle_inner_rate(g, c, iters):
