@@ -89,14 +89,14 @@ def solver_opts(args):
 
 # the configurations: k, the precision of the headline value, the tolerance rule, the reference
 WORKLOADS = {
-    "grid128^3": dict(k=20, prec="mixed", tol="c4", ref="grid3d:128,128,128", desc="3-D 7-point grid 128^3"),
-    "rmat20": dict(k=10, prec="fp64", tol="c4", ref="golden:rmat20_tight.json",
+    "grid128^3": dict(k=20, prec="mixed", tol="accuracy", ref="grid3d:128,128,128", desc="3-D 7-point grid 128^3"),
+    "rmat20": dict(k=10, prec="fp64", tol="accuracy", ref="golden:rmat20_tight.json",
                    desc="R-MAT scale 20, edge factor 16, a,b,c,d=.57/.19/.19/.05, seed 1, symmetrised LCC"),
     "grid100x100": dict(k=5, prec="fp64", tol="abs:1e-10", ref="grid2d:100,100", desc="2-D 5-point grid 100 x 100"),
-    "rgg4M": dict(k=20, prec="mixed", tol="c4", ref=None,
+    "rgg4M": dict(k=20, prec="mixed", tol="accuracy", ref=None,
                   desc="random geometric graph, unit square, n = 4e6, r = sqrt(12/(pi n)), seed 1, LCC "
                        "(GPU cell-list generator)"),
-    "rmat24": dict(k=10, prec="mixed", tol="c4", ref=None,
+    "rmat24": dict(k=10, prec="mixed", tol="accuracy", ref=None,
                    desc="R-MAT scale 24, edge factor 16, same a,b,c,d, seed 1, symmetrised LCC (GPU generator)"),
     "batch256": dict(k=8, prec="mixed", tol="rel:1e-8", ref=None,
                      desc="256 graphs, n log-uniform in [1e3, 2e5]: ER mean degree 8 / 2-D grid / WS k=10 p=0.1"),
@@ -402,7 +402,7 @@ def kernel_rooflines(st, n, Z, word, workload, prec_tag):
 def oracle_counts(workload):
     """Unit counts of the FP64 oracle's own full run at the accuracy tolerance (tests/golden,
     written by tests/golden/make_golden.py, which calls only oracle/)."""
-    name = {"grid128^3": "grid128_c4.json", "rmat20": "rmat20_c4.json"}.get(workload)
+    name = {"grid128^3": "grid128_accuracy.json", "rmat20": "rmat20_accuracy.json"}.get(workload)
     if name is None:
         return None, None
     path = os.path.join(ROOT, "tests", "golden", name)

@@ -1,6 +1,7 @@
-"""CPU checks of bench.py's host-side arithmetic: the accuracy-driven lock tolerance (the survey's
-rule C4) reproduces the tolerance the oracle's golden 128^3-grid run was made at, from the grid's
-closed-form spectrum; the byte models and the CPU-baseline projection are the stated sums."""
+"""CPU checks of bench.py's host-side arithmetic: the accuracy-driven lock tolerance
+min(1e-8 ||L||, sqrt(1e-10 lambda_j gap_j)) reproduces the tolerance the oracle's golden 128^3-grid
+run was made at, from the grid's closed-form spectrum; the byte models and the CPU-baseline
+projection are the stated sums."""
 import json
 import math
 import os
@@ -19,8 +20,8 @@ def _grid_spectrum(dims, k):
     return np.sort(lam)[1:k + 1]
 
 
-def test_c4_tolerance_of_the_128_grid_matches_the_golden_run():
-    g = json.load(open(os.path.join(ROOT, "tests", "golden", "grid128_c4.json")))
+def test_accuracy_tolerance_of_the_128_grid_matches_the_golden_run():
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "grid128_accuracy.json")))
     eps = bench.accuracy_eps(_grid_spectrum([128, 128, 128], 20), 12.0)
     # the golden run took its estimates from a loose GPU solve; the closed form gives the same
     # tolerance to the accuracy of those estimates
@@ -28,7 +29,7 @@ def test_c4_tolerance_of_the_128_grid_matches_the_golden_run():
     assert eps < 1e-8 * 12.0
 
 
-def test_c4_tolerance_merges_clusters_and_caps_at_the_residual_bar():
+def test_accuracy_tolerance_merges_clusters_and_caps_at_the_residual_bar():
     # a triple eigenvalue and a well separated one: only the gap to the other cluster counts
     lam = [1.0, 1.0 + 1e-9, 1.0 - 1e-9, 2.0]
     assert math.isclose(bench.accuracy_eps(lam, 1e4), math.sqrt(1e-10 * (1.0 - 1e-9) * (1.0 + 1e-9)))

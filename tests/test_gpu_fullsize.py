@@ -95,15 +95,15 @@ def test_rmat20_accuracy_tolerance_matches_oracle(rmat20, prec):
     g = rmat20
     normL = 2.0 * g.degrees.max()
     eps = bench.accuracy_eps(golden("rmat20_bench.json")["eigvals"], normL)
-    c4 = golden("rmat20_c4.json")
-    assert abs(eps - c4["eps_abs"]) <= 1e-3 * eps
+    acc = golden("rmat20_accuracy.json")
+    assert abs(eps - acc["eps_abs"]) <= 1e-3 * eps
     res = solve(g, prec, eps_abs=eps)
     assert res.status == 0
     lam = res.eigvals.numpy()
     V = res.eigvecs.cpu().numpy()
     r = oracle_residuals(g, lam, V)
     assert r.max() <= 1e-8 and r.max() * normL <= 1.01 * eps
-    for ref in (golden("rmat20_tight.json")["eigvals"], c4["eigvals"]):
+    for ref in (golden("rmat20_tight.json")["eigvals"], acc["eigvals"]):
         np.testing.assert_allclose(lam, ref, rtol=1e-9)
     np.testing.assert_allclose(V.T @ V, np.eye(10), atol=1e-10)
 
